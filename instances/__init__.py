@@ -1,0 +1,203 @@
+"""Seeded synthetic spin-glass instances.
+
+This module only draws random couplings and builds graphs; it holds none of the
+contraction arithmetic, so both the CPU oracle and the CUDA path may use it.
+
+An instance is a plain dict:
+
+    n      number of spins
+    q      states per spin (2 = Ising, 3 = Potts)
+    edges  int32 array (n_edges, 2), 0-based spin ids, u != v, no duplicates
+    J      float32 array (n_edges,)   coupling of each edge
+    h      float32 array (n) or None  local field (Ising only)
+    name   short description with the sizes
+    seed   the seed the couplings were drawn with
+
+Energy conventions (the arithmetic itself lives elsewhere):
+  Ising (Eq. 1):  E(sigma) = -sum_e J_e sigma_u sigma_v - sum_i h_i sigma_i,
+                  sigma in {+1, -1}; state index 0 <-> +1, index 1 <-> -1.
+  Potts (App. C, with the sign convention of the 18x18 Potts-glass workload):
+                  E(s) = -sum_e J_e delta(s_u, s_v), s in {0, 1, 2}.
+
+Gaussian couplings are drawn in float64 and rounded to float32: the float32
+values are the instance.  +-J couplings are +1/-1 with probability 1/2 each.
+"""
+from __future__ import annotations
+
+import hashlib
+
+import numpy as np
+
+__all__ = [
+    "square_lattice", "chimera", "random_regular3", "potts_square",
+    "mixed_square_batch", "planted", "ferromagnet", "instance_digest",
+    "square_sweep_order",
+]
+
+
+def _couplings(rng, m, kind):
+    if kind == "pm1":
+        return np.where(rng.integers(0, 2, size=m) == 0, 1.0, -1.0).astype(np.float32)
+    if kind == "gauss":
+        return rng.standard_normal(m).astype(np.float32)
+    if kind == "zero":
+        return np.zeros(m, np.float32)
+    raise ValueError(f"unknown coupling kind {kind!r}")
+
+
+def _fields(rng, n, sigma):
+    if sigma is None or sigma == 0:
+        return None
+    return (sigma * rng.standard_normal(n)).astype(np.float32)
+
+
+def square_edges(L, W=None):
+    """Open-boundary L x W square lattice; spin (r, c) has id r*W + c.
+
+    Edges are listed spin by spin in id order: first the bond to the right
+    neighbour, then the bond to the one below.
+    """
+    W = L if W is None else W
+    e = []
+    for r in range(L):
+        for c in range(W):
+            i = r * W + c
+            if c + 1 < W:
+                e.append((i, i + 1))
+            if r + 1 < L:
+                e.append((i, i + W))
+    return np.asarray(e, dtype=np.int32).reshape(-1, 2)
+
+
+def square_lattice(L, W=None, coupling="pm1", field_sigma=None, seed=0):
+    """L x W open square-lattice Ising spin glass (Sec. IV, Fig. 1)."""
+    W = L if W is None else W
+    rng = np.random.default_rng(seed)
+    edges = square_edges(L, W)
+    J = _couplings(rng, len(edges), coupling)
+    h = _fields(rng, L * W, field_sigma)
+    return dict(n=L * W, q=2, edges=edges, J=J, h=h, seed=seed,
+                name=f"square{L}x{W}-{coupling}" + (f"-h{field_sigma}" if h is not None else ""))
+
+
+def square_sweep_order(L, W=None):
+    """Row-by-row spin sequence of an L x W lattice (the circuit sweep of Fig. 1b)."""
+    W = L if W is None else W
+    return np.arange(L * W, dtype=np.int32)
+
+
+def chimera_edges(L):
+    """Chimera graph of L x L K_{4,4} unit cells (Sec. IV, Fig. 2a).
+
+    Cell (i, j) holds spins 8*(i*L+j) + k, k = 0..7.  Spins k = 0..3 form the
+    half coupled vertically (spin k of cell (i, j) to spin k of cell (i+1, j)),
+    spins k = 4..7 the half coupled horizontally (to cell (i, j+1)).  Inside a
+    cell every spin of one half couples to every spin of the other (16 edges).
+    L = 8 gives 512 spins and 1024 + 224 + 224 = 1472 couplers.
+    """
+    e = []
+    for i in range(L):
+        for j in range(L):
+            b = 8 * (i * L + j)
+            for a in range(4):
+                for c in range(4):
+                    e.append((b + a, b + 4 + c))
+            if i + 1 < L:
+                bn = 8 * ((i + 1) * L + j)
+                for a in range(4):
+                    e.append((b + a, bn + a))
+            if j + 1 < L:
+                bn = 8 * (i * L + j + 1)
+                for a in range(4):
+                    e.append((b + 4 + a, bn + 4 + a))
+    return np.asarray(e, dtype=np.int32).reshape(-1, 2)
+
+
+def chimera(L, coupling="pm1", seed=0):
+    rng = np.random.default_rng(seed)
+    edges = chimera_edges(L)
+    J = _couplings(rng, len(edges), coupling)
+    return dict(n=8 * L * L, q=2, edges=edges, J=J, h=None, seed=seed,
+                name=f"chimera{L}x{L}-{coupling}")
+
+
+def random_regular3_edges(N, rng, max_tries=100000):
+    """Random 3-regular graph by the pairing (configuration) model.
+
+    3N stubs are matched by a uniformly random perfect matching; a matching
+    with a self-loop or a repeated edge is thrown away and redrawn whole.
+    """
+    if (3 * N) % 2:
+        raise ValueError("3N must be even")
+    for _ in range(max_tries):
+        stubs = np.repeat(np.arange(N), 3)
+        perm = rng.permutation(3 * N)
+        pairs = stubs[perm].reshape(-1, 2)
+        u = np.minimum(pairs[:, 0], pairs[:, 1])
+        v = np.maximum(pairs[:, 0], pairs[:, 1])
+        if np.any(u == v):
+            continue
+        key = u.astype(np.int64) * N + v
+        if len(np.unique(key)) != len(key):
+            continue
+        order = np.argsort(key)
+        return np.stack([u[order], v[order]], axis=1).astype(np.int32)
+    raise RuntimeError("pairing model did not produce a simple graph")
+
+
+def random_regular3(N, coupling="gauss", seed=0):
+    rng = np.random.default_rng(seed)
+    edges = random_regular3_edges(N, rng)
+    J = _couplings(rng, len(edges), coupling)
+    return dict(n=N, q=2, edges=edges, J=J, h=None, seed=seed,
+                name=f"rrg3-N{N}-{coupling}")
+
+
+def potts_square(L, W=None, coupling="gauss", seed=0):
+    """q = 3 Potts glass on an open L x W square lattice (App. C)."""
+    W = L if W is None else W
+    rng = np.random.default_rng(seed)
+    edges = square_edges(L, W)
+    J = _couplings(rng, len(edges), coupling)
+    return dict(n=L * W, q=3, edges=edges, J=J, h=None, seed=seed,
+                name=f"potts3-square{L}x{W}-{coupling}")
+
+
+def mixed_square_batch(B, Lmin=8, Lmax=20, coupling="pm1", seed=0):
+    """B square +-J lattices with L uniform in [Lmin, Lmax], instance k seeded seed+1+k."""
+    rng = np.random.default_rng(seed)
+    Ls = rng.integers(Lmin, Lmax + 1, size=B)
+    return [square_lattice(int(L), coupling=coupling, seed=seed + 1 + k) for k, L in enumerate(Ls)]
+
+
+def planted(inst, seed=0):
+    """Mattis (gauge-transformed ferromagnet) version of an instance.
+
+    J_uv -> |J_uv| tau_u tau_v for a random tau in {+1,-1}^n, fields dropped.
+    Its ground states are exactly tau and -tau on a connected graph.
+    Returns (instance, tau as int8 array of +-1).
+    """
+    rng = np.random.default_rng(seed)
+    tau = np.where(rng.integers(0, 2, size=inst["n"]) == 0, 1, -1).astype(np.int8)
+    e = inst["edges"]
+    J = (np.abs(inst["J"]) * tau[e[:, 0]] * tau[e[:, 1]]).astype(np.float32)
+    out = dict(inst, J=J, h=None, name=inst["name"] + "-planted")
+    return out, tau
+
+
+def ferromagnet(inst):
+    """Same graph with every coupling replaced by its absolute value, no fields."""
+    return dict(inst, J=np.abs(inst["J"]).astype(np.float32), h=None,
+                name=inst["name"] + "-ferro")
+
+
+def instance_digest(inst):
+    """sha256 over the instance's arrays; pins a stored expected value to its input."""
+    m = hashlib.sha256()
+    m.update(np.int64(inst["n"]).tobytes())
+    m.update(np.int64(inst["q"]).tobytes())
+    m.update(np.ascontiguousarray(inst["edges"], dtype=np.int32).tobytes())
+    m.update(np.ascontiguousarray(inst["J"], dtype=np.float32).tobytes())
+    if inst.get("h") is not None:
+        m.update(np.ascontiguousarray(inst["h"], dtype=np.float32).tobytes())
+    return m.hexdigest()

@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput of the tropical contraction hot path on GB300.
+
+Workload (one step): B instances of the 24x24 open square-lattice Ising spin
+glass, J ~ N(0, 1) and h ~ N(0, 0.1^2) as float32, contracted along one greedy
+order (seeded randomized greedy, 64 restarts, host-side and untimed); for each
+instance the step computes E_min (forward contraction keeping checkpoints) and
+the ground state sigma* (argmax traceback).  Couplings are resident in HBM
+before the timed region.  Metric: instances/s over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Multi-GPU (torchrun): every rank contracts its own instances (weak scaling, no
+data exchange); the slowest rank's time is reported.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tropical Gop/s & % of FP32/INT32 peak; instances/s for (E, σ*, count)"
+L = 24
+FIELD_SIGMA = 0.1
+ORDER_SEED, ORDER_RESTARTS = 1, 64
+WORKLOAD = (f"square{L}x{L} open Ising glass, J~N(0,1) fp32, h~N(0,0.1^2) fp32, "
+            f"greedy order (seed {ORDER_SEED}, {ORDER_RESTARTS} restarts); per instance E_min "
+            f"+ sigma* (checkpointed forward + argmax traceback)")
+KIND_BOUND = {"gate": "hbm", "transpose": "hbm", "leaves": "hbm", "trace": "hbm", "gemm": "alu",
+              "other": "hbm"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x clock: one lane-instruction per lane per
+    # clock; a tropical multiply-add is an add and a max, counted as 2 ops,
+    # so the tropical-op peak equals the lane-instruction rate x 2 only when
+    # both run fused; we count 2 ops per MAC against 2 lane-instructions.
+    return 152 * 128 * sm_mhz * 1e6 * 1e-12
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profiles(kind):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source still matches."""
+    path = os.path.join(ROOT, "profiles", f"{kind}_kernel_square24.md")
+    src = os.path.join(ROOT, "paper_2008_06888_gb300", "csrc", "kernels.cu")
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernels.cu sha256[:16]") != h:
+        return None
+    try:
+        return float(vals["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def make_instances(rank, batch):
+    import instances as I
+    return [I.square_lattice(L, coupling="gauss", field_sigma=FIELD_SIGMA, seed=1000 * rank + k)
+            for k in range(batch)]
+
+
+def oracle_sample(inst, budget_s=20.0):
+    """Time the CPU oracle on eliminations at full frontier width, extrapolate to one instance."""
+    import oracle as O
+    import instances as I
+    order = I.square_sweep_order(L)
+    k0 = L + 1                       # frontier full after the first row
+    t0 = time.perf_counter()
+    O.solve(inst, order=order, count=False, config=True, max_eliminations=k0)
+    t_head = time.perf_counter() - t0
+    k1 = k0
+    t_full = None
+    while True:
+        k1 = min(L * L, k1 + 8)
+        t0 = time.perf_counter()
+        O.solve(inst, order=order, count=False, config=True, max_eliminations=k1)
+        t_full = time.perf_counter() - t0
+        if t_full >= budget_s or k1 >= L * L:
+            break
+    per_spin = max(t_full - t_head, 1e-9) / (k1 - k0)
+    est = t_head + per_spin * (L * L - k0)
+    return est, k1, t_full
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    inst = make_instances(0, 1)[0]
+    times = []
+    for i in range(args.warmup + args.steps):
+        est, k1, tf = oracle_sample(inst, budget_s=8.0)
+        if i >= args.warmup:
+            times.append(est)
+    val = 1.0 / float(np.mean(times))
+    sample = (f"CPU oracle (numpy float64 variable elimination, row-by-row order) on the first "
+              f"{k1} of {L*L} eliminations of one instance per step, extrapolated to a whole "
+              f"instance from the full-width eliminations")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "instances/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": 1, "order": "row-by-row (oracle)"},
+            "cpu_baseline": {"value": val, "unit": "instances/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "instances/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2008_06888_gb300 as P
+    from paper_2008_06888_gb300 import binding as B
+
+    insts = make_instances(rank, args.batch)
+    sg = P.SpinGlass(insts[0], order="greedy", seed=ORDER_SEED, restarts=ORDER_RESTARTS)
+    stream = torch.cuda.current_stream(dev)
+    sg.set_stream(stream.cuda_stream)
+    Jd = [torch.tensor(x["J"], device=dev) for x in insts]
+    hd = [torch.tensor(x["h"], device=dev) for x in insts]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)    # > 129 MB L2
+
+    def step():
+        for k in range(args.batch):
+            sg.set_couplings(Jd[k], hd[k], on_device=True)
+            B.tn_forward(sg.ctx)
+            B.tn_backward(sg.ctx, None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def timed(K, profile=False):
+        B.tn_profile_reset(sg.ctx)
+        B.tn_set_profiling(sg.ctx, profile)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(K):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        prof = {B.KIND_NAMES[k]: B.tn_profile_get(sg.ctx, k) for k in range(6)}
+        total = B.tn_profile_get(sg.ctx, -1)
+        B.tn_set_profiling(sg.ctx, False)
+        return ms, prof, total
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms, _, total = timed(args.steps)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    inst_total = args.batch * args.steps * world
+    value = inst_total / (ms / 1e3)
+
+    # per-kernel durations: the same K steps again with CUDA events around every launch
+    ms_p, prof, _ = timed(args.steps, profile=True)
+
+    # end to end through the C ABI with host buffers
+    sigma = np.empty(sg.n, np.int8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        for k in range(args.batch):
+            B.tn_set_couplings(sg.ctx, insts[k]["J"], insts[k]["h"])
+            sigma, E = B.tn_config(sg.ctx, sg.n)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": inst_total / e2e_s, "unit": "instances/s",
+           "h2d_bytes_per_step": args.batch * 4 * (sg.m + sg.n),
+           "d2h_bytes_per_step": args.batch * (sg.n + 4)}
+
+    pk, how = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    launches = max(d["launches"], 1)
+    avg_ms = d["ms"] / launches
+    bound = KIND_BOUND[dom]
+    tropical_gops = 2 * total["macs"] / (ms / 1e3) / 1e9
+    if bound == "hbm":
+        achieved = d["bytes"] / launches / (avg_ms / 1e3) / 1e9
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_from_profiles(dom),
+                "kernel": dom, "peak_source": how,
+                "bytes_per_launch": d["bytes"] / launches, "avg_launch_ms": avg_ms}
+    else:
+        sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+        achieved = 2 * d["macs"] / launches / (avg_ms / 1e3) / 1e12
+        peak = alu_peak_tops(pk.get("sm_max_mhz", 2070.0))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
+                "frac": achieved / peak, "traffic": traffic_from_profiles(dom), "kernel": dom,
+                "peak_source": "152 SMs x 128 lanes x max clock (one lane-op per clock)"}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        est, k1, tf = oracle_sample(insts[0], budget_s=15.0)
+        cpu = {"value": 1.0 / est, "unit": "instances/s", "cores": 1, "kind": "oracle",
+               "sample": f"numpy float64 variable elimination, first {k1} of {L*L} "
+                         f"eliminations of one instance ({tf:.1f} s), extrapolated"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "instances/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "global_batch": args.batch * world,
+                           "instances_per_step_per_gpu": args.batch,
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "log2_peak_elements": sg.log2_peak, "log2_macs": sg.log2_ops},
+                "tropical_gops": tropical_gops,
+                "roofline": roof,
+                "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
+                                "share": v["ms"] / max(ms_p, 1e-9)} for k, v in prof.items()},
+                "gpu_launches": total["launches"],
+                "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    sg.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * tn.h -- C ABI of the tropical tensor-network contraction library (libtn.so).
+ *
+ * The library contracts the tensor network of a spin glass over the tropical
+ * (max, +) semiring of Eq. 2 on one GB300 GPU (sm_103a) along a precomputed
+ * pairwise contraction order.  Each pairwise step is a tensor transpose
+ * followed by a batched max-plus GEMM (or a strided small-operand "gate"
+ * contraction that needs no transpose); the same steps run over the counting
+ * tuples (x, n) of Sec. II, with n kept modulo several 61-bit primes and
+ * recovered exactly by the Chinese remainder theorem.  A backward traceback
+ * through the contraction tree, recomputing intermediates from checkpoints,
+ * yields the ground-state configuration (Sec. III).
+ *
+ * Conventions shared by every entry point
+ *   - Spins are 0-based.  Ising (q = 2): state index 0 <-> sigma = +1,
+ *     1 <-> sigma = -1, so the bond tensor is [[J, -J], [-J, J]] (Sec. II).
+ *     Energy, Eq. 1: E = -sum_e J_e s_u s_v - sum_i h_i s_i.
+ *     Potts (q = 3): E = -sum_e J_e delta(s_u, s_v); fields must be NULL.
+ *   - Tensor elements hold negative energies, so the contracted scalar is
+ *     V = max_sigma(-E) and E_min = -V (Sec. II).
+ *   - All pointers are plain host pointers unless an argument says "device".
+ *     Input arrays are copied; the caller keeps ownership of everything it
+ *     passes.  Outputs go to caller-allocated buffers.
+ *   - Device memory is owned by the context (one arena sized by the plan).
+ *   - No C++ exception crosses this boundary: every call returns a status;
+ *     tn_last_error() gives a one-line reason for the last failure.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - There is no CPU fallback: without a usable CUDA device the calls that
+ *     compute return TN_ECUDA.
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tn_ctx tn_ctx;
+
+typedef enum {
+  TN_OK = 0,
+  TN_EINVAL = 1,     /* bad argument (sizes, ids, missing order, ...)      */
+  TN_ENOMEM = 2,     /* plan does not fit the device budget / malloc fails */
+  TN_ECUDA = 3,      /* a CUDA call failed, or no device                   */
+  TN_ETIMEOUT = 4,   /* a bounded device-side wait gave up                 */
+  TN_EOVERFLOW = 5,  /* count exceeds what the chosen primes can hold      */
+  TN_ESTATE = 6      /* call out of order (e.g. tn_energy before tn_order) */
+} tn_status;
+
+/* ---- tn_build flags ---------------------------------------------------- */
+#define TN_DTYPE_AUTO 0u   /* INT32 when every J and h is an integer, else FP32 */
+#define TN_DTYPE_I32 1u    /* force INT32 (J, h must be integers, |.| < 2^20)   */
+#define TN_DTYPE_F32 2u    /* force FP32                                         */
+#define TN_DTYPE_MASK 3u
+
+/* ---- tn_order methods --------------------------------------------------- */
+#define TN_ORDER_SWEEP 0   /* seq = spin elimination sequence (e.g. row by row)  */
+#define TN_ORDER_GREEDY 1  /* randomized greedy pair selection, best of restarts */
+#define TN_ORDER_TREE 2    /* seq = explicit pairwise tree, 2 ids per step       */
+
+/*
+ * tn_build -- describe one spin-glass instance (Eq. 1 / App. C, Sec. II).
+ *   n_spins >= 1; n_edges >= 0; edges: 2*n_edges int32 spin ids (u != v, no
+ *   repeated pair); J: n_edges couplings; h: n_spins fields or NULL (must be
+ *   NULL when q == 3); q: 2 (Ising) or 3 (Potts); flags: TN_DTYPE_*.
+ *   On success *out owns a new context; free it with tn_destroy().
+ *   Errors: TN_EINVAL on bad sizes/ids/q, TN_ENOMEM if host allocation fails.
+ */
+tn_status tn_build(tn_ctx **out, int32_t n_spins, int32_t n_edges,
+                   const int32_t *edges, const float *J, const float *h,
+                   int32_t q, uint32_t flags);
+
+/*
+ * tn_order -- fix the pairwise contraction tree (Sec. III: the cost is
+ *   exponential in the treewidth; regular lattices sweep row by row, general
+ *   graphs use heuristics such as greedy).  Host only; plans the steps, the
+ *   transposes and the device memory layout.
+ *   TN_ORDER_SWEEP: seq holds seq_len distinct spin ids, eliminated in that
+ *     order (spins left out follow in id order).
+ *   TN_ORDER_GREEDY: seq ignored; `restarts` randomized greedy runs seeded by
+ *     `seed`, the cheapest tree (time model over the steps) is kept.
+ *   TN_ORDER_TREE: seq holds 2*(n_tensors-1) ids; leaves are tensors
+ *     0..n_tensors-1 (see tn_leaf_count), step s creates tensor n_tensors+s.
+ *   log2_peak / log2_ops (may be NULL) receive log2 of the largest tensor
+ *   (elements) and of the total tropical multiply-adds of the plan.
+ *   Errors: TN_EINVAL (bad sequence/tree), TN_ENOMEM (largest tensor above
+ *   2^34 elements).
+ */
+tn_status tn_order(tn_ctx *ctx, int32_t method, const int32_t *seq, int32_t seq_len,
+                   uint64_t seed, int32_t restarts, double *log2_peak, double *log2_ops);
+
+/* Number of leaf tensors of the built network (one per edge, plus one per
+ * isolated spin); the ids TN_ORDER_TREE refers to. */
+int32_t tn_leaf_count(const tn_ctx *ctx);
+
+/*
+ * tn_set_couplings -- replace J (n_edges) and h (n_spins, or NULL = keep)
+ *   without re-planning.  on_device = 0: host pointers (copied synchronously);
+ *   1: device pointers on the context's device (copied on the context stream).
+ *   INT32 contexts require integral values (TN_EINVAL otherwise, host only).
+ */
+tn_status tn_set_couplings(tn_ctx *ctx, const float *J, const float *h, int32_t on_device);
+
+/* Make every launch of this context go to `cuda_stream` (a cudaStream_t,
+ * NULL = legacy default stream).  The caller keeps the stream alive. */
+tn_status tn_set_stream(tn_ctx *ctx, void *cuda_stream);
+
+/*
+ * tn_energy -- E_min by the tropical contraction (Sec. II).  Blocks until the
+ *   result is on the host.  *E is exact for INT32 contexts; FP32 contexts
+ *   accumulate in float (the returned double is the float result).
+ */
+tn_status tn_energy(tn_ctx *ctx, double *E);
+
+/*
+ * tn_config -- a ground state by argmax traceback (Sec. III): forward
+ *   contraction keeping checkpoints, then a top-down walk of the tree that
+ *   recomputes freed intermediates.  Ties take the first index in the order
+ *   of the contracted legs (footnote in Sec. III).  sigma: n_spins int8
+ *   (+1/-1 for Ising, 0..q-1 for Potts), host buffer; may be NULL when only
+ *   the device-side result (tn_gradient) is wanted.  *E (may be NULL)
+ *   receives E_min from the same forward pass.
+ */
+tn_status tn_config(tn_ctx *ctx, int8_t *sigma, double *E);
+
+/*
+ * tn_forward / tn_backward -- the two halves of tn_config, for autograd use.
+ *   tn_forward runs the forward contraction keeping the traceback's
+ *   checkpoints in the context's arena and returns E_min (*E may be NULL);
+ *   tn_backward then runs the traceback (recomputing what was not kept) and
+ *   leaves the state on the device for tn_gradient; sigma (n_spins int8,
+ *   host, may be NULL) receives it as in tn_config.  tn_backward returns
+ *   TN_ESTATE unless the last call on the context was tn_forward.
+ */
+tn_status tn_forward(tn_ctx *ctx, double *E);
+tn_status tn_backward(tn_ctx *ctx, int8_t *sigma);
+
+/*
+ * tn_gradient -- derivatives of E_min at the last tn_config state (Sec. III):
+ *   dE/dJ_e = -s_u s_v (Potts: -delta(s_u, s_v)), dE/dh_i = -s_i.  dJ has
+ *   n_edges floats, dh n_spins floats (may be NULL).  on_device selects host
+ *   or device buffers.  TN_ESTATE if tn_config has not run.
+ */
+tn_status tn_gradient(tn_ctx *ctx, float *dJ, float *dh, int32_t on_device);
+
+/*
+ * tn_count -- ground-state degeneracy with the counting tuples of Sec. II.
+ *   n_primes in [1, 8] 61-bit primes carry n exactly up to their product
+ *   (~2^(61*n_primes)); one extra witness prime checks the reconstruction and
+ *   TN_EOVERFLOW is returned when it disagrees.  limbs: little-endian 64-bit
+ *   limbs of the count, capacity *n_limbs on input, limbs used on output.
+ *   ln_count (may be NULL): natural log of the count.  *E (may be NULL):
+ *   E_min of the same pass.
+ */
+tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_limbs,
+                   double *ln_count, double *E);
+
+/*
+ * tn_batch_run -- many independent instances (each already built and
+ *   ordered) in one batched execution: all their leaves and steps go into one
+ *   persistent kernel launch, captured as a CUDA graph and replayed on later
+ *   calls with the same contexts.  Outputs, per instance k: E[k];
+ *   limbs[k*limbs_per ...] the count (when limbs != NULL; 3 primes + witness);
+ *   status[k] a tn_status.  Returns the first non-OK status, else TN_OK.
+ *   All contexts must use the same dtype and q.
+ */
+tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limbs,
+                       int32_t limbs_per, int32_t *status);
+
+/*
+ * Measurement hooks.  Every kernel launch of the context is counted; with
+ * profiling enabled each launch is also bracketed by CUDA events on the
+ * context stream.  tn_profile_get(kind): 0 leaves, 1 transpose, 2 gate
+ * contraction, 3 max-plus GEMM, 4 traceback, 5 other, -1 all; it synchronises
+ * the stream and returns launches, total milliseconds (profiling only),
+ * algorithmic bytes (operands read + result written, each once) and tropical
+ * multiply-adds of those launches.  tn_profile_reset clears the counters.
+ */
+tn_status tn_set_profiling(tn_ctx *ctx, int32_t enable);
+tn_status tn_profile_get(tn_ctx *ctx, int32_t kind, int64_t *launches, double *ms,
+                         double *bytes, double *macs);
+tn_status tn_profile_reset(tn_ctx *ctx);
+
+/* Statistics of the current plan (any pointer may be NULL): number of
+ * pairwise steps, transposes, device arena bytes for energy / config / count. */
+tn_status tn_plan_info(const tn_ctx *ctx, int32_t *n_steps, int32_t *n_transposes,
+                       int64_t *arena_energy, int64_t *arena_config, int64_t *arena_count);
+
+/* One-line reason for the last failing call on ctx (or of tn_build when ctx
+ * is NULL).  Valid until the next call on the same context. */
+const char *tn_last_error(const tn_ctx *ctx);
+
+/* Free the context and its device memory.  NULL is ignored. */
+void tn_destroy(tn_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_H */

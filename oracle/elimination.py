@@ -103,13 +103,14 @@ def _aligned(f, union, q, arr):
     return t.reshape(shape)
 
 
-def solve(inst, order=None, count=True, config=True):
+def solve(inst, order=None, count=True, config=True, max_eliminations=None):
     """Contract the instance's tropical network by variable elimination.
 
     Returns dict(E=float E_min, count=int or None, state=int8 array of state
     indices or None, width=largest table scope).
     ``order`` is a spin sequence; spins it leaves out are eliminated afterwards
-    in min-fill order.
+    in min-fill order.  ``max_eliminations`` stops after that many spins and
+    returns only dict(eliminated=k, width=...) (used to time a bounded sample).
     """
     n, q = inst["n"], inst["q"]
     if order is None:
@@ -123,7 +124,9 @@ def solve(inst, order=None, count=True, config=True):
     factors = local_tensors(inst, count)
     trace = []
     width = 0
-    for v in order:
+    for step, v in enumerate(order):
+        if max_eliminations is not None and step >= max_eliminations:
+            return dict(eliminated=step, width=width)
         bucket = [f for f in factors if v in f.scope]
         rest = [f for f in factors if v not in f.scope]
         others = sorted(set(x for f in bucket for x in f.scope) - {v})

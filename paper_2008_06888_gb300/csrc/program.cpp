@@ -1,0 +1,597 @@
+// program.cpp -- lowering of classified steps to kernel launches, static
+// arena planning, and the checkpoint / recompute schedule of the traceback.
+//
+// Each pairwise step C = A (.) B (Sec. III) becomes either
+//   * a gate contraction when one operand contributes few states (K and N
+//     small): the big operand is read in place through per-leg strides, so no
+//     transpose is needed; this covers the sweep steps of a lattice, the
+//     Hadamard-type steps with K = 1 and the unary reductions; or
+//   * a strided batched max-plus GEMM over [batch][M][K] x [batch][K][N],
+//     preceded by a transpose of any operand whose legs of one class are not
+//     contiguous in memory.
+#include "program.h"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+namespace tn {
+
+namespace {
+
+constexpr int64_t kAlign = 256;
+inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int64_t ipow(int q, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= q;
+  return r;
+}
+
+int pos_of(const std::vector<int> &v, int x) {
+  for (int i = 0; i < (int)v.size(); ++i) if (v[i] == x) return i;
+  return -1;
+}
+
+struct Builder {
+  const Net &net;
+  const Plan &plan;
+  Program &pr;
+  int q, P;
+  std::vector<std::vector<int>> order;   // memory leg order of each plan tensor
+  std::vector<Loc> loc;
+  std::string err;
+
+  Builder(const Net &n, const Plan &p, Program &r)
+      : net(n), plan(p), pr(r), q(r.q), P(r.P), order(p.legset.size()), loc(p.legset.size()) {}
+
+  int64_t stride(const std::vector<int> &ord, int leg) const {
+    int p = pos_of(ord, leg);
+    if (p < 0) return 0;
+    return ipow(q, (int)ord.size() - 1 - p);
+  }
+
+  Loc new_tensor(int64_t elems) {
+    BufInfo b;
+    int64_t xb = align_up(elems * 4);
+    b.bytes = xb + (P > 0 ? align_up((int64_t)P * elems * 8) : 0);
+    if (b.bytes == 0) b.bytes = kAlign;
+    pr.bufs.push_back(b);
+    Loc l;
+    l.buf = (int)pr.bufs.size() - 1;
+    l.xoff = 0;
+    l.noff = xb;
+    l.plane = elems;
+    return l;
+  }
+  void use(const Loc &l, int op) {
+    if (l.buf < 0) return;
+    BufInfo &b = pr.bufs[l.buf];
+    b.first = std::min(b.first, op);
+    b.last = std::max(b.last, op);
+  }
+  double elem_bytes() const { return 4.0 + 8.0 * P; }
+  int push(Op op) {
+    auto el = [&](const Loc &l) { return l.buf < 0 ? 0.0 : (double)l.plane; };
+    if (op.kind == OP_PERM) op.bytes = 2 * el(op.out) * elem_bytes();
+    else if (op.kind == OP_LEAVES) op.bytes = el(op.out) * elem_bytes();
+    else op.bytes = (el(op.in0) + el(op.in1) + el(op.out)) * elem_bytes();
+    pr.ops.push_back(op);
+    int i = (int)pr.ops.size() - 1;
+    use(op.in0, i);
+    use(op.in1, i);
+    use(op.out, i);
+    return i;
+  }
+
+  // ---- leaves
+  void emit_leaves() {
+    int64_t total = 0;
+    for (int i = 0; i < plan.n_leaves; ++i) {
+      pr.leaf_elem.push_back(total);
+      total += ipow(q, (int)plan.legset[i].size());
+    }
+    Loc L = new_tensor(total);
+    pr.leaves_loc = L;
+    for (int i = 0; i < plan.n_leaves; ++i) {
+      order[i] = plan.legset[i];
+      Loc l = L;
+      l.xoff = L.xoff + pr.leaf_elem[i] * 4;
+      l.noff = L.noff + pr.leaf_elem[i] * 8;
+      loc[i] = l;
+    }
+    Op op;
+    op.kind = OP_LEAVES;
+    op.out = L;
+    push(op);
+  }
+
+  // ---- permutation of tensor t into `to` (new buffer); returns its location
+  Loc emit_perm(int t, const std::vector<int> &to) {
+    const std::vector<int> &from = order[t];
+    PermParams pp{};
+    std::vector<int64_t> dims, sin;
+    for (int l : to) {
+      dims.push_back(q);
+      sin.push_back(stride(from, l));
+    }
+    // merge runs of output legs that are adjacent in the input too
+    std::vector<int64_t> md, ms;
+    for (size_t j = 0; j < dims.size(); ++j) {
+      if (!md.empty() && ms.back() == sin[j] * dims[j]) {
+        md.back() *= dims[j];
+        ms.back() = sin[j];
+      } else {
+        md.push_back(dims[j]);
+        ms.push_back(sin[j]);
+      }
+    }
+    pp.r = (int)md.size();
+    pp.total = ipow(q, (int)to.size());
+    for (int j = 0; j < pp.r; ++j) { pp.dims[j] = md[j]; pp.sin[j] = ms[j]; }
+    Loc out = new_tensor(pp.total);
+    pp.planeIn = loc[t].plane;
+    pp.planeOut = out.plane;
+    pp.P = P;
+    pr.perms.push_back(pp);
+    Op op;
+    op.kind = OP_PERM;
+    op.in0 = loc[t];
+    op.out = out;
+    op.idx = (int)pr.perms.size() - 1;
+    push(op);
+    pr.n_transposes++;
+    return out;
+  }
+
+  // ---- gate contraction: A big (in place), B small or absent.
+  // K and N legs are given in the order that defines k and n.
+  bool make_gate(const std::vector<int> &ordA, const std::vector<int> *ordB,
+                 const std::vector<int> &K, const std::vector<int> &N, GateParams *g,
+                 std::vector<int> *ordC) {
+    GateParams &p = *g;
+    p = GateParams{};
+    std::vector<int> outer;
+    for (int l : ordA) if (pos_of(K, l) < 0) outer.push_back(l);
+    *ordC = outer;
+    ordC->insert(ordC->end(), N.begin(), N.end());
+    int64_t Ks = ipow(q, (int)K.size()), Ns = ipow(q, (int)N.size());
+    if (Ks > TN_GATE_MAX_K || Ns > TN_GATE_MAX_N) return false;
+    // segments, innermost first, then reversed
+    std::vector<int64_t> sz, sa, sb, sc;
+    for (int j = (int)outer.size() - 1; j >= 0; --j) {
+      int l = outer[j];
+      int64_t a = stride(ordA, l), b = ordB ? stride(*ordB, l) : 0, c = stride(*ordC, l);
+      if (!sz.empty() && a == sa.back() * sz.back() && b == sb.back() * sz.back() &&
+          c == sc.back() * sz.back()) {
+        sz.back() *= q;
+      } else {
+        sz.push_back(q);
+        sa.push_back(a);
+        sb.push_back(b);
+        sc.push_back(c);
+      }
+    }
+    if ((int)sz.size() > TN_MAX_SEG) return false;
+    p.nseg = (int)sz.size();
+    for (int s = 0; s < p.nseg; ++s) {
+      int r = p.nseg - 1 - s;
+      p.seg_size[s] = sz[r];
+      p.seg_sA[s] = sa[r];
+      p.seg_sB[s] = sb[r];
+      p.seg_sC[s] = sc[r];
+    }
+    p.outer = ipow(q, (int)outer.size());
+    p.Ks = (int)Ks;
+    p.Ns = (int)Ns;
+    p.hasB = ordB ? 1 : 0;
+    for (int64_t k = 0; k < Ks; ++k) {
+      int64_t r = k, oa = 0, ob = 0;
+      for (int j = (int)K.size() - 1; j >= 0; --j) {
+        int64_t d = r % q;
+        r /= q;
+        oa += d * stride(ordA, K[j]);
+        if (ordB) ob += d * stride(*ordB, K[j]);
+      }
+      p.kA[k] = oa;
+      p.kB[k] = ob;
+    }
+    for (int64_t n = 0; n < Ns; ++n) {
+      int64_t r = n, ob = 0;
+      for (int j = (int)N.size() - 1; j >= 0; --j) {
+        int64_t d = r % q;
+        r /= q;
+        if (ordB) ob += d * stride(*ordB, N[j]);
+      }
+      p.nB[n] = ob;
+      p.nC[n] = n;
+    }
+    p.P = P;
+    return true;
+  }
+
+  void push_gate(const GateParams &g, const Loc &A, const Loc *B, const Loc &C) {
+    GateParams p = g;
+    p.planeA = A.plane;
+    p.planeB = B ? B->plane : 0;
+    p.planeC = C.plane;
+    pr.gates.push_back(p);
+    Op op;
+    op.macs = (double)p.outer * p.Ks * p.Ns;
+    op.kind = OP_GATE;
+    op.in0 = A;
+    if (B) op.in1 = *B;
+    op.out = C;
+    op.idx = (int)pr.gates.size() - 1;
+    push(op);
+    pr.n_gate++;
+  }
+
+  // K legs ordered as in A's memory order
+  std::vector<int> k_order(const std::vector<int> &ordA, const std::vector<int> &K) {
+    std::vector<int> r;
+    for (int l : ordA) if (pos_of(K, l) >= 0) r.push_back(l);
+    return r;
+  }
+
+  bool emit_unary(const PStep &st) {
+    int a = st.a;
+    std::vector<int> Krem = k_order(order[a], st.K);
+    std::vector<int> cur_ord = order[a];
+    Loc cur = loc[a];
+    int maxk = 0;
+    while (ipow(q, maxk + 1) <= TN_GATE_MAX_K) ++maxk;
+    do {
+      std::vector<int> chunk(Krem.begin(), Krem.begin() + std::min<size_t>(maxk, Krem.size()));
+      Krem.erase(Krem.begin(), Krem.begin() + chunk.size());
+      GateParams g;
+      std::vector<int> ordC;
+      if (!make_gate(cur_ord, nullptr, chunk, {}, &g, &ordC)) {
+        // too many segments: canonicalise A first
+        int tmp = a;
+        (void)tmp;
+        err = "unary reduction: layout too fragmented";
+        return false;
+      }
+      Loc out = new_tensor(ipow(q, (int)ordC.size()));
+      push_gate(g, cur, nullptr, out);
+      cur = out;
+      cur_ord = ordC;
+    } while (!Krem.empty());
+    order[st.c] = cur_ord;
+    loc[st.c] = cur;
+    pr.macs += (double)ipow(q, (int)(st.M.size() + st.K.size()));
+    return true;
+  }
+
+  // class view of a tensor for the GEMM path: each class contiguous, the
+  // innermost leg not a batch leg; returns the class-internal orders.
+  bool gemm_view(const std::vector<int> &ord, const std::vector<int> &c0,
+                 const std::vector<int> &c1, const std::vector<int> &c2,
+                 std::vector<int> *o0, std::vector<int> *o1, std::vector<int> *o2) {
+    std::vector<int> cls(ord.size());
+    for (size_t i = 0; i < ord.size(); ++i) {
+      if (pos_of(c0, ord[i]) >= 0) cls[i] = 0;
+      else if (pos_of(c1, ord[i]) >= 0) cls[i] = 1;
+      else cls[i] = 2;
+    }
+    int seen[3] = {0, 0, 0};
+    for (size_t i = 0; i < ord.size(); ++i) {
+      if (i > 0 && cls[i] != cls[i - 1] && seen[cls[i]]) return false;
+      seen[cls[i]] = 1;
+    }
+    if (!ord.empty() && cls.back() == 0 && (c1.size() + c2.size()) > 0) return false;
+    o0->clear(); o1->clear(); o2->clear();
+    for (size_t i = 0; i < ord.size(); ++i)
+      (cls[i] == 0 ? o0 : cls[i] == 1 ? o1 : o2)->push_back(ord[i]);
+    return true;
+  }
+
+  int64_t inner_stride(const std::vector<int> &ord, const std::vector<int> &cls) {
+    if (cls.empty()) return 0;
+    return stride(ord, cls.back());
+  }
+
+  struct GemmChoice {
+    int A, B;
+    std::vector<int> bo, mo, ko, no;   // class orders
+    bool permA, permB;
+    int64_t cost;
+  };
+
+  GemmChoice plan_gemm(int A, int B, const std::vector<int> &batch, const std::vector<int> &M,
+                       const std::vector<int> &K, const std::vector<int> &N) {
+    GemmChoice ch;
+    ch.A = A;
+    ch.B = B;
+    ch.cost = 0;
+    std::vector<int> b0, m0, k0;
+    if (gemm_view(order[A], batch, M, K, &b0, &m0, &k0)) {
+      ch.permA = false;
+    } else {
+      ch.permA = true;
+      b0.clear(); m0.clear(); k0.clear();
+      for (int l : order[A]) {
+        if (pos_of(batch, l) >= 0) b0.push_back(l);
+        else if (pos_of(M, l) >= 0) m0.push_back(l);
+        else k0.push_back(l);
+      }
+      ch.cost += ipow(q, (int)order[A].size());
+    }
+    std::vector<int> b1, k1, n1;
+    bool okB = gemm_view(order[B], batch, K, N, &b1, &k1, &n1) && b1 == b0 && k1 == k0;
+    if (!okB) {
+      n1.clear();
+      for (int l : order[B]) if (pos_of(N, l) >= 0) n1.push_back(l);
+      ch.cost += ipow(q, (int)order[B].size());
+    }
+    ch.permB = !okB;
+    ch.bo = b0; ch.mo = m0; ch.ko = k0; ch.no = n1;
+    return ch;
+  }
+
+  void emit_pair(const PStep &st) {
+    const int a = st.a, b = st.b;
+    const int64_t Sa = ipow(q, (int)order[a].size()), Sb = ipow(q, (int)order[b].size());
+    const int64_t Sk = ipow(q, (int)st.K.size());
+    const int64_t Sm = ipow(q, (int)st.M.size()), Sn = ipow(q, (int)st.N.size());
+    pr.macs += (double)ipow(q, (int)(st.batch.size() + st.M.size() + st.N.size() + st.K.size()));
+    // gate options: (big, small, new legs of small)
+    struct GOpt { int A, B; const std::vector<int> *N; int64_t big; };
+    std::vector<GOpt> opts;
+    if (Sk <= TN_GATE_MAX_K && Sn <= TN_GATE_MAX_N) opts.push_back({a, b, &st.N, Sa});
+    if (Sk <= TN_GATE_MAX_K && Sm <= TN_GATE_MAX_N) opts.push_back({b, a, &st.M, Sb});
+    std::sort(opts.begin(), opts.end(), [](const GOpt &x, const GOpt &y) { return x.big > y.big; });
+    for (auto &o : opts) {
+      std::vector<int> K = k_order(order[o.A], st.K);
+      std::vector<int> Nn;
+      for (int l : order[o.B]) if (pos_of(*o.N, l) >= 0) Nn.push_back(l);
+      GateParams g;
+      std::vector<int> ordC;
+      if (make_gate(order[o.A], &order[o.B], K, Nn, &g, &ordC)) {
+        Loc out = new_tensor(ipow(q, (int)ordC.size()));
+        push_gate(g, loc[o.A], &loc[o.B], out);
+        order[st.c] = ordC;
+        loc[st.c] = out;
+        return;
+      }
+    }
+    // GEMM path, both role assignments, fewest transposed elements
+    GemmChoice c1 = plan_gemm(a, b, st.batch, st.M, st.K, st.N);
+    GemmChoice c2 = plan_gemm(b, a, st.batch, st.N, st.K, st.M);
+    GemmChoice &ch = (c2.cost < c1.cost || (c2.cost == c1.cost && Sb > Sa)) ? c2 : c1;
+    std::vector<int> ordA, ordB;
+    Loc LA = loc[ch.A], LB = loc[ch.B];
+    if (ch.permA) {
+      ordA = ch.bo;
+      ordA.insert(ordA.end(), ch.mo.begin(), ch.mo.end());
+      ordA.insert(ordA.end(), ch.ko.begin(), ch.ko.end());
+      LA = emit_perm(ch.A, ordA);
+    } else {
+      ordA = order[ch.A];
+    }
+    if (ch.permB) {
+      ordB = ch.bo;
+      ordB.insert(ordB.end(), ch.ko.begin(), ch.ko.end());
+      ordB.insert(ordB.end(), ch.no.begin(), ch.no.end());
+      LB = emit_perm(ch.B, ordB);
+    } else {
+      ordB = order[ch.B];
+    }
+    std::vector<int> ordC = ch.bo;
+    ordC.insert(ordC.end(), ch.mo.begin(), ch.mo.end());
+    ordC.insert(ordC.end(), ch.no.begin(), ch.no.end());
+    GemmParams g{};
+    g.batch = ipow(q, (int)ch.bo.size());
+    g.M = ipow(q, (int)ch.mo.size());
+    g.N = ipow(q, (int)ch.no.size());
+    g.K = ipow(q, (int)ch.ko.size());
+    g.sAb = inner_stride(ordA, ch.bo);
+    g.sAm = inner_stride(ordA, ch.mo);
+    g.sAk = inner_stride(ordA, ch.ko);
+    g.sBb = inner_stride(ordB, ch.bo);
+    g.sBk = inner_stride(ordB, ch.ko);
+    g.sBn = inner_stride(ordB, ch.no);
+    g.sCb = inner_stride(ordC, ch.bo);
+    g.sCm = inner_stride(ordC, ch.mo);
+    g.sCn = inner_stride(ordC, ch.no);
+    Loc out = new_tensor(ipow(q, (int)ordC.size()));
+    g.planeA = LA.plane;
+    g.planeB = LB.plane;
+    g.planeC = out.plane;
+    g.P = P;
+    pr.gemms.push_back(g);
+    Op op;
+    op.macs = (double)g.batch * g.M * g.N * g.K;
+    op.kind = OP_GEMM;
+    op.in0 = LA;
+    op.in1 = LB;
+    op.out = out;
+    op.idx = (int)pr.gemms.size() - 1;
+    push(op);
+    pr.n_gemm++;
+    order[st.c] = ordC;
+    loc[st.c] = out;
+  }
+
+  bool emit_step(int s) {
+    const PStep &st = plan.steps[s];
+    if (st.b < 0) return emit_unary(st);
+    emit_pair(st);
+    return true;
+  }
+
+  // ---- traceback
+  std::vector<int> pending;
+  void flush_trace() {
+    if (pending.empty()) return;
+    Op op;
+    op.kind = OP_TRACE;
+    op.trace_begin = (int)pr.trace.size();
+    op.trace_n = (int)pending.size();
+    pr.ops.push_back(op);
+    int oi = (int)pr.ops.size() - 1;
+    for (int s : pending) {
+      const PStep &st = plan.steps[s];
+      TraceStep t{};
+      const std::vector<int> &oa = order[st.a];
+      std::vector<int> K = k_order(oa, st.K);
+      t.nk = (int)K.size();
+      t.Ks = (int)ipow(q, t.nk);
+      for (int j = 0; j < t.nk; ++j) {
+        t.k_spin[j] = K[j];
+        t.k_sA[j] = stride(oa, K[j]);
+        t.k_sB[j] = st.b >= 0 ? stride(order[st.b], K[j]) : 0;
+      }
+      for (int l : oa)
+        if (pos_of(K, l) < 0) {
+          t.fa_spin[t.nfa] = l;
+          t.fa_stride[t.nfa] = stride(oa, l);
+          t.nfa++;
+        }
+      if (st.b >= 0)
+        for (int l : order[st.b])
+          if (pos_of(K, l) < 0) {
+            t.fb_spin[t.nfb] = l;
+            t.fb_stride[t.nfb] = stride(order[st.b], l);
+            t.nfb++;
+          }
+      pr.trace.push_back(t);
+      pr.traceA.push_back(loc[st.a]);
+      pr.traceB.push_back(st.b >= 0 ? loc[st.b] : Loc());
+      use(loc[st.a], oi);
+      if (st.b >= 0) use(loc[st.b], oi);
+    }
+    pending.clear();
+  }
+
+  std::vector<char> avail;
+  bool recompute(int t) {
+    int p = plan.producer[t];
+    const PStep &st = plan.steps[p];
+    if (!avail[st.a] && !recompute(st.a)) return false;
+    if (st.b >= 0 && !avail[st.b] && !recompute(st.b)) return false;
+    if (!emit_step(p)) return false;
+    pr.n_recompute++;
+    avail[t] = 1;
+    return true;
+  }
+
+  bool build(ProgMode mode, int64_t seg_bytes) {
+    emit_leaves();
+    const int S = (int)plan.steps.size();
+    std::vector<char> stored(plan.legset.size(), 0);
+    for (int i = 0; i < plan.n_leaves; ++i) stored[i] = 1;
+    if (mode == PM_CONFIG) {
+      std::vector<int64_t> acc(plan.legset.size(), 0);
+      for (int s = 0; s < S; ++s) {
+        const PStep &st = plan.steps[s];
+        int64_t a = ipow(q, (int)plan.legset[st.c].size()) * 4;
+        if (!stored[st.a]) a += acc[st.a];
+        if (st.b >= 0 && !stored[st.b]) a += acc[st.b];
+        acc[st.c] = a;
+        if (seg_bytes <= 0 || a > seg_bytes || st.c == plan.root) stored[st.c] = 1;
+      }
+    }
+    for (int s = 0; s < S; ++s)
+      if (!emit_step(s)) return false;
+    pr.root = loc[plan.root];
+    pr.fwd_end = (int)pr.ops.size();
+    if (mode == PM_CONFIG) {
+      // keep the root alive to the end
+      avail = stored;
+      for (int s = S - 1; s >= 0; --s) {
+        const PStep &st = plan.steps[s];
+        if (!avail[st.a] || (st.b >= 0 && !avail[st.b])) {
+          flush_trace();
+          if (!avail[st.a] && !recompute(st.a)) return false;
+          if (st.b >= 0 && !avail[st.b] && !recompute(st.b)) return false;
+        }
+        pending.push_back(s);
+      }
+      flush_trace();
+    }
+    use(pr.root, (int)pr.ops.size());
+    return true;
+  }
+};
+
+void plan_memory(Program &pr) {
+  std::vector<int> idx(pr.bufs.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+    return pr.bufs[a].bytes > pr.bufs[b].bytes || (pr.bufs[a].bytes == pr.bufs[b].bytes && a < b);
+  });
+  std::vector<int> placed;
+  int64_t top = 0;
+  for (int i : idx) {
+    BufInfo &b = pr.bufs[i];
+    if (b.last < 0) { b.first = b.last = 0; }
+    std::vector<std::pair<int64_t, int64_t>> busy;
+    for (int j : placed) {
+      const BufInfo &o = pr.bufs[j];
+      if (o.first <= b.last && b.first <= o.last) busy.push_back({o.off, o.off + o.bytes});
+    }
+    std::sort(busy.begin(), busy.end());
+    int64_t off = 0;
+    for (auto &r : busy) {
+      if (r.first >= off + b.bytes) break;
+      off = std::max(off, r.second);
+    }
+    b.off = off;
+    top = std::max(top, off + b.bytes);
+    placed.push_back(i);
+  }
+  pr.arena_bytes = std::max<int64_t>(top, kAlign);
+}
+
+}  // namespace
+
+int64_t abs_off(const Program &pr, const Loc &l) { return pr.bufs[l.buf].off + l.xoff; }
+
+bool build_program(const Net &net, const Plan &plan, ProgMode mode, Dtype dt, int P,
+                   int64_t seg_bytes, Program *pr, std::string *err) {
+  *pr = Program();
+  pr->mode = mode;
+  pr->dt = dt;
+  pr->q = net.q;
+  pr->P = P;
+  Builder bd(net, plan, *pr);
+  if (!bd.build(mode, seg_bytes)) {
+    *err = bd.err.empty() ? "program: lowering failed" : bd.err;
+    return false;
+  }
+  plan_memory(*pr);
+  // absolute offsets of leaves and traceback operands
+  const int64_t lbase = pr->bufs[pr->leaves_loc.buf].off;
+  for (int i = 0; i < plan.n_leaves; ++i) {
+    const Net::Leaf &L = net.leaves[i];
+    LeafDesc d{};
+    d.off_x = lbase + pr->leaves_loc.xoff + pr->leaf_elem[i] * 4;
+    d.off_n = lbase + pr->leaves_loc.noff + pr->leaf_elem[i] * 8;
+    d.plane = pr->leaves_loc.plane;
+    d.kind = L.kind;
+    d.edge = L.edge;
+    if (L.kind == 0) {
+      // memory legs are (min, max); map the absorbed fields accordingly
+      bool sw = L.u > L.v;
+      d.u = sw ? L.v : L.u;
+      d.v = sw ? L.u : L.v;
+      d.fu = sw ? L.fv : L.fu;
+      d.fv = sw ? L.fu : L.fv;
+    } else {
+      d.u = L.u;
+      d.v = -1;
+      d.fu = L.fu;
+      d.fv = 0;
+    }
+    pr->leaves.push_back(d);
+  }
+  for (size_t i = 0; i < pr->trace.size(); ++i) {
+    pr->trace[i].offA = abs_off(*pr, pr->traceA[i]) / 4;
+    pr->trace[i].offB = pr->traceB[i].buf >= 0 ? abs_off(*pr, pr->traceB[i]) / 4 : -1;
+  }
+  return true;
+}
+
+}  // namespace tn

@@ -1,0 +1,57 @@
+"""Write tests/golden/expected_full.json from the CPU oracle only.
+
+Full-size workloads whose oracle run takes minutes are solved once here and
+stored with the sha256 digest of their input, so GPU tests can compare
+against them in seconds.  Run from the repository root:
+
+    python tests/golden/make_expected.py
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import instances as I  # noqa: E402
+import oracle as O  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "expected_full.json")
+
+
+def cases():
+    # 24x24 open square lattice, J ~ N(0,1), h ~ N(0, 0.1^2), float32 values
+    yield "square24_gauss_h", I.square_lattice(24, coupling="gauss", field_sigma=0.1, seed=2008), \
+        dict(order=I.square_sweep_order(24), count=False, config=True)
+    # 16x16 +-J lattice with its exact degeneracy
+    yield "square16_pm", I.square_lattice(16, coupling="pm1", seed=2008), \
+        dict(order=I.square_sweep_order(16), count=True, config=True)
+    # 12x12 3-state Potts glass, Gaussian couplings
+    yield "potts12_gauss", I.potts_square(12, coupling="gauss", seed=2008), \
+        dict(order=I.square_sweep_order(12), count=True, config=True)
+
+
+def main():
+    out = {}
+    if os.path.exists(OUT):
+        with open(OUT) as f:
+            out = json.load(f)
+    only = set(sys.argv[1:])
+    for name, inst, kw in cases():
+        if only and name not in only:
+            continue
+        t = time.time()
+        r = O.solve(inst, **kw)
+        out[name] = dict(
+            name=inst["name"], seed=inst["seed"], digest=I.instance_digest(inst),
+            E=r["E"], count=None if r["count"] is None else str(r["count"]),
+            state="".join(str(int(x)) for x in r["state"]) if r["state"] is not None else None,
+            oracle_seconds=round(time.time() - t, 1))
+        print(name, out[name]["E"], out[name]["count"], out[name]["oracle_seconds"], flush=True)
+        with open(OUT, "w") as f:
+            json.dump(out, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -243,7 +243,7 @@ def test_autograd_gradient_is_ground_state():
     sigma, E2 = sg.config()
     s = torch.tensor(sigma, dtype=torch.float32, device="cuda")
     e = torch.tensor(inst["edges"], dtype=torch.long, device="cuda")
-    assert float(E) == E2
+    assert float(E.detach()) == E2
     assert torch.equal(h.grad, -s)
     assert torch.equal(J.grad, -(s[e[:, 0]] * s[e[:, 1]]))
 

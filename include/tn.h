@@ -188,6 +188,35 @@ tn_status tn_profile_reset(tn_ctx *ctx);
 tn_status tn_plan_info(const tn_ctx *ctx, int32_t *n_steps, int32_t *n_transposes,
                        int64_t *arena_energy, int64_t *arena_config, int64_t *arena_count);
 
+/*
+ * tn_energy_noalloc -- E_min like tn_energy, for callers that cannot allocate
+ *   device memory: code recording work inside a CUDA stream capture (where
+ *   cudaMalloc is not allowed), frameworks whose caching allocator owns the
+ *   whole device, and latency-critical loops that cannot pay for the device
+ *   synchronisation that cudaMalloc / cudaFree imply.  The paper has no
+ *   counterpart; it is an interface of this library only.
+ *   ctx must be built and ordered (both are host-only and allocate no device
+ *   memory).  J_dev (n_edges floats) and h_dev (n_spins floats; NULL only for
+ *   instances built without fields) are device pointers the caller owns;
+ *   E_dev receives E_min as one float in device memory; the work is queued
+ *   on cuda_stream (NULL = legacy default stream) and the call does not wait
+ *   for it.  INT32 contexts read J_dev / h_dev as integers (rounded).
+ *   Scratch: a static 32 MiB device array inside libtn.so, held by every GPU
+ *   that loads the library until the process exits.  A plan whose
+ *   intermediates plus leaf descriptors need more returns TN_ENOMEM with the
+ *   size it needs (lattices up to about 20 x 20 fit).  The first call on a
+ *   device looks up the array's device address (cudaGetSymbolAddress); make
+ *   that first call before any stream capture.  No cudaMalloc, cudaFree or
+ *   allocating library routine is called; the leaf descriptors are copied
+ *   into the scratch with one cudaMemcpyAsync from host memory.
+ *   All calls share the one array and it keeps the last call's contents;
+ *   every intermediate is written before it is read, so nothing needs
+ *   clearing, but calls that overlap on the GPU (other streams, other host
+ *   threads, other contexts) race on the scratch: serialise them.
+ */
+tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev, float *E_dev,
+                            void *cuda_stream);
+
 /* One-line reason for the last failing call on ctx (or of tn_build when ctx
  * is NULL).  Valid until the next call on the same context. */
 const char *tn_last_error(const tn_ctx *ctx);

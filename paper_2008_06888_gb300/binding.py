@@ -44,6 +44,8 @@ _SIGS = {
                                  C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
     "tn_profile_reset": (C.c_int, [C.c_void_p]),
+    "tn_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
     "tn_last_error": (C.c_char_p, [C.c_void_p]),
     "tn_destroy": (None, [C.c_void_p]),
 }
@@ -217,6 +219,17 @@ def tn_profile_get(ctx, kind=-1):
 
 def tn_profile_reset(ctx):
     _check(lib().tn_profile_reset(ctx), ctx)
+
+
+def tn_energy_noalloc(ctx, J_ptr, h_ptr, E_ptr, stream_handle=0):
+    """E_min into device memory without any device allocation (include/tn.h).
+
+    J_ptr, h_ptr (may be None), E_ptr: device addresses as ints; the result
+    lands in E_ptr asynchronously on the given stream.
+    """
+    _check(lib().tn_energy_noalloc(ctx, C.c_void_p(J_ptr), None if h_ptr is None else
+                                   C.c_void_p(h_ptr), C.c_void_p(E_ptr),
+                                   C.c_void_p(stream_handle)), ctx)
 
 
 def tn_last_error(ctx):

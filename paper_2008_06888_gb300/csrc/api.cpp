@@ -51,6 +51,9 @@ struct tn_ctx {
   struct Pending { int kind, e0, e1; };
   std::vector<Pending> pending;
   int ev_next = 0;
+  // host-side program of tn_energy_noalloc and the plan fingerprint it was built for
+  std::unique_ptr<Program> prog_noalloc;
+  uint64_t noalloc_fp = 0;
 };
 
 static std::string g_build_err;
@@ -657,6 +660,76 @@ tn_status tn_plan_info(const tn_ctx *ctx, int32_t *n_steps, int32_t *n_transpose
     if (!build_program(ctx->net, ctx->plan, PM_COUNT, ctx->dt, 4, 0, &pn, &err)) return TN_EINVAL;
     *arena_count = pn.arena_bytes;
   }
+  return TN_OK;
+}
+
+// For callers that cannot allocate device memory (see tn.h): the energy
+// program runs in the static scratch of noalloc.cu.  Nothing here calls
+// cudaMalloc/cudaFree; the only device traffic besides the kernels is one
+// host-to-device copy of the leaf descriptors into the scratch.
+tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev, float *E_dev,
+                            void *cuda_stream) {
+  if (!ctx) return TN_EINVAL;
+  if (!E_dev) return fail(ctx, TN_EINVAL, "E_dev is NULL");
+  if (ctx->net.m > 0 && !J_dev) return fail(ctx, TN_EINVAL, "J_dev is NULL");
+  if (!ctx->net.h.empty() && !h_dev)
+    return fail(ctx, TN_EINVAL, "the instance has fields: h_dev is required");
+  if (!ctx->ordered) return fail(ctx, TN_ESTATE, "tn_order has not been called");
+  uint64_t fp = 1469598103934665603ull;
+  for (auto &st : ctx->plan.steps) {
+    fp = (fp ^ (uint64_t)(st.a + 7)) * 1099511628211ull;
+    fp = (fp ^ (uint64_t)(st.b + 7)) * 1099511628211ull;
+    fp = (fp ^ (uint64_t)(st.c + 7)) * 1099511628211ull;
+  }
+  if (!ctx->prog_noalloc || ctx->noalloc_fp != fp) {
+    std::unique_ptr<Program> pg(new Program());
+    std::string err;
+    if (!build_program(ctx->net, ctx->plan, PM_ENERGY, ctx->dt, 0, 0, pg.get(), &err))
+      return fail(ctx, TN_EINVAL, err);
+    ctx->prog_noalloc = std::move(pg);
+    ctx->noalloc_fp = fp;
+  }
+  Program &p = *ctx->prog_noalloc;
+  const int64_t leaves_off = (p.arena_bytes + 255) / 256 * 256;
+  const int64_t need = leaves_off + (int64_t)(p.leaves.size() * sizeof(LeafDesc));
+  const int64_t cap = (int64_t)noalloc_scratch_bytes();
+  if (need > cap)
+    return fail(ctx, TN_ENOMEM, "tn_energy_noalloc: this plan needs " + std::to_string(need) +
+                                    " bytes of scratch; the static scratch holds " +
+                                    std::to_string(cap) + " bytes (use tn_energy)");
+  char *base = nullptr;
+  CK(noalloc_scratch(&base));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  LeafDesc *d_leaves = reinterpret_cast<LeafDesc *>(base + leaves_off);
+  if (!p.leaves.empty())
+    CK(cudaMemcpyAsync(d_leaves, p.leaves.data(), p.leaves.size() * sizeof(LeafDesc),
+                       cudaMemcpyHostToDevice, st));
+  PrimeSet ps;
+  for (int i = 0; i < TN_MAX_PRIMES; ++i) ps.c[i] = kPrimeC[i];
+  auto X = [&](const Loc &l) -> void * { return l.buf < 0 ? nullptr : base + abs_off(p, l); };
+  for (const Op &op : p.ops) {
+    cudaError_t e = cudaSuccess;
+    switch (op.kind) {
+      case OP_LEAVES:
+        e = launch_leaves(p.dt, p.q, d_leaves, (int)p.leaves.size(), J_dev, h_dev, base, 0, st);
+        break;
+      case OP_PERM:
+        e = launch_permute(p.perms[op.idx], X(op.in0), X(op.out), nullptr, nullptr, st);
+        break;
+      case OP_GATE:
+        e = launch_gate(p.dt, p.gates[op.idx], X(op.in0), X(op.in1), X(op.out), nullptr,
+                        nullptr, nullptr, ps, st);
+        break;
+      case OP_GEMM:
+        e = launch_gemm(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out), st);
+        break;
+      case OP_TRACE:
+        break;
+    }
+    if (e != cudaSuccess)
+      return fail(ctx, TN_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  }
+  CK(launch_energy_out(p.dt, X(p.root), E_dev, st));
   return TN_OK;
 }
 

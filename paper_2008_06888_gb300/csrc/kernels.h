@@ -44,4 +44,11 @@ cudaError_t launch_grad(int q, int n, int m, const int32_t *eu, const int32_t *e
 // Convert a state (indices) to the +-1 / 0..q-1 convention of tn_config.
 cudaError_t launch_state_out(int q, int n, const int8_t *state, int8_t *out, cudaStream_t st);
 
+// Static scratch of tn_energy_noalloc (noalloc.cu): its size, its device
+// address on the current device (looked up once per device), and the kernel
+// writing E = -root as float.
+size_t noalloc_scratch_bytes();
+cudaError_t noalloc_scratch(char **ptr);
+cudaError_t launch_energy_out(Dtype dt, const void *root, float *E, cudaStream_t st);
+
 }  // namespace tn

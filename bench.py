@@ -34,8 +34,8 @@ ORDER_SEED, ORDER_RESTARTS = 1, 64
 WORKLOAD = (f"square{L}x{L} open Ising glass, J~N(0,1) fp32, h~N(0,0.1^2) fp32, "
             f"greedy order (seed {ORDER_SEED}, {ORDER_RESTARTS} restarts); per instance E_min "
             f"+ sigma* (checkpointed forward + argmax traceback)")
-KIND_BOUND = {"gate": "hbm", "transpose": "hbm", "leaves": "hbm", "trace": "hbm", "gemm": "alu",
-              "other": "hbm"}
+KIND_BOUND = {"gate": "hbm", "transpose": "hbm", "leaves": "hbm", "trace": "latency",
+              "gemm": "alu", "other": "hbm", "chain": "hbm"}
 
 
 def parse():
@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--L", type=int, default=24, help="lattice side (profiling runs only)")
+    ap.add_argument("--mode", default="config", choices=["config", "energy"],
+                    help="config: E_min + sigma* (the workload); energy: E_min only (profiling)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
 
 
@@ -141,9 +145,9 @@ def traffic_from_profiles(kind):
         return None
 
 
-def make_instances(rank, batch):
+def make_instances(rank, batch, side=L):
     import instances as I
-    return [I.square_lattice(L, coupling="gauss", field_sigma=FIELD_SIGMA, seed=1000 * rank + k)
+    return [I.square_lattice(side, coupling="gauss", field_sigma=FIELD_SIGMA, seed=1000 * rank + k)
             for k in range(batch)]
 
 
@@ -212,7 +216,7 @@ def main():
     import paper_2008_06888_gb300 as P
     from paper_2008_06888_gb300 import binding as B
 
-    insts = make_instances(rank, args.batch)
+    insts = make_instances(rank, args.batch, args.L)
     sg = P.SpinGlass(insts[0], order="greedy", seed=ORDER_SEED, restarts=ORDER_RESTARTS)
     stream = torch.cuda.current_stream(dev)
     sg.set_stream(stream.cuda_stream)
@@ -223,8 +227,11 @@ def main():
     def step():
         for k in range(args.batch):
             sg.set_couplings(Jd[k], hd[k], on_device=True)
-            B.tn_forward(sg.ctx)
-            B.tn_backward(sg.ctx, None)
+            if args.mode == "energy":
+                B.tn_energy(sg.ctx)
+            else:
+                B.tn_forward(sg.ctx)
+                B.tn_backward(sg.ctx, None)
 
     for _ in range(args.warmup):
         step()
@@ -247,7 +254,7 @@ def main():
         if world > 1:
             dist.barrier()
         ms = sum(a.elapsed_time(b) for a, b in ev)
-        prof = {B.KIND_NAMES[k]: B.tn_profile_get(sg.ctx, k) for k in range(6)}
+        prof = {B.KIND_NAMES[k]: B.tn_profile_get(sg.ctx, k) for k in range(len(B.KIND_NAMES))}
         total = B.tn_profile_get(sg.ctx, -1)
         B.tn_set_profiling(sg.ctx, False)
         return ms, prof, total
@@ -307,7 +314,7 @@ def main():
                 "peak_source": "152 SMs x 128 lanes x max clock (one lane-op per clock)"}
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu and args.L == L:
         est, k1, tf = oracle_sample(insts[0], budget_s=15.0)
         cpu = {"value": 1.0 / est, "unit": "instances/s", "cores": 1, "kind": "oracle",
                "sample": f"numpy float64 variable elimination, first {k1} of {L*L} "
@@ -318,7 +325,9 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "global_batch": args.batch * world,
+                "config": {"workload": WORKLOAD if (args.L == L and args.mode == "config") else
+                           f"square{args.L}x{args.L} Gaussian, mode {args.mode} (profiling run)",
+                           "global_batch": args.batch * world,
                            "instances_per_step_per_gpu": args.batch,
                            "l2": "flushed between timed steps (256 MB write)",
                            "log2_peak_elements": sg.log2_peak, "log2_macs": sg.log2_ops},

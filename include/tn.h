@@ -173,7 +173,8 @@ tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limb
  * Measurement hooks.  Every kernel launch of the context is counted; with
  * profiling enabled each launch is also bracketed by CUDA events on the
  * context stream.  tn_profile_get(kind): 0 leaves, 1 transpose, 2 gate
- * contraction, 3 max-plus GEMM, 4 traceback, 5 other, -1 all; it synchronises
+ * contraction, 3 max-plus GEMM, 4 traceback, 5 other, 6 fused gate chain,
+ * -1 all; it synchronises
  * the stream and returns launches, total milliseconds (profiling only),
  * algorithmic bytes (operands read + result written, each once) and tropical
  * multiply-adds of those launches.  tn_profile_reset clears the counters.

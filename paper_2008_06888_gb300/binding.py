@@ -202,7 +202,7 @@ def tn_plan_info(ctx):
                 arena_config=ac.value, arena_count=an.value)
 
 
-KIND_NAMES = ["leaves", "transpose", "gate", "gemm", "trace", "other"]
+KIND_NAMES = ["leaves", "transpose", "gate", "gemm", "trace", "other", "chain"]
 
 
 def tn_set_profiling(ctx, enable=True):

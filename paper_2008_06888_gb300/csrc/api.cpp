@@ -42,11 +42,12 @@ struct tn_ctx {
   int prog_P = 0;
   bool have_state = false;
   bool fwd_done = false;   // tn_forward ran last; its checkpoints are live
+  cudaStream_t cap_stream = nullptr;   // private stream for graph capture
   // measurement
   bool profiling = false;
-  int64_t launches[6] = {0, 0, 0, 0, 0, 0};
-  double prof_ms[6] = {0, 0, 0, 0, 0, 0}, prof_bytes[6] = {0, 0, 0, 0, 0, 0};
-  double prof_macs[6] = {0, 0, 0, 0, 0, 0};
+  int64_t launches[7] = {0, 0, 0, 0, 0, 0, 0};
+  double prof_ms[7] = {0, 0, 0, 0, 0, 0, 0}, prof_bytes[7] = {0, 0, 0, 0, 0, 0, 0};
+  double prof_macs[7] = {0, 0, 0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> ev_pool;
   struct Pending { int kind, e0, e1; };
   std::vector<Pending> pending;
@@ -88,8 +89,13 @@ void free_program(Program *p) {
   if (!p) return;
   if (p->d_leaves) cudaFree(p->d_leaves);
   if (p->d_trace) cudaFree(p->d_trace);
+  if (p->d_chain_traces) cudaFree(p->d_chain_traces);
+  for (auto &g : p->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  p->graphs.clear();
   p->d_leaves = nullptr;
   p->d_trace = nullptr;
+  p->d_chain_traces = nullptr;
 }
 
 tn_status ensure_device(tn_ctx *ctx) {
@@ -170,6 +176,11 @@ tn_status get_program(tn_ctx *ctx, ProgMode mode, int P, Program **out) {
       CK(cudaMemcpy(p.d_trace, p.trace.data(), p.trace.size() * sizeof(TraceStep),
                     cudaMemcpyHostToDevice));
     }
+    if (!p.chain_traces.empty()) {
+      CK(cudaMalloc(&p.d_chain_traces, p.chain_traces.size() * sizeof(ChainTrace)));
+      CK(cudaMemcpy(p.d_chain_traces, p.chain_traces.data(),
+                    p.chain_traces.size() * sizeof(ChainTrace), cudaMemcpyHostToDevice));
+    }
     if (mode == PM_COUNT) ctx->prog_P = P;
   }
   Program &p = *slot;
@@ -217,20 +228,20 @@ int op_kind_slot(OpKind k) {
     case OP_GATE: return 2;
     case OP_GEMM: return 3;
     case OP_TRACE: return 4;
+    case OP_CHAIN: return 6;
   }
   return 5;
 }
 
-tn_status run_program(tn_ctx *ctx, Program &p, int op_begin = 0, int op_end = -1) {
+tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_t st,
+                  bool account) {
   char *ar = ctx->d_arena;
-  cudaStream_t st = ctx->stream;
   PrimeSet ps;
   for (int i = 0; i < TN_MAX_PRIMES; ++i) ps.c[i] = kPrimeC[i];
   auto X = [&](const Loc &l) -> void * { return l.buf < 0 ? nullptr : ar + abs_off(p, l); };
   auto Nn = [&](const Loc &l) -> uint64_t * {
     return l.buf < 0 ? nullptr : (uint64_t *)(ar + p.bufs[l.buf].off + l.noff);
   };
-  if (op_end < 0) op_end = (int)p.ops.size();
   if (p.mode == PM_CONFIG && op_end > p.fwd_end)
     CK(cudaMemsetAsync(ctx->d_state, 0xff, std::max(1, ctx->net.n), st));
   if (ctx->profiling && ctx->ev_next > 4096) collect_profile(ctx);
@@ -262,8 +273,12 @@ tn_status run_program(tn_ctx *ctx, Program &p, int op_begin = 0, int op_end = -1
                                 Nn(op.in0), Nn(op.in1), Nn(op.out), ps, st);
         break;
       case OP_TRACE:
-        e = launch_trace(p.dt, p.q, p.d_trace + op.trace_begin, op.trace_n, ar, ctx->d_state,
-                         ctx->d_err, st);
+        e = launch_trace(p.dt, p.q, p.d_trace + op.trace_begin, op.trace_n, p.d_chain_traces,
+                         p.trace_smem, ar, ctx->d_state, ctx->net.n, ctx->d_err, st);
+        break;
+      case OP_CHAIN:
+        e = launch_chain(p.dt, p.chains[op.idx], ar, X(op.in0), Nn(op.in0), X(op.out), Nn(op.out),
+                         ps, st);
         break;
     }
     if (e != cudaSuccess)
@@ -271,15 +286,78 @@ tn_status run_program(tn_ctx *ctx, Program &p, int op_begin = 0, int op_end = -1
     int nl = 1;
     if (op.kind == OP_GEMM && p.P > 0) nl = 2;
     if (op.kind == OP_PERM && p.P > 0) nl = 2;
-    ctx->launches[slot] += nl;
-    ctx->prof_bytes[slot] += op.bytes;
-    ctx->prof_macs[slot] += op.macs;
+    if (account) {
+      ctx->launches[slot] += nl;
+      ctx->prof_bytes[slot] += op.bytes;
+      ctx->prof_macs[slot] += op.macs;
+    }
     if (ctx->profiling) {
       int e1 = ctx->ev_next;
       cudaEventRecord(next_event(ctx), st);
       ctx->pending.push_back({slot, e0, e1});
     }
   }
+  return TN_OK;
+}
+
+void account_range(tn_ctx *ctx, const Program &p, int b, int e) {
+  for (int oi = b; oi < e; ++oi) {
+    const Op &op = p.ops[oi];
+    const int slot = op_kind_slot(op.kind);
+    int nl = 1;
+    if ((op.kind == OP_GEMM || op.kind == OP_PERM) && p.P > 0) nl = 2;
+    ctx->launches[slot] += nl;
+    ctx->prof_bytes[slot] += op.bytes;
+    ctx->prof_macs[slot] += op.macs;
+  }
+}
+
+// Eager on the first run of a range (and whenever profiling, or with
+// TN_NO_GRAPH set); captured into a CUDA graph on the second run and
+// replayed from then on.
+tn_status run_program(tn_ctx *ctx, Program &p, int op_begin = 0, int op_end = -1) {
+  if (op_end < 0) op_end = (int)p.ops.size();
+  static const bool no_graph = std::getenv("TN_NO_GRAPH") != nullptr;
+  if (ctx->profiling || no_graph) return run_ops(ctx, p, op_begin, op_end, ctx->stream, true);
+  Program::Graph *g = nullptr;
+  for (auto &x : p.graphs)
+    if (x.begin == op_begin && x.end == op_end) g = &x;
+  if (g && g->arena != ctx->d_arena) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+    g->runs = 0;
+    g->arena = ctx->d_arena;
+  }
+  if (!g) {
+    p.graphs.push_back(Program::Graph{op_begin, op_end, 0, ctx->d_arena, nullptr});
+    g = &p.graphs.back();
+  }
+  if (!g->exec && g->runs == 0) {
+    g->runs = 1;
+    return run_ops(ctx, p, op_begin, op_end, ctx->stream, true);
+  }
+  if (!g->exec) {
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    tn_status s = run_ops(ctx, p, op_begin, op_end, ctx->cap_stream, false);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (s != TN_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return fail(ctx, TN_ECUDA, std::string("graph capture: ") +
+                                                       cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g->exec = nullptr;
+      return fail(ctx, TN_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+  }
+  CK(cudaGraphLaunch(g->exec, ctx->stream));
+  g->runs++;
+  account_range(ctx, p, op_begin, op_end);
   return TN_OK;
 }
 
@@ -612,11 +690,11 @@ tn_status tn_set_profiling(tn_ctx *ctx, int32_t enable) {
 
 tn_status tn_profile_get(tn_ctx *ctx, int32_t kind, int64_t *launches, double *ms,
                          double *bytes, double *macs) {
-  if (!ctx || kind < -1 || kind > 5) return TN_EINVAL;
+  if (!ctx || kind < -1 || kind > 6) return TN_EINVAL;
   collect_profile(ctx);
   int64_t l = 0;
   double t = 0, b = 0, m = 0;
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < 7; ++k)
     if (kind == -1 || kind == k) {
       l += ctx->launches[k];
       t += ctx->prof_ms[k];
@@ -633,7 +711,7 @@ tn_status tn_profile_get(tn_ctx *ctx, int32_t kind, int64_t *launches, double *m
 tn_status tn_profile_reset(tn_ctx *ctx) {
   if (!ctx) return TN_EINVAL;
   collect_profile(ctx);
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 7; ++k) {
     ctx->launches[k] = 0;
     ctx->prof_ms[k] = ctx->prof_bytes[k] = ctx->prof_macs[k] = 0;
   }
@@ -725,6 +803,10 @@ tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev,
         break;
       case OP_TRACE:
         break;
+      case OP_CHAIN:
+        e = launch_chain(p.dt, p.chains[op.idx], base, X(op.in0), nullptr, X(op.out), nullptr, ps,
+                         st);
+        break;
     }
     if (e != cudaSuccess)
       return fail(ctx, TN_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -751,6 +833,7 @@ void tn_destroy(tn_ctx *ctx) {
   }
   if (ctx->d_arena) cudaFree(ctx->d_arena);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 

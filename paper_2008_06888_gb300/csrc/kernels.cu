@@ -127,9 +127,14 @@ __global__ void __launch_bounds__(256) k_gate(const GateParams p, const T *__res
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < p.outer; o += stride) {
     int64_t r = o, oa = 0, ob = 0, oc = 0;
     for (int s = p.nseg - 1; s >= 0; --s) {
-      int64_t sz = p.seg_size[s];
-      int64_t i = r % sz;
-      r /= sz;
+      int64_t i;
+      if (p.seg_sh[s] >= 0) {
+        i = r & (p.seg_size[s] - 1);
+        r >>= p.seg_sh[s];
+      } else {
+        i = r % p.seg_size[s];
+        r /= p.seg_size[s];
+      }
       oa += i * p.seg_sA[s];
       ob += i * p.seg_sB[s];
       oc += i * p.seg_sC[s];
@@ -350,91 +355,792 @@ cudaError_t launch_permute(const PermParams &p, const void *xin, void *xout, con
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------- fused gate chains
+
+template <int Q> __device__ __forceinline__ int div_p(int x, int d, int sh) {
+  return Q == 2 ? (x >> sh) : x / d;
+}
+template <int Q> __device__ __forceinline__ int mod_q(int x) { return Q == 2 ? (x & 1) : x % Q; }
+
+// B offset (within B) of the batch digits of local index x.
+template <int Q>
+__device__ __forceinline__ int gate_boff(const ChainGate &g, int x) {
+  int o = 0;
+  if (g.nb > 0) o += mod_q<Q>(div_p<Q>(x, g.lsb[0], g.lsbh[0])) * (int)g.sBb[0];
+  if (g.nb > 1) o += mod_q<Q>(div_p<Q>(x, g.lsb[1], g.lsbh[1])) * (int)g.sBb[1];
+  return o;
+}
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 t; };
+template <> struct Vec2<int32_t> { typedef int2 t; };
+
+// q = 2 replace gate whose B is a plain 2x2 matrix (no tile legs): the
+// matrix sits in registers and pairs are moved as 2-vectors.
+template <typename T>
+__device__ __forceinline__ void replace2(const ChainGate &g, const T *src, T *dst, const T *sB,
+                                         int tile) {
+  typedef typename Vec2<T>::t V;
+  const T m00 = sB[0], m01 = sB[g.sBn], m10 = sB[g.sBk], m11 = sB[g.sBk + g.sBn];
+  if (g.ls == 1) {
+    const V *vs = reinterpret_cast<const V *>(src);
+    V *vd = reinterpret_cast<V *>(dst);
+    for (int j = threadIdx.x; j < tile / 2; j += blockDim.x) {
+      V v = vs[j], o;
+      o.x = max(v.x + m00, v.y + m10);
+      o.y = max(v.x + m01, v.y + m11);
+      vd[j] = o;
+    }
+    return;
+  }
+  for (int jj = threadIdx.x; jj < tile / 4; jj += blockDim.x) {
+    const int j = 2 * jj;
+    const int x = ((j >> g.lsh) << (g.lsh + 1)) | (j & (g.ls - 1));
+    const V a = *reinterpret_cast<const V *>(src + x);
+    const V b = *reinterpret_cast<const V *>(src + x + g.ls);
+    V o0, o1;
+    o0.x = max(a.x + m00, b.x + m10);
+    o0.y = max(a.y + m00, b.y + m10);
+    o1.x = max(a.x + m01, b.x + m11);
+    o1.y = max(a.y + m01, b.y + m11);
+    *reinterpret_cast<V *>(dst + x) = o0;
+    *reinterpret_cast<V *>(dst + x + g.ls) = o1;
+  }
+}
+
+// q = 2 diagonal gate on one or two tile legs: 2 or 4 values in registers.
+template <typename T>
+__device__ __forceinline__ void diag2(const ChainGate &g, const T *src, T *dst, const T *sB,
+                                      int tile) {
+  if (g.nb == 2) {
+    const T b00 = sB[0], b01 = sB[g.sBb[1]], b10 = sB[g.sBb[0]], b11 = sB[g.sBb[0] + g.sBb[1]];
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) {
+      const int d0 = (i >> g.lsbh[0]) & 1, d1 = (i >> g.lsbh[1]) & 1;
+      const T add = d0 ? (d1 ? b11 : b10) : (d1 ? b01 : b00);
+      dst[i] = src[i] + add;
+    }
+  } else {
+    const T b0 = sB[0], b1 = sB[g.sBb[0]];
+    for (int i = threadIdx.x; i < tile; i += blockDim.x)
+      dst[i] = src[i] + (((i >> g.lsbh[0]) & 1) ? b1 : b0);
+  }
+}
+
+// Apply one gate to a tile in shared memory (src may equal dst): a replace
+// gate maps each q-tuple along the replaced leg, a diagonal gate adds B.
+template <typename T, int Q>
+__device__ __forceinline__ void apply_gate(const ChainGate &g, const T *src, T *dst,
+                                           const T *sB, int tile) {
+  if (Q == 2 && g.kind == 0 && g.nb == 0) {
+    replace2<T>(g, src, dst, sB, tile);
+    return;
+  }
+  if (Q == 2 && g.kind == 1 && g.nb >= 1) {
+    diag2<T>(g, src, dst, sB, tile);
+    return;
+  }
+  if (g.kind == 0) {
+    const int n = tile / Q;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const int hi = div_p<Q>(j, g.ls, g.lsh);
+      const int x = hi * g.ls * Q + (j - hi * g.ls);
+      const int bo = gate_boff<Q>(g, x);
+      T in[Q];
+#pragma unroll
+      for (int u = 0; u < Q; ++u) in[u] = src[x + u * g.ls];
+#pragma unroll
+      for (int v = 0; v < Q; ++v) {
+        T best = in[0] + sB[bo + v * (int)g.sBn];
+#pragma unroll
+        for (int u = 1; u < Q; ++u) best = max(best, in[u] + sB[bo + u * (int)g.sBk + v * (int)g.sBn]);
+        dst[x + v * g.ls] = best;
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) dst[i] = src[i] + sB[gate_boff<Q>(g, i)];
+  }
+}
+
+// Counting version: values and P residue planes (plane stride `tile`).
+template <typename T, int Q>
+__device__ __forceinline__ void apply_gate_count(const ChainGate &g, T *s, uint64_t *sn,
+                                                 const T *sB, const uint64_t *sBn, int nBel,
+                                                 int tile, int P, const PrimeSet &ps) {
+  if (g.kind == 0) {
+    const int n = tile / Q;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const int hi = div_p<Q>(j, g.ls, g.lsh);
+      const int x = hi * g.ls * Q + (j - hi * g.ls);
+      const int64_t bo = gate_boff<Q>(g, x);
+      T in[Q], out[Q];
+#pragma unroll
+      for (int u = 0; u < Q; ++u) in[u] = s[x + u * g.ls];
+#pragma unroll
+      for (int v = 0; v < Q; ++v) {
+        T best = in[0] + sB[bo + v * g.sBn];
+#pragma unroll
+        for (int u = 1; u < Q; ++u) best = max(best, in[u] + sB[bo + u * g.sBk + v * g.sBn]);
+        out[v] = best;
+      }
+      for (int pl = 0; pl < P; ++pl) {
+        uint64_t *np = sn + (int64_t)pl * tile;
+        const uint64_t *bp = sBn + (int64_t)pl * nBel;
+        uint64_t nin[Q], nout[Q];
+#pragma unroll
+        for (int u = 0; u < Q; ++u) nin[u] = np[x + u * g.ls];
+#pragma unroll
+        for (int v = 0; v < Q; ++v) {
+          uint64_t c = 0;
+#pragma unroll
+          for (int u = 0; u < Q; ++u) {
+            const int64_t bi = bo + u * g.sBk + v * g.sBn;
+            if (in[u] + sB[bi] == out[v]) c = addmod61(c, mulmod61(nin[u], bp[bi], ps.c[pl]), ps.c[pl]);
+          }
+          nout[v] = c;
+        }
+#pragma unroll
+        for (int v = 0; v < Q; ++v) np[x + v * g.ls] = nout[v];
+      }
+#pragma unroll
+      for (int v = 0; v < Q; ++v) s[x + v * g.ls] = out[v];
+    }
+  } else {
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) {
+      const int64_t bo = gate_boff<Q>(g, i);
+      s[i] = s[i] + sB[bo];
+      for (int pl = 0; pl < P; ++pl)
+        sn[(int64_t)pl * tile + i] = mulmod61(sn[(int64_t)pl * tile + i], sBn[(int64_t)pl * nBel + bo],
+                                              ps.c[pl]);
+    }
+  }
+}
+
+// Copy every gate's B (values, and planes when P > 0) into shared memory.
+template <typename T>
+__device__ __forceinline__ void load_gate_operands(const ChainParams &p, const T *X,
+                                                   const uint64_t *Xn, T *sB, uint64_t *sBn,
+                                                   int stride_el) {
+  for (int gi = 0; gi < p.ngates; ++gi) {
+    const ChainGate &g = p.g[gi];
+    for (int e = threadIdx.x; e < g.nBel; e += blockDim.x) {
+      sB[gi * stride_el + e] = X[g.offB + e];
+      for (int pl = 0; pl < p.P; ++pl)
+        sBn[((int64_t)gi * p.P + pl) * stride_el + e] = Xn[g.offBn + pl * g.planeB + e];
+    }
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ int64_t tile_elem_off(const ChainParams &p, int i) {
+  const int h = Q == 2 ? (i >> p.loh) : i / p.lo;
+  return p.hi_off[h] + (i - h * p.lo);
+}
+
+constexpr int kGateBMax = 27;  // q^3 elements of one gate operand
+
+template <typename T, int Q, bool COUNT>
+__global__ void __launch_bounds__(256) k_chain(const ChainParams p, const T *__restrict__ X,
+                                               const uint64_t *__restrict__ Xn,
+                                               const T *__restrict__ Ax,
+                                               const uint64_t *__restrict__ An,
+                                               T *__restrict__ Cx, uint64_t *__restrict__ Cn,
+                                               const PrimeSet ps) {
+  extern __shared__ __align__(16) char smem[];
+  T *s = reinterpret_cast<T *>(smem);
+  T *sB = s + p.tile;
+  uint64_t *sn = reinterpret_cast<uint64_t *>(
+      smem + ((sizeof(T) * (p.tile + TN_CHAIN_MAX_G * kGateBMax) + 15) / 16) * 16);
+  uint64_t *sBn = sn + (int64_t)p.P * p.tile;
+  load_gate_operands<T>(p, X, Xn, sB, sBn, kGateBMax);
+  for (int64_t o = blockIdx.x; o < p.outer; o += gridDim.x) {
+    int64_t r = o, base = 0;
+    for (int sg = p.nseg - 1; sg >= 0; --sg) {
+      if (Q == 2) {
+        base += (r & (p.seg_size[sg] - 1)) * p.seg_s[sg];
+        r >>= p.seg_sh[sg];
+      } else {
+        const int64_t sz = p.seg_size[sg];
+        base += (r % sz) * p.seg_s[sg];
+        r /= sz;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.tile; i += blockDim.x) {
+      const int64_t off = base + tile_elem_off<Q>(p, i);
+      s[i] = Ax[off];
+      if (COUNT)
+        for (int pl = 0; pl < p.P; ++pl) sn[(int64_t)pl * p.tile + i] = An[pl * p.planeA + off];
+    }
+    __syncthreads();
+    for (int gi = 0; gi < p.ngates; ++gi) {
+      if (COUNT)
+        apply_gate_count<T, Q>(p.g[gi], s, sn, sB + gi * kGateBMax,
+                               sBn + (int64_t)gi * p.P * kGateBMax, kGateBMax, p.tile, p.P, ps);
+      else
+        apply_gate<T, Q>(p.g[gi], s, s, sB + gi * kGateBMax, p.tile);
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < p.tile; i += blockDim.x) {
+      const int64_t off = base + tile_elem_off<Q>(p, i);
+      Cx[off] = s[i];
+      if (COUNT)
+        for (int pl = 0; pl < p.P; ++pl) Cn[pl * p.planeC + off] = sn[(int64_t)pl * p.tile + i];
+    }
+  }
+}
+
+size_t chain_smem_bytes(const ChainParams &p, size_t elem) {
+  size_t a = ((elem * (p.tile + TN_CHAIN_MAX_G * kGateBMax) + 15) / 16) * 16;
+  return a + (size_t)p.P * 8 * (p.tile + (size_t)TN_CHAIN_MAX_G * kGateBMax);
+}
+
+template <typename T, int Q, bool COUNT>
+static cudaError_t launch_chain_t(const ChainParams &p, const char *arena, const void *Ax,
+                                  const uint64_t *An, void *Cx, uint64_t *Cn, const PrimeSet &ps,
+                                  cudaStream_t st) {
+  size_t sm = chain_smem_bytes(p, sizeof(T));
+  static size_t configured = 0;
+  if (sm > 48 * 1024 && sm > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_chain<T, Q, COUNT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    configured = sm;
+  }
+  int64_t blocks = p.outer < 152 * 8 ? p.outer : 152 * 8;
+  k_chain<T, Q, COUNT><<<(int)blocks, 256, sm, st>>>(
+      p, reinterpret_cast<const T *>(arena), reinterpret_cast<const uint64_t *>(arena),
+      static_cast<const T *>(Ax), An, static_cast<T *>(Cx), Cn, ps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
+                          void *Cx, cudaStream_t st);
+
+cudaError_t launch_chain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
+                         const uint64_t *An, void *Cx, uint64_t *Cn, const PrimeSet &ps,
+                         cudaStream_t st) {
+  if (p.outer == 0) return cudaSuccess;
+  if (p.mode == 1) return launch_rchain(dt, p, arena, Ax, Cx, st);
+  const bool c = p.P > 0;
+  if (dt == DT_F32) {
+    if (p.q == 2) return c ? launch_chain_t<float, 2, true>(p, arena, Ax, An, Cx, Cn, ps, st)
+                           : launch_chain_t<float, 2, false>(p, arena, Ax, An, Cx, Cn, ps, st);
+    return c ? launch_chain_t<float, 3, true>(p, arena, Ax, An, Cx, Cn, ps, st)
+             : launch_chain_t<float, 3, false>(p, arena, Ax, An, Cx, Cn, ps, st);
+  }
+  if (p.q == 2) return c ? launch_chain_t<int32_t, 2, true>(p, arena, Ax, An, Cx, Cn, ps, st)
+                         : launch_chain_t<int32_t, 2, false>(p, arena, Ax, An, Cx, Cn, ps, st);
+  return c ? launch_chain_t<int32_t, 3, true>(p, arena, Ax, An, Cx, Cn, ps, st)
+           : launch_chain_t<int32_t, 3, false>(p, arena, Ax, An, Cx, Cn, ps, st);
+}
+
+// Traceback of one chain record by the whole block: reload the input tile,
+// replay the gates keeping every intermediate tile, then walk back.
+template <typename T, int Q>
+__device__ void trace_chain(const ChainTrace &ct, const T *X, int8_t *state, int *err, char *smem,
+                            int64_t *sbase) {
+  const ChainParams &p = ct.p;
+  T *buf = reinterpret_cast<T *>(smem);                 // (ngates + 1) tiles
+  T *sB = buf + (int64_t)(p.ngates + 1) * p.tile;       // gate operands
+  if (threadIdx.x == 0) {
+    int64_t b = ct.offIn;
+    for (int i = 0; i < ct.nout; ++i) {
+      int d = state[ct.out_spin[i]];
+      if (d < 0 || d >= Q) { *err = 1; d = 0; }
+      b += (int64_t)d * ct.out_stride[i];
+    }
+    *sbase = b;
+  }
+  load_gate_operands<T>(p, X, nullptr, sB, nullptr, kGateBMax);
+  __syncthreads();
+  const int64_t base = *sbase;
+  for (int i = threadIdx.x; i < p.tile; i += blockDim.x) buf[i] = X[base + tile_elem_off<Q>(p, i)];
+  __syncthreads();
+  for (int gi = 0; gi < p.ngates; ++gi) {
+    apply_gate<T, Q>(p.g[gi], buf + (int64_t)gi * p.tile, buf + (int64_t)(gi + 1) * p.tile,
+                     sB + gi * kGateBMax, p.tile);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int x = 0;
+    for (int j = 0; j < p.t; ++j) {
+      int d = state[ct.local_spin[j]];
+      if (d < 0 || d >= Q) { *err = 1; d = 0; }
+      x = x * Q + d;
+    }
+    for (int gi = p.ngates - 1; gi >= 0; --gi) {
+      const ChainGate &g = p.g[gi];
+      if (g.kind != 0) continue;
+      const T *src = buf + (int64_t)gi * p.tile;
+      const T *gB = sB + gi * kGateBMax;
+      const int v = mod_q<Q>(div_p<Q>(x, g.ls, g.lsh));
+      const int x0 = x - v * g.ls;
+      const int64_t bo = gate_boff<Q>(g, x0);
+      int bu = 0;
+      T best = src[x0] + gB[bo + v * g.sBn];
+      for (int u = 1; u < Q; ++u) {
+        T val = src[x0 + u * g.ls] + gB[bo + u * g.sBk + v * g.sBn];
+        if (val > best) { best = val; bu = u; }
+      }
+      state[g.kspin] = (int8_t)bu;
+      x = x0 + bu * g.ls;
+    }
+  }
+  __syncthreads();
+}
+
+
+// ---------------------------------------------------------------- register chains (q = 2)
+//
+// Gate kinds in a register chain: 0 replace on register bit J = ls, whose B
+// may depend on one more leg (nb = 1); 2 a diagonal gate folded into the
+// replace gate just before it (its leg 0 is the replaced leg, leg 1 optional);
+// 1 a diagonal gate applied on its own.  A leg is a register bit (lsb >= 0)
+// or fixed per thread (digit = (base >> lsbh) & 1).
+
+constexpr int kRegBits = 5;   // every thread owns 2^5 elements
+
+// mask / fixed-digit form of leg k: digit(e) = ((e & mask) != 0) | fixed
+__device__ __forceinline__ void leg_sel(const ChainGate &g, int k, int64_t base, int *mask,
+                                        int *fixed) {
+  if (g.lsb[k] >= 0) {
+    *mask = 1 << g.lsb[k];
+    *fixed = 0;
+  } else {
+    *mask = 0;
+    *fixed = (int)((base >> g.lsbh[k]) & 1);
+  }
+}
+
+template <int RB, int J, typename T>
+__device__ __forceinline__ void rc_replace(T (&v)[1 << RB], const ChainGate *gs, int nfold,
+                                           const T *sB, int64_t base) {
+  const ChainGate &g = gs[0];
+  // B of the replace gate for each digit w of its extra leg
+  const int wl = g.nb > 0 ? (int)g.sBb[0] : 0;
+  int wm = 0, wf = 0;
+  if (g.nb > 0) leg_sel(g, 0, base, &wm, &wf);
+  const T a00 = sB[0], a01 = sB[g.sBn], a10 = sB[g.sBk], a11 = sB[g.sBk + g.sBn];
+  const T b00 = sB[wl], b01 = sB[wl + g.sBn], b10 = sB[wl + g.sBk], b11 = sB[wl + g.sBk + g.sBn];
+  // folded diagonal gates: value d[v][x], x the digit of their second leg
+  T d[2][2][2];
+  int dm[2] = {0, 0}, df[2] = {0, 0};
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    if (f < nfold) {
+      const ChainGate &h = gs[1 + f];
+      const T *hB = sB + (1 + f) * kGateBMax;
+      const int s0 = (int)h.sBb[0], s1 = h.nb > 1 ? (int)h.sBb[1] : 0;
+      if (h.nb > 1) leg_sel(h, 1, base, &dm[f], &df[f]);
+      d[f][0][0] = hB[0];
+      d[f][0][1] = hB[s1];
+      d[f][1][0] = hB[s0];
+      d[f][1][1] = hB[s0 + s1];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < (1 << RB); ++e) {
+    if (e & (1 << J)) continue;
+    const int w = ((e & wm) != 0) | wf;
+    const T m00 = w ? b00 : a00, m01 = w ? b01 : a01, m10 = w ? b10 : a10, m11 = w ? b11 : a11;
+    const T a = v[e], b = v[e | (1 << J)];
+    T o0 = max(a + m00, b + m10);
+    T o1 = max(a + m01, b + m11);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      if (f < nfold) {
+        const int x = ((e & dm[f]) != 0) | df[f];
+        o0 = o0 + (x ? d[f][0][1] : d[f][0][0]);
+        o1 = o1 + (x ? d[f][1][1] : d[f][1][0]);
+      }
+    }
+    v[e] = o0;
+    v[e | (1 << J)] = o1;
+  }
+}
+
+// Diagonal gate with its register legs known at compile time (K < 0: no
+// register leg in that slot): every element gets one add, the value picked
+// by compile-time digits.
+template <int RB, int K0, int K1, typename T>
+__device__ __forceinline__ void rc_diag_t(T (&v)[1 << RB], T c00, T c01, T c10, T c11) {
+#pragma unroll
+  for (int e = 0; e < (1 << RB); ++e) {
+    const int x0 = K0 >= 0 ? (e >> (K0 < 0 ? 0 : K0)) & 1 : 0;
+    const int x1 = K1 >= 0 ? (e >> (K1 < 0 ? 0 : K1)) & 1 : 0;
+    v[e] = v[e] + (x0 ? (x1 ? c11 : c10) : (x1 ? c01 : c00));
+  }
+}
+
+template <int RB, typename T>
+__device__ __forceinline__ void rc_diag(T (&v)[1 << RB], const ChainGate &g, const T *sB,
+                                        int64_t base) {
+  // table over (leg0, leg1); fixed legs are collapsed per thread first
+  const int s0 = (int)g.sBb[0], s1 = g.nb > 1 ? (int)g.sBb[1] : 0;
+  T c00 = sB[0], c01 = sB[s1], c10 = sB[s0], c11 = sB[s0 + s1];
+  int k0 = g.lsb[0], k1 = g.nb > 1 ? g.lsb[1] : -1;
+  if (k0 < 0) {
+    const int f = (int)((base >> g.lsbh[0]) & 1);
+    c00 = f ? c10 : c00;
+    c01 = f ? c11 : c01;
+  }
+  if (g.nb > 1 && k1 < 0) {
+    const int f = (int)((base >> g.lsbh[1]) & 1);
+    c00 = f ? c01 : c00;
+    c10 = f ? c11 : c10;
+  }
+  if (g.nb < 2) k1 = -1;
+  // after collapsing, a missing leg reads digit 0 (c00 / c10 for leg 1)
+#define RC_D(A, B) rc_diag_t<RB, A, B>(v, c00, c01, c10, c11)
+  switch ((k0 + 1) * 6 + (k1 + 1)) {
+    case 0: RC_D(-1, -1); break;
+    case 1: RC_D(-1, 0); break;
+    case 2: RC_D(-1, 1); break;
+    case 3: RC_D(-1, 2); break;
+    case 4: RC_D(-1, 3); break;
+    case 5: RC_D(-1, 4); break;
+    case 6: RC_D(0, -1); break;
+    case 8: RC_D(0, 1); break;
+    case 9: RC_D(0, 2); break;
+    case 10: RC_D(0, 3); break;
+    case 11: RC_D(0, 4); break;
+    case 12: RC_D(1, -1); break;
+    case 13: RC_D(1, 0); break;
+    case 15: RC_D(1, 2); break;
+    case 16: RC_D(1, 3); break;
+    case 17: RC_D(1, 4); break;
+    case 18: RC_D(2, -1); break;
+    case 19: RC_D(2, 0); break;
+    case 20: RC_D(2, 1); break;
+    case 22: RC_D(2, 3); break;
+    case 23: RC_D(2, 4); break;
+    case 24: RC_D(3, -1); break;
+    case 25: RC_D(3, 0); break;
+    case 26: RC_D(3, 1); break;
+    case 27: RC_D(3, 2); break;
+    case 29: RC_D(3, 4); break;
+    case 30: RC_D(4, -1); break;
+    case 31: RC_D(4, 0); break;
+    case 32: RC_D(4, 1); break;
+    case 33: RC_D(4, 2); break;
+    case 34: RC_D(4, 3); break;
+    default: break;
+  }
+#undef RC_D
+}
+
+template <typename T, int RB>
+__global__ void __launch_bounds__(256, 2) k_rchain(const ChainParams p, const T *__restrict__ X,
+                                                   const T *__restrict__ A, T *__restrict__ C) {
+  __shared__ T sB[TN_CHAIN_MAX_G * kGateBMax];
+  __shared__ int64_t soff[1 << RB];
+  load_gate_operands<T>(p, X, nullptr, sB, nullptr, kGateBMax);
+  for (int e = threadIdx.x; e < (1 << RB); e += blockDim.x) soff[e] = p.hi_off[e];
+  __syncthreads();
+  // offsets are re-read at the store instead of being kept live in registers
+  const volatile int64_t *voff = soff;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t tau = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tau < p.outer; tau += stride) {
+    int64_t r = tau, base = 0;
+    for (int sg = p.nseg - 1; sg >= 0; --sg) {
+      base += (r & (p.seg_size[sg] - 1)) * p.seg_s[sg];
+      r >>= p.seg_sh[sg];
+    }
+    T v[1 << RB];
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) v[e] = A[base + voff[e]];
+    for (int gi = 0; gi < p.ngates;) {
+      const ChainGate &g = p.g[gi];
+      if (g.kind == 1) {
+        rc_diag<RB>(v, g, sB + gi * kGateBMax, base);
+        ++gi;
+        continue;
+      }
+      int nf = 0;
+      while (nf < 2 && gi + 1 + nf < p.ngates && p.g[gi + 1 + nf].kind == 2) ++nf;
+      const T *gB = sB + gi * kGateBMax;
+      switch (g.ls) {
+        case 0: rc_replace<RB, 0>(v, &p.g[gi], nf, gB, base); break;
+        case 1: rc_replace<RB, 1>(v, &p.g[gi], nf, gB, base); break;
+        case 2: rc_replace<RB, 2>(v, &p.g[gi], nf, gB, base); break;
+        case 3: rc_replace<RB, 3>(v, &p.g[gi], nf, gB, base); break;
+        default: rc_replace<RB, RB - 1>(v, &p.g[gi], nf, gB, base); break;
+      }
+      gi += 1 + nf;
+    }
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) C[base + voff[e]] = v[e];
+  }
+}
+
+// Traceback of a register chain by one warp: lane e holds element e of the
+// 2^t elements of the fixed outer index; the gates are replayed (every
+// intermediate kept in shared memory) with the forward's operation order,
+// then lane 0 undoes each replace gate with the first-index argmax.
+template <typename T>
+__device__ void trace_rchain(const ChainTrace &ct, const T *X, int8_t *state, int *err,
+                             char *smem, int64_t *sbase) {
+  const ChainParams &p = ct.p;
+  const int E = p.tile;   // 32
+  T *buf = reinterpret_cast<T *>(smem);
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    int64_t part = 0;
+    for (int i = lane; i < ct.nout; i += 32) {
+      int d = state[ct.out_spin[i]];
+      if (d < 0 || d > 1) { *err = 1; d = 0; }
+      part += (int64_t)d * ct.out_stride[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const int64_t base = part;
+    auto digit = [&](const ChainGate &g, int k, int e) {
+      return g.lsb[k] >= 0 ? ((e >> g.lsb[k]) & 1) : (int)((base >> g.lsbh[k]) & 1);
+    };
+    for (int e = lane; e < E; e += 32) buf[e] = X[ct.offIn + base + p.hi_off[e]];
+    __syncwarp();
+    int gi = 0, slot = 0;
+    while (gi < p.ngates) {
+      const ChainGate &g = p.g[gi];
+      const T *src = buf + (int64_t)slot * E;
+      T *dst = buf + (int64_t)(slot + 1) * E;
+      const T *gB = X + g.offB;
+      if (g.kind == 1) {
+        for (int e = lane; e < E; e += 32) {
+          const int x0 = digit(g, 0, e), x1 = g.nb > 1 ? digit(g, 1, e) : 0;
+          dst[e] = src[e] + gB[x0 * g.sBb[0] + (g.nb > 1 ? x1 * g.sBb[1] : 0)];
+        }
+        __syncwarp();
+        ++gi;
+        ++slot;
+        continue;
+      }
+      int nf = 0;
+      while (nf < 2 && gi + 1 + nf < p.ngates && p.g[gi + 1 + nf].kind == 2) ++nf;
+      for (int e = lane; e < E; e += 32) {
+        if (e & (1 << g.ls)) continue;
+        const int e1 = e | (1 << g.ls);
+        const int w = g.nb > 0 ? digit(g, 0, e) : 0;
+        const int bo = w * (g.nb > 0 ? (int)g.sBb[0] : 0);
+        const T a = src[e], b = src[e1];
+        T o0 = max(a + gB[bo], b + gB[bo + g.sBk]);
+        T o1 = max(a + gB[bo + g.sBn], b + gB[bo + g.sBk + g.sBn]);
+        for (int f = 0; f < nf; ++f) {
+          const ChainGate &h = p.g[gi + 1 + f];
+          const T *hB = X + h.offB;
+          const int x = h.nb > 1 ? digit(h, 1, e) : 0;
+          const int s1 = h.nb > 1 ? x * (int)h.sBb[1] : 0;
+          o0 = o0 + hB[s1];
+          o1 = o1 + hB[(int)h.sBb[0] + s1];
+        }
+        dst[e] = o0;
+        dst[e1] = o1;
+      }
+      __syncwarp();
+      gi += 1 + nf;
+      ++slot;
+    }
+    if (lane == 0) {
+      int x = 0;
+      for (int j = 0; j < p.t; ++j) {
+        int d = state[ct.local_spin[j]];
+        if (d < 0 || d > 1) { *err = 1; d = 0; }
+        x |= d << j;
+      }
+      // walk the replace gates backwards (slot s holds the input of replace s)
+      int nslots = slot;
+      int gidx[TN_CHAIN_MAX_G];
+      int ns = 0;
+      for (int i = 0; i < p.ngates;) {
+        gidx[ns++] = i;
+        if (p.g[i].kind == 1) { ++i; continue; }
+        int nf = 0;
+        while (nf < 2 && i + 1 + nf < p.ngates && p.g[i + 1 + nf].kind == 2) ++nf;
+        i += 1 + nf;
+      }
+      (void)nslots;
+      for (int si = ns - 1; si >= 0; --si) {
+        const ChainGate &g = p.g[gidx[si]];
+        if (g.kind != 0) continue;
+        const T *src = buf + (int64_t)si * E;
+        const T *gB = X + g.offB;
+        const int v = (x >> g.ls) & 1;
+        const int x0 = x & ~(1 << g.ls);
+        const int w = g.nb > 0 ? digit(g, 0, x0) : 0;
+        const int bo = w * (g.nb > 0 ? (int)g.sBb[0] : 0);
+        const T c0 = src[x0] + gB[bo + v * g.sBn];
+        const T c1 = src[x0 | (1 << g.ls)] + gB[bo + g.sBk + v * g.sBn];
+        const int u = c1 > c0 ? 1 : 0;
+        state[g.kspin] = (int8_t)u;
+        x = x0 | (u << g.ls);
+      }
+    }
+  }
+  __syncthreads();
+  (void)sbase;
+}
+
+cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
+                          void *Cx, cudaStream_t st) {
+  if (p.outer == 0) return cudaSuccess;
+  int64_t blocks = (p.outer + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (dt == DT_F32)
+    k_rchain<float, kRegBits><<<(int)blocks, 256, 0, st>>>(
+        p, reinterpret_cast<const float *>(arena), static_cast<const float *>(Ax),
+        static_cast<float *>(Cx));
+  else
+    k_rchain<int32_t, kRegBits><<<(int)blocks, 256, 0, st>>>(
+        p, reinterpret_cast<const int32_t *>(arena), static_cast<const int32_t *>(Ax),
+        static_cast<int32_t *>(Cx));
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- traceback
 
 // Steps are processed in order (the host lists them top-down).  For each, the
 // fixed legs select the slice of A and B, the block finds the first k that
 // maximises A + B, and the contracted spins take the digits of k.
+constexpr int kTraceThreads = 1024;
+
+// (value, k) pair reduction keeping the larger value, the smaller k on ties.
 template <typename T>
-__global__ void __launch_bounds__(256) k_trace(const TraceStep *__restrict__ steps, int nsteps,
-                                               const char *__restrict__ arena, int8_t *state, int q,
-                                               int *err) {
+__device__ __forceinline__ void argmax_merge(T &v, int &k, T v2, int k2) {
+  if (k2 != 0x7fffffff && (k == 0x7fffffff || v2 > v || (v2 == v && k2 < k))) {
+    v = v2;
+    k = k2;
+  }
+}
+
+// One block walks the records in order (the host lists them top-down).  The
+// spin state lives in shared memory (`sst`) for the whole walk.  Plain
+// records: the fixed legs select a slice of A and B, the block finds the first
+// k maximising A + B and assigns the contracted spins.  Chain records:
+// trace_chain above.
+template <typename T, int Q>
+__global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceStep *__restrict__ steps,
+                                                         int nsteps,
+                                                         const ChainTrace *__restrict__ chains,
+                                                         const char *__restrict__ arena,
+                                                         int8_t *state, int nspins, int *err) {
+  extern __shared__ __align__(16) char tsmem[];
+  int8_t *sst = reinterpret_cast<int8_t *>(tsmem);
+  char *work = tsmem + ((nspins + 15) / 16) * 16;
   const T *X = reinterpret_cast<const T *>(arena);
   __shared__ int64_t sbase[2];
-  __shared__ T sv[256];
-  __shared__ int32_t sk[256];
+  __shared__ T sv[32];
+  __shared__ int sk[32];
+  __shared__ int serr;
+  if (threadIdx.x == 0) serr = 0;
+  for (int i = threadIdx.x; i < nspins; i += blockDim.x) sst[i] = state[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int s = 0; s < nsteps; ++s) {
     const TraceStep &st = steps[s];
-    if (threadIdx.x == 0) {
-      // every fixed leg was assigned by an ancestor step; an unassigned or
-      // out-of-range digit is a planning error: flag it and read index 0
-      int64_t a = st.offA, b = st.offB;
-      for (int i = 0; i < st.nfa; ++i) {
-        int d = state[st.fa_spin[i]];
-        if (d < 0 || d >= q) { *err = 1; d = 0; }
-        a += (int64_t)d * st.fa_stride[i];
+    if (st.chain >= 0) {
+      if (chains[st.chain].p.mode == 1)
+        trace_rchain<T>(chains[st.chain], X, sst, &serr, work, &sbase[0]);
+      else
+        trace_chain<T, Q>(chains[st.chain], X, sst, &serr, work, &sbase[0]);
+      continue;
+    }
+    if (warp < 2) {
+      // warp 0 sums A's fixed legs, warp 1 B's
+      const int nf = warp == 0 ? st.nfa : (st.offB >= 0 ? st.nfb : 0);
+      int64_t part = 0;
+      for (int i = lane; i < nf; i += 32) {
+        const int sp = warp == 0 ? st.fa_spin[i] : st.fb_spin[i];
+        int d = sst[sp];
+        if (d < 0 || d >= Q) { serr = 1; d = 0; }
+        part += (int64_t)d * (warp == 0 ? st.fa_stride[i] : st.fb_stride[i]);
       }
-      if (st.offB >= 0)
-        for (int i = 0; i < st.nfb; ++i) {
-          int d = state[st.fb_spin[i]];
-          if (d < 0 || d >= q) { *err = 1; d = 0; }
-          b += (int64_t)d * st.fb_stride[i];
-        }
-      sbase[0] = a;
-      sbase[1] = b;
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+      if (lane == 0) sbase[warp] = (warp == 0 ? st.offA : st.offB) + part;
     }
     __syncthreads();
     const int64_t ba = sbase[0], bb = sbase[1];
     T best = Lim<T>::neg();
-    int32_t bk = 0x7fffffff;
+    int bk = 0x7fffffff;
     for (int k = threadIdx.x; k < st.Ks; k += blockDim.x) {
       int64_t oa = ba, ob = bb;
       int r = k;
       for (int j = st.nk - 1; j >= 0; --j) {
-        int d = r % q;
-        r /= q;
+        const int d = r % Q;
+        r /= Q;
         oa += d * st.k_sA[j];
         ob += d * st.k_sB[j];
       }
       T v = X[oa];
       if (st.offB >= 0) v = v + X[ob];
-      if (bk == 0x7fffffff || v > best) { best = v; bk = k; }
+      argmax_merge(best, bk, v, k);
     }
-    sv[threadIdx.x] = best;
-    sk[threadIdx.x] = bk;
+    for (int o = 16; o > 0; o >>= 1) {
+      T v2 = __shfl_down_sync(0xffffffffu, best, o);
+      int k2 = __shfl_down_sync(0xffffffffu, bk, o);
+      argmax_merge(best, bk, v2, k2);
+    }
+    if (lane == 0) { sv[warp] = best; sk[warp] = bk; }
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) {
-        T v2 = sv[threadIdx.x + w];
-        int32_t k2 = sk[threadIdx.x + w];
-        if (k2 != 0x7fffffff &&
-            (sk[threadIdx.x] == 0x7fffffff || v2 > sv[threadIdx.x] ||
-             (v2 == sv[threadIdx.x] && k2 < sk[threadIdx.x]))) {
-          sv[threadIdx.x] = v2;
-          sk[threadIdx.x] = k2;
-        }
+    if (warp == 0) {
+      const int nw = blockDim.x / 32;
+      best = lane < nw ? sv[lane] : Lim<T>::neg();
+      bk = lane < nw ? sk[lane] : 0x7fffffff;
+      for (int o = 16; o > 0; o >>= 1) {
+        T v2 = __shfl_down_sync(0xffffffffu, best, o);
+        int k2 = __shfl_down_sync(0xffffffffu, bk, o);
+        argmax_merge(best, bk, v2, k2);
       }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      int r = sk[0];
-      for (int j = st.nk - 1; j >= 0; --j) {
-        state[st.k_spin[j]] = (int8_t)(r % q);
-        r /= q;
+      if (lane == 0) {
+        int r = bk;
+        for (int j = st.nk - 1; j >= 0; --j) {
+          sst[st.k_spin[j]] = (int8_t)(r % Q);
+          r /= Q;
+        }
       }
     }
     __syncthreads();
   }
+  for (int i = threadIdx.x; i < nspins; i += blockDim.x) state[i] = sst[i];
+  if (threadIdx.x == 0 && serr) *err = 1;
+}
+
+size_t trace_smem_bytes(const ChainParams &p, size_t elem) {
+  if (p.mode == 1) return elem * (size_t)(p.ngates + 1) * p.tile;
+  return elem * ((size_t)(p.ngates + 1) * p.tile + (size_t)TN_CHAIN_MAX_G * kGateBMax);
+}
+
+size_t trace_state_bytes(int nspins) { return ((size_t)(nspins + 15) / 16) * 16; }
+
+template <typename T, int Q>
+static cudaError_t launch_trace_t(const TraceStep *d_steps, int nsteps, const ChainTrace *chains,
+                                  size_t smem, const char *arena, int8_t *state, int nspins,
+                                  int *err, cudaStream_t st) {
+  smem += trace_state_bytes(nspins);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_trace<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  k_trace<T, Q><<<1, kTraceThreads, smem, st>>>(d_steps, nsteps, chains, arena, state, nspins,
+                                                err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_trace(Dtype dt, int q, const TraceStep *d_steps, int nsteps,
-                           const char *arena, int8_t *state, int *err, cudaStream_t st) {
+                         const ChainTrace *d_chains, size_t smem, const char *arena, int8_t *state,
+                         int nspins, int *err, cudaStream_t st) {
   if (nsteps == 0) return cudaSuccess;
   if (dt == DT_F32)
-    k_trace<float><<<1, 256, 0, st>>>(d_steps, nsteps, arena, state, q, err);
-  else
-    k_trace<int32_t><<<1, 256, 0, st>>>(d_steps, nsteps, arena, state, q, err);
-  return cudaGetLastError();
+    return q == 2 ? launch_trace_t<float, 2>(d_steps, nsteps, d_chains, smem, arena, state, nspins,
+                                             err, st)
+                  : launch_trace_t<float, 3>(d_steps, nsteps, d_chains, smem, arena, state, nspins,
+                                             err, st);
+  return q == 2 ? launch_trace_t<int32_t, 2>(d_steps, nsteps, d_chains, smem, arena, state, nspins,
+                                             err, st)
+                : launch_trace_t<int32_t, 3>(d_steps, nsteps, d_chains, smem, arena, state, nspins,
+                                             err, st);
 }
 
 // ---------------------------------------------------------------- gradient / output

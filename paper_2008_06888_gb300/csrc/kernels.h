@@ -34,8 +34,19 @@ cudaError_t launch_permute(const PermParams &p, const void *xin, void *xout, con
 
 // Argmax traceback over steps [0, nsteps) of d_steps (Sec. III).
 // *err is set to 1 if a step meets an unassigned spin (a planning error).
-cudaError_t launch_trace(Dtype dt, int q, const TraceStep *d_steps, int nsteps, const char *arena,
-                         int8_t *state, int *err, cudaStream_t st);
+// Records with chain >= 0 refer to d_chains; smem: dynamic shared memory for
+// the largest chain record (trace_smem_bytes).
+// The spin state (nspins int8) is staged in shared memory during the walk.
+cudaError_t launch_trace(Dtype dt, int q, const TraceStep *d_steps, int nsteps,
+                         const ChainTrace *d_chains, size_t smem, const char *arena, int8_t *state,
+                         int nspins, int *err, cudaStream_t st);
+size_t trace_smem_bytes(const ChainParams &p, size_t elem);
+
+// Fused gate chain over tiles of the big tensor (values; planes when P > 0).
+cudaError_t launch_chain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
+                         const uint64_t *An, void *Cx, uint64_t *Cn, const PrimeSet &ps,
+                         cudaStream_t st);
+size_t chain_smem_bytes(const ChainParams &p, size_t elem);
 
 // dE/dJ and dE/dh at the traced state.
 cudaError_t launch_grad(int q, int n, int m, const int32_t *eu, const int32_t *ev,

@@ -13,6 +13,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 
 namespace tn {
@@ -180,6 +182,9 @@ struct Builder {
       p.seg_sA[s] = sa[r];
       p.seg_sB[s] = sb[r];
       p.seg_sC[s] = sc[r];
+      p.seg_sh[s] = -1;
+      for (int b = 0; b < 62; ++b)
+        if ((int64_t(1) << b) == sz[r]) p.seg_sh[s] = b;
     }
     p.outer = ipow(q, (int)outer.size());
     p.Ks = (int)Ks;
@@ -421,8 +426,360 @@ struct Builder {
     return true;
   }
 
+  // ---- fused gate chains
+  struct CGate {
+    int kind = 0;            // 0 replace, 1 diagonal
+    int pos = -1;            // replaced position (replace)
+    int kspin = -1;
+    int btensor = -1;
+    std::vector<int> bpos;   // positions of B's legs that are legs of the state
+    int64_t sBk = 0, sBn = 0, sBb[2] = {0, 0};
+  };
+  struct Macro {
+    bool chain = false;
+    int step = -1;
+    std::vector<int> steps;
+    int in = -1, out = -1;
+    std::vector<CGate> gates;
+    std::vector<int> touched;   // positions touched by the gates
+    std::vector<int> rpos;      // positions replaced by the gates
+  };
+  std::vector<Macro> macros;
+  std::vector<int> macro_of;    // tensor -> macro producing it
+  bool fuse = true;
+  bool regmode = false;         // q == 2 values: register chains (ChainParams mode 1)
+  static constexpr int kRB = 5; // register legs of a register chain
+  bool fold_diag = false;       // apply diagonal gates inside the preceding replace gate
+  int tmax = 11, wlow = 5;
+  Macro open;
+  bool has_open = false;
+
+  int64_t tsize(int t) const { return ipow(q, (int)plan.legset[t].size()); }
+
+  // a rank-preserving step of a big tensor with a small one, as a chain gate
+  bool try_gate(const PStep &st, int big, int small, CGate *g) {
+    const std::vector<int> &ob = order[big], &os = order[small];
+    const int R = (int)ob.size();
+    if ((int)os.size() > 3 || R < (regmode ? kRB + 8 : tmax + 3)) return false;
+    const std::vector<int> &N = (big == st.a) ? st.N : st.M;
+    if (st.K.size() != N.size() || st.K.size() > 1 || st.batch.size() > 2) return false;
+    if (regmode && st.K.size() == 1 && st.batch.size() > 1) return false;
+    g->btensor = small;
+    g->bpos.clear();
+    for (int l : st.batch) g->bpos.push_back(pos_of(ob, l));
+    for (size_t j = 0; j < st.batch.size(); ++j) g->sBb[j] = stride(os, st.batch[j]);
+    if (st.K.size() == 1) {
+      g->kind = 0;
+      g->pos = pos_of(ob, st.K[0]);
+      g->kspin = st.K[0];
+      g->sBk = stride(os, st.K[0]);
+      g->sBn = stride(os, N[0]);
+    } else {
+      g->kind = 1;
+      g->pos = -1;
+      if (g->bpos.empty()) return false;
+    }
+    return true;
+  }
+
+  std::vector<int> local_set(int R, const std::vector<int> &touched) const {
+    std::vector<int> T;
+    for (int p = std::max(0, R - wlow); p < R; ++p) T.push_back(p);
+    for (int p : touched) if (pos_of(T, p) < 0) T.push_back(p);
+    std::sort(T.begin(), T.end());
+    return T;
+  }
+
+  bool fits(const Macro &m, const CGate &g) const {
+    if ((int)m.gates.size() >= TN_CHAIN_MAX_G) return false;
+    if (regmode) {
+      int n = (int)m.rpos.size();
+      if (g.kind == 0 && pos_of(m.rpos, g.pos) < 0) ++n;
+      return n <= kRB;
+    }
+    std::vector<int> t = m.touched;
+    if (g.pos >= 0) t.push_back(g.pos);
+    for (int p : g.bpos) t.push_back(p);
+    const int R = (int)order[m.in].size();
+    return (int)local_set(R, t).size() <= tmax;
+  }
+
+  void append(Macro &m, int s, const CGate &g) {
+    const PStep &st = plan.steps[s];
+    std::vector<int> ord = order[m.out];
+    if (g.kind == 0) {
+      const std::vector<int> &N = (m.out == st.a) ? st.N : st.M;
+      ord[g.pos] = N[0];
+      m.touched.push_back(g.pos);
+      if (pos_of(m.rpos, g.pos) < 0) m.rpos.push_back(g.pos);
+    }
+    for (int p : g.bpos) m.touched.push_back(p);
+    std::sort(m.touched.begin(), m.touched.end());
+    m.touched.erase(std::unique(m.touched.begin(), m.touched.end()), m.touched.end());
+    m.gates.push_back(g);
+    m.steps.push_back(s);
+    m.out = st.c;
+    order[st.c] = ord;
+    const int R = (int)ord.size();
+    pr.macs += (double)ipow(q, R) * (g.kind == 0 ? q : 1);
+  }
+
+  // register legs of a register chain: the replaced positions (fastest
+  // first), padded with the slowest positions to kRB legs
+  std::vector<int> reg_legs(const Macro &m) const {
+    std::vector<int> S = m.rpos;
+    std::sort(S.begin(), S.end(), [](int x, int y) { return x > y; });
+    for (int p = 0; (int)S.size() < kRB; ++p)
+      if (pos_of(S, p) < 0) S.push_back(p);
+    return S;
+  }
+
+  ChainParams reg_chain_params(const Macro &m, std::vector<Loc> *blocs) {
+    ChainParams cp{};
+    const std::vector<int> &ord = order[m.out];
+    const int R = (int)ord.size();
+    std::vector<int> S = reg_legs(m);
+    cp.mode = 1;
+    cp.q = 2;
+    cp.t = kRB;
+    cp.tile = 1 << kRB;
+    for (int e = 0; e < cp.tile; ++e) {
+      int64_t off = 0;
+      for (int j = 0; j < kRB; ++j)
+        if (e >> j & 1) off += int64_t(1) << (R - 1 - S[j]);
+      cp.hi_off[e] = off;
+    }
+    std::vector<int64_t> sz, st;
+    std::vector<int> sh;
+    for (int p = 0; p < R; ++p) {
+      if (pos_of(S, p) >= 0) continue;
+      const int64_t sp = int64_t(1) << (R - 1 - p);
+      if (!sz.empty() && p > 0 && pos_of(S, p - 1) < 0) {
+        sz.back() *= 2;
+        st.back() = sp;
+        sh.back()++;
+      } else {
+        sz.push_back(2);
+        st.push_back(sp);
+        sh.push_back(1);
+      }
+    }
+    cp.nseg = (int)sz.size();
+    cp.outer = int64_t(1) << (R - kRB);
+    for (int i = 0; i < cp.nseg; ++i) {
+      cp.seg_size[i] = sz[i];
+      cp.seg_s[i] = st[i];
+      cp.seg_sh[i] = sh[i];
+    }
+    cp.ngates = (int)m.gates.size();
+    blocs->clear();
+    int last_replace = -1, nfold = 0;
+    for (int i = 0; i < cp.ngates; ++i) {
+      const CGate &g = m.gates[i];
+      ChainGate &c = cp.g[i];
+      c.kind = g.kind;
+      c.ls = g.kind == 0 ? pos_of(S, g.pos) : 0;
+      c.nb = (int)g.bpos.size();
+      for (int j = 0; j < c.nb; ++j) {
+        c.lsb[j] = pos_of(S, g.bpos[j]);
+        c.lsbh[j] = R - 1 - g.bpos[j];
+        c.sBb[j] = g.sBb[j];
+      }
+      // a diagonal gate right after a replace gate on one of its legs is
+      // applied inside that gate (same additions in the same order)
+      if (fold_diag && g.kind == 1 && last_replace >= 0 && nfold < 2) {
+        const int rp = m.gates[last_replace].pos;
+        const int k = pos_of(g.bpos, rp);
+        if (k >= 0) {
+          c.kind = 2;
+          if (k == 1) {
+            std::swap(c.lsb[0], c.lsb[1]);
+            std::swap(c.lsbh[0], c.lsbh[1]);
+            std::swap(c.sBb[0], c.sBb[1]);
+          }
+          ++nfold;
+        }
+      }
+      if (c.kind == 0) {
+        last_replace = i;
+        nfold = 0;
+      } else if (c.kind == 1) {
+        last_replace = -1;
+      }
+      c.kspin = g.kspin;
+      c.sBk = g.sBk;
+      c.sBn = g.sBn;
+      c.nBel = (int)tsize(g.btensor);
+      blocs->push_back(loc[g.btensor]);
+    }
+    cp.P = 0;
+    return cp;
+  }
+
+  ChainParams chain_params(const Macro &m, std::vector<Loc> *blocs) {
+    if (regmode) return reg_chain_params(m, blocs);
+    ChainParams cp{};
+    const std::vector<int> &ord = order[m.out];
+    const int R = (int)ord.size();
+    std::vector<int> T = local_set(R, m.touched);
+    cp.q = q;
+    cp.t = (int)T.size();
+    cp.tile = (int)ipow(q, cp.t);
+    int w = std::min(R, wlow);
+    cp.lo = (int)ipow(q, w);
+    cp.nhi = cp.tile / cp.lo;
+    cp.loh = 0;
+    while ((1 << cp.loh) < cp.lo) ++cp.loh;
+    std::vector<int> H(T.begin(), T.end() - w);
+    for (int h = 0; h < cp.nhi; ++h) {
+      int64_t r = h, off = 0;
+      for (int j = (int)H.size() - 1; j >= 0; --j) {
+        off += (r % q) * ipow(q, R - 1 - H[j]);
+        r /= q;
+      }
+      cp.hi_off[h] = off;
+    }
+    // outer positions, merged into runs
+    std::vector<int64_t> sz, st;
+    for (int p = 0; p < R; ++p) {
+      if (pos_of(T, p) >= 0) continue;
+      const int64_t sp = ipow(q, R - 1 - p);
+      if (!sz.empty() && st.back() == sp * q && p > 0 && pos_of(T, p - 1) < 0) {
+        sz.back() *= q;
+        st.back() = sp;
+      } else {
+        sz.push_back(q);
+        st.push_back(sp);
+      }
+    }
+    cp.nseg = (int)sz.size();
+    cp.outer = 1;
+    for (int i = 0; i < cp.nseg; ++i) {
+      cp.seg_size[i] = sz[i];
+      cp.seg_s[i] = st[i];
+      cp.seg_sh[i] = 0;
+      while ((int64_t(1) << cp.seg_sh[i]) < sz[i]) cp.seg_sh[i]++;
+      cp.outer *= sz[i];
+    }
+    auto lstride = [&](int p) { return (int)ipow(q, cp.t - 1 - pos_of(T, p)); };
+    auto lg = [](int x) { int r = 0; while ((1 << r) < x) ++r; return r; };
+    cp.ngates = (int)m.gates.size();
+    blocs->clear();
+    for (int i = 0; i < cp.ngates; ++i) {
+      const CGate &g = m.gates[i];
+      ChainGate &c = cp.g[i];
+      c.kind = g.kind;
+      c.ls = g.kind == 0 ? lstride(g.pos) : 1;
+      c.lsh = lg(c.ls);
+      c.nb = (int)g.bpos.size();
+      for (int j = 0; j < c.nb; ++j) {
+        c.lsb[j] = lstride(g.bpos[j]);
+        c.lsbh[j] = lg(c.lsb[j]);
+        c.sBb[j] = g.sBb[j];
+      }
+      c.kspin = g.kspin;
+      c.sBk = g.sBk;
+      c.sBn = g.sBn;
+      c.nBel = (int)tsize(g.btensor);
+      blocs->push_back(loc[g.btensor]);
+    }
+    cp.P = P;
+    return cp;
+  }
+
+  void emit_chain(const Macro &m) {
+    std::vector<Loc> bl;
+    ChainParams cp = chain_params(m, &bl);
+    Loc out = new_tensor(tsize(m.out));
+    cp.planeA = loc[m.in].plane;
+    cp.planeC = out.plane;
+    pr.chains.push_back(cp);
+    pr.chain_blocs.push_back(bl);
+    Op op;
+    op.kind = OP_CHAIN;
+    op.in0 = loc[m.in];
+    op.out = out;
+    op.idx = (int)pr.chains.size() - 1;
+    op.macs = 0;
+    for (auto &g : m.gates) op.macs += (double)tsize(m.in) * (g.kind == 0 ? q : 1);
+    int oi = push(op);
+    for (auto &l : bl) use(l, oi);
+    pr.n_chain++;
+    pr.n_chain_gates += (int)m.gates.size();
+    loc[m.out] = out;
+  }
+
+  void flush_chain() {
+    if (!has_open) return;
+    emit_chain(open);
+    macros.push_back(open);
+    macro_of[open.out] = (int)macros.size() - 1;
+    has_open = false;
+  }
+
+  bool forward() {
+    macro_of.assign(plan.legset.size(), -1);
+    for (int s = 0; s < (int)plan.steps.size(); ++s) {
+      const PStep &st = plan.steps[s];
+      if (fuse && st.b >= 0) {
+        CGate g;
+        if (has_open && (st.a == open.out || st.b == open.out)) {
+          int small = st.a == open.out ? st.b : st.a;
+          if (try_gate(st, open.out, small, &g) && fits(open, g)) {
+            append(open, s, g);
+            continue;
+          }
+          flush_chain();
+        }
+        int big = tsize(st.a) >= tsize(st.b) ? st.a : st.b;
+        int small = big == st.a ? st.b : st.a;
+        if (try_gate(st, big, small, &g)) {
+          flush_chain();
+          open = Macro();
+          open.chain = true;
+          open.in = open.out = big;
+          if (fits(open, g)) {
+            append(open, s, g);
+            has_open = true;
+            continue;
+          }
+        }
+      }
+      if (has_open && (st.a == open.out || st.b == open.out)) flush_chain();
+      if (!emit_step(s)) return false;
+      Macro m;
+      m.step = s;
+      m.out = st.c;
+      macros.push_back(m);
+      macro_of[st.c] = (int)macros.size() - 1;
+    }
+    flush_chain();
+    return true;
+  }
+
+  std::vector<int> macro_inputs(const Macro &m) const {
+    std::vector<int> r;
+    if (m.chain) {
+      r.push_back(m.in);
+      for (auto &g : m.gates) r.push_back(g.btensor);
+    } else {
+      const PStep &st = plan.steps[m.step];
+      r.push_back(st.a);
+      if (st.b >= 0) r.push_back(st.b);
+    }
+    return r;
+  }
+
+  bool emit_macro(const Macro &m) {
+    if (m.chain) {
+      emit_chain(m);
+      return true;
+    }
+    return emit_step(m.step);
+  }
+
   // ---- traceback
-  std::vector<int> pending;
+  std::vector<int> pending;   // macros
   void flush_trace() {
     if (pending.empty()) return;
     Op op;
@@ -431,9 +788,37 @@ struct Builder {
     op.trace_n = (int)pending.size();
     pr.ops.push_back(op);
     int oi = (int)pr.ops.size() - 1;
-    for (int s : pending) {
-      const PStep &st = plan.steps[s];
+    for (int mi : pending) {
+      const Macro &m = macros[mi];
       TraceStep t{};
+      t.chain = -1;
+      if (m.chain) {
+        ChainTrace ct{};
+        std::vector<Loc> bl;
+        ct.p = chain_params(m, &bl);
+        const std::vector<int> &ord = order[m.out];
+        const int R = (int)ord.size();
+        std::vector<int> T = regmode ? reg_legs(m) : local_set(R, m.touched);
+        for (int p = 0; p < R; ++p) {
+          if (pos_of(T, p) >= 0) continue;
+          ct.out_spin[ct.nout] = ord[p];
+          ct.out_stride[ct.nout] = ipow(q, R - 1 - p);
+          ct.nout++;
+        }
+        for (int j = 0; j < (int)T.size(); ++j) ct.local_spin[j] = ord[T[j]];
+        t.chain = (int)pr.chain_traces.size();
+        pr.chain_traces.push_back(ct);
+        pr.ctrace_in.push_back(loc[m.in]);
+        pr.ctrace_blocs.push_back(bl);
+        pr.trace_smem = std::max(pr.trace_smem, trace_smem_bytes(ct.p, 4));
+        use(loc[m.in], oi);
+        for (auto &l : bl) use(l, oi);
+        pr.trace.push_back(t);
+        pr.traceA.push_back(Loc());
+        pr.traceB.push_back(Loc());
+        continue;
+      }
+      const PStep &st = plan.steps[m.step];
       const std::vector<int> &oa = order[st.a];
       std::vector<int> K = k_order(oa, st.K);
       t.nk = (int)K.size();
@@ -467,47 +852,47 @@ struct Builder {
 
   std::vector<char> avail;
   bool recompute(int t) {
-    int p = plan.producer[t];
-    const PStep &st = plan.steps[p];
-    if (!avail[st.a] && !recompute(st.a)) return false;
-    if (st.b >= 0 && !avail[st.b] && !recompute(st.b)) return false;
-    if (!emit_step(p)) return false;
+    const int mi = macro_of[t];
+    if (mi < 0) { err = "recompute: tensor has no producer"; return false; }
+    const Macro &m = macros[mi];
+    for (int x : macro_inputs(m))
+      if (!avail[x] && !recompute(x)) return false;
+    if (!emit_macro(m)) return false;
     pr.n_recompute++;
     avail[t] = 1;
     return true;
   }
 
   bool build(ProgMode mode, int64_t seg_bytes) {
+    fuse = std::getenv("TN_NO_FUSION") == nullptr;
+    regmode = q == 2 && P == 0 && std::getenv("TN_TILE_CHAINS") == nullptr;
+    if (q == 3) { tmax = 7; wlow = 4; }
     emit_leaves();
-    const int S = (int)plan.steps.size();
-    std::vector<char> stored(plan.legset.size(), 0);
-    for (int i = 0; i < plan.n_leaves; ++i) stored[i] = 1;
-    if (mode == PM_CONFIG) {
-      std::vector<int64_t> acc(plan.legset.size(), 0);
-      for (int s = 0; s < S; ++s) {
-        const PStep &st = plan.steps[s];
-        int64_t a = ipow(q, (int)plan.legset[st.c].size()) * 4;
-        if (!stored[st.a]) a += acc[st.a];
-        if (st.b >= 0 && !stored[st.b]) a += acc[st.b];
-        acc[st.c] = a;
-        if (seg_bytes <= 0 || a > seg_bytes || st.c == plan.root) stored[st.c] = 1;
-      }
-    }
-    for (int s = 0; s < S; ++s)
-      if (!emit_step(s)) return false;
+    if (!forward()) return false;
     pr.root = loc[plan.root];
     pr.fwd_end = (int)pr.ops.size();
     if (mode == PM_CONFIG) {
-      // keep the root alive to the end
+      std::vector<char> stored(plan.legset.size(), 0);
+      for (int i = 0; i < plan.n_leaves; ++i) stored[i] = 1;
+      std::vector<int64_t> acc(plan.legset.size(), 0);
+      for (const Macro &m : macros) {
+        int64_t a = tsize(m.out) * 4;
+        for (int x : macro_inputs(m))
+          if (!stored[x]) a += acc[x];
+        acc[m.out] = a;
+        if (seg_bytes <= 0 || a > seg_bytes || m.out == plan.root || tsize(m.out) <= 4096)
+          stored[m.out] = 1;
+      }
       avail = stored;
-      for (int s = S - 1; s >= 0; --s) {
-        const PStep &st = plan.steps[s];
-        if (!avail[st.a] || (st.b >= 0 && !avail[st.b])) {
+      for (int mi = (int)macros.size() - 1; mi >= 0; --mi) {
+        bool need = false;
+        for (int x : macro_inputs(macros[mi])) need = need || !avail[x];
+        if (need) {
           flush_trace();
-          if (!avail[st.a] && !recompute(st.a)) return false;
-          if (st.b >= 0 && !avail[st.b] && !recompute(st.b)) return false;
+          for (int x : macro_inputs(macros[mi]))
+            if (!avail[x] && !recompute(x)) return false;
         }
-        pending.push_back(s);
+        pending.push_back(mi);
       }
       flush_trace();
     }
@@ -562,6 +947,40 @@ bool build_program(const Net &net, const Plan &plan, ProgMode mode, Dtype dt, in
     return false;
   }
   plan_memory(*pr);
+  if (const char *dump = std::getenv("TN_DUMP_PROGRAM")) {
+    if (*dump == '1') {
+      for (size_t i = 0; i < pr->ops.size(); ++i) {
+        const Op &o = pr->ops[i];
+        std::fprintf(stderr, "op %zu kind %d in0 %lld in1 %lld out %lld", i, (int)o.kind,
+                     (long long)(o.in0.buf >= 0 ? o.in0.plane : -1),
+                     (long long)(o.in1.buf >= 0 ? o.in1.plane : -1),
+                     (long long)(o.out.buf >= 0 ? o.out.plane : -1));
+        if (o.kind == OP_GATE) {
+          const GateParams &g = pr->gates[o.idx];
+          std::fprintf(stderr, " outer %lld Ks %d Ns %d nseg %d inA %d outA %d", (long long)g.outer,
+                       g.Ks, g.Ns, g.nseg, o.in0.buf, o.out.buf);
+          for (int s2 = 0; s2 < g.nseg; ++s2)
+            std::fprintf(stderr, " [%lld:%lld,%lld,%lld]", (long long)g.seg_size[s2],
+                         (long long)g.seg_sA[s2], (long long)g.seg_sB[s2], (long long)g.seg_sC[s2]);
+          std::fprintf(stderr, " kA");
+          for (int k = 0; k < g.Ks; ++k) std::fprintf(stderr, " %lld", (long long)g.kA[k]);
+        }
+        if (o.kind == OP_CHAIN) {
+          const ChainParams &c = pr->chains[o.idx];
+          std::fprintf(stderr, " chain mode %d outer %lld t %d gates", c.mode, (long long)c.outer, c.t);
+          for (int g = 0; g < c.ngates; ++g)
+            std::fprintf(stderr, " (%d,%d,%d,%d,%d)", c.g[g].kind, c.g[g].ls, c.g[g].nb, c.g[g].lsb[0],
+                         c.g[g].nb > 1 ? c.g[g].lsb[1] : 9);
+        }
+        if (o.kind == OP_GEMM) {
+          const GemmParams &g = pr->gemms[o.idx];
+          std::fprintf(stderr, " b %lld M %lld N %lld K %lld", (long long)g.batch, (long long)g.M,
+                       (long long)g.N, (long long)g.K);
+        }
+        std::fprintf(stderr, "\n");
+      }
+    }
+  }
   // absolute offsets of leaves and traceback operands
   const int64_t lbase = pr->bufs[pr->leaves_loc.buf].off;
   for (int i = 0; i < plan.n_leaves; ++i) {
@@ -588,8 +1007,21 @@ bool build_program(const Net &net, const Plan &plan, ProgMode mode, Dtype dt, in
     pr->leaves.push_back(d);
   }
   for (size_t i = 0; i < pr->trace.size(); ++i) {
+    if (pr->trace[i].chain >= 0) continue;
     pr->trace[i].offA = abs_off(*pr, pr->traceA[i]) / 4;
     pr->trace[i].offB = pr->traceB[i].buf >= 0 ? abs_off(*pr, pr->traceB[i]) / 4 : -1;
+  }
+  auto patch = [&](ChainParams &cp, const std::vector<Loc> &bl) {
+    for (int g = 0; g < cp.ngates; ++g) {
+      cp.g[g].offB = abs_off(*pr, bl[g]) / 4;
+      cp.g[g].offBn = (pr->bufs[bl[g].buf].off + bl[g].noff) / 8;
+      cp.g[g].planeB = bl[g].plane;
+    }
+  };
+  for (size_t i = 0; i < pr->chains.size(); ++i) patch(pr->chains[i], pr->chain_blocs[i]);
+  for (size_t i = 0; i < pr->chain_traces.size(); ++i) {
+    patch(pr->chain_traces[i].p, pr->ctrace_blocs[i]);
+    pr->chain_traces[i].offIn = abs_off(*pr, pr->ctrace_in[i]) / 4;
   }
   return true;
 }

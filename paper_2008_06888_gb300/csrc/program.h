@@ -24,7 +24,7 @@ struct BufInfo {
   int64_t off = -1;
 };
 
-enum OpKind { OP_LEAVES, OP_PERM, OP_GATE, OP_GEMM, OP_TRACE };
+enum OpKind { OP_LEAVES, OP_PERM, OP_GATE, OP_GEMM, OP_TRACE, OP_CHAIN };
 
 struct Op {
   OpKind kind;
@@ -45,6 +45,12 @@ struct Program {
   std::vector<GateParams> gates;
   std::vector<GemmParams> gemms;
   std::vector<PermParams> perms;
+  std::vector<ChainParams> chains;                  // fused gate chains
+  std::vector<std::vector<Loc>> chain_blocs;        // their gate operands
+  std::vector<ChainTrace> chain_traces;             // traceback records of chains
+  std::vector<Loc> ctrace_in;
+  std::vector<std::vector<Loc>> ctrace_blocs;
+  size_t trace_smem = 0;                            // dynamic smem of the trace kernel
   std::vector<LeafDesc> leaves;      // offsets absolute after planning
   std::vector<TraceStep> trace;      // offsets absolute after planning
   std::vector<Loc> traceA, traceB;
@@ -53,11 +59,19 @@ struct Program {
   Loc root;
   int64_t arena_bytes = 0;
   int fwd_end = 0;                   // ops [0, fwd_end) are the forward pass
-  int n_transposes = 0, n_gate = 0, n_gemm = 0, n_recompute = 0;
+  int n_transposes = 0, n_gate = 0, n_gemm = 0, n_recompute = 0, n_chain = 0, n_chain_gates = 0;
   double macs = 0;                   // tropical multiply-adds of the forward steps
+  // CUDA graphs of op ranges, captured on the second run of a range
+  struct Graph {
+    int begin, end, runs;
+    const char *arena;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
   // device copies (owned by the context)
   LeafDesc *d_leaves = nullptr;
   TraceStep *d_trace = nullptr;
+  ChainTrace *d_chain_traces = nullptr;
 };
 
 // Build the program for a plan.  seg_bytes: traceback checkpoint segment

@@ -23,6 +23,7 @@ struct GateParams {
   int64_t seg_sA[TN_MAX_SEG];
   int64_t seg_sB[TN_MAX_SEG];    // 0 for M legs (B does not have them)
   int64_t seg_sC[TN_MAX_SEG];
+  int32_t seg_sh[TN_MAX_SEG];    // log2(seg_size) when every size is a power of two, else -1
   int Ks, Ns;
   int hasB;                      // 0: unary reduction, B == tropical one (0)
   int64_t kA[TN_GATE_MAX_K];
@@ -70,6 +71,7 @@ struct LeafDesc {
 // output index is already fixed picks the first k maximising A + B and
 // assigns the contracted spins.
 struct TraceStep {
+  int32_t chain;               // >= 0: this record is ChainTrace[chain]
   int64_t offA, offB;          // element offsets (offB < 0: unary, B == 0)
   int32_t nfa, nfb, nk;        // fixed legs of A, of B; contracted legs
   int32_t Ks;                  // q^nk
@@ -80,6 +82,68 @@ struct TraceStep {
   int32_t k_spin[TN_MAX_TRACE_LEGS];
   int64_t k_sA[TN_MAX_TRACE_LEGS];
   int64_t k_sB[TN_MAX_TRACE_LEGS];
+};
+
+// ---- fused gate chains
+// A chain applies G consecutive rank-preserving gate contractions to one big
+// tensor in a single pass: the tensor is cut into tiles over a set of t
+// "local" legs (the q^w fastest legs, for coalescing, plus every leg a gate
+// touches); each CTA loads a tile into shared memory, applies the gates in
+// order and writes it back.  A replace gate contracts the leg at local stride
+// ls and puts the new leg in its place: C[.., v, ..] = max_u A[.., u, ..] +
+// B[u, v, b..]; a diagonal gate adds B[b..] (all of B's legs are legs of A).
+#define TN_CHAIN_MAX_G 20
+#define TN_CHAIN_MAX_T 12
+#define TN_CHAIN_MAX_HI 128
+
+struct ChainGate {
+  int32_t kind;      // 0 replace, 1 diagonal
+  int32_t ls;        // local stride of the replaced leg (replace)
+  int32_t nb;        // B legs that are legs of the tile (0..2)
+  int32_t lsb[2];    // their local strides
+  int32_t kspin;     // contracted spin (replace), for the traceback
+  int32_t lsh;       // log2(ls) when q == 2
+  int32_t lsbh[2];   // log2(lsb) when q == 2
+  int32_t nBel;      // elements of B
+  int64_t offB;      // element offset of B's values in the arena
+  int64_t offBn;     // u64 offset of B's residue plane 0 in the arena (counting)
+  int64_t planeB;    // elements between B's residue planes
+  int64_t sBk, sBn;  // B strides of the contracted and of the new leg
+  int64_t sBb[2];    // B strides of the tile legs
+};
+
+// mode 1 (q = 2 only, "register chains"): every thread owns the 2^t elements
+// that differ in the chain's replaced legs (the register legs; t = RB); the
+// replace gate's ls is a register-bit index, a B leg is a register bit
+// (lsb >= 0) or a leg fixed per thread (lsb < 0, digit = (base >> lsbh) & 1);
+// hi_off[e] is the state offset of register index e, seg_* decode the thread
+// index over the other legs.
+struct ChainParams {
+  int32_t mode;            // 0: shared-memory tiles, 1: register chains
+  int32_t q, t, tile;      // tile = q^t elements
+  int32_t lo, nhi;         // tile = nhi * lo; lo = q^w contiguous elements
+  int32_t loh;             // log2(lo) when q == 2
+  int32_t nseg, ngates;
+  int32_t P;               // residue planes (0 = values only)
+  int64_t outer;           // number of tiles
+  int64_t hi_off[TN_CHAIN_MAX_HI];
+  int64_t seg_size[TN_MAX_SEG];
+  int64_t seg_s[TN_MAX_SEG];
+  int32_t seg_sh[TN_MAX_SEG];  // log2(seg_size) when q == 2
+  int64_t planeA, planeC;  // plane distances of input and output
+  ChainGate g[TN_CHAIN_MAX_G];
+};
+
+// Traceback record of a chain: the tile of the chain input selected by the
+// (already fixed) spins on the outer legs is recomputed gate by gate in
+// shared memory, then walked backwards to fix each contracted spin.
+struct ChainTrace {
+  int64_t offIn;                       // element offset of the chain input
+  int32_t nout;                        // outer legs
+  int32_t out_spin[TN_MAX_TRACE_LEGS];
+  int64_t out_stride[TN_MAX_TRACE_LEGS];
+  int32_t local_spin[TN_CHAIN_MAX_T];  // spin on each local leg after the chain (slowest first)
+  ChainParams p;
 };
 
 // 61-bit pseudo-Mersenne primes p = 2^61 - c (reduction after Crandall).

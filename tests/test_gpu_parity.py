@@ -343,3 +343,46 @@ def test_full_potts12_counts():
     sg = P.SpinGlass(inst, order="sweep", seq=I.square_sweep_order(12))
     c, _, E = sg.count(3)
     assert close(E, exp["E"]) and c == int(exp["count"])
+
+
+# ------------------------------------------------------------ fused gate chains
+
+@pytest.mark.parametrize("kind", ["square16_gauss_h", "square15_pm", "potts9_gauss"])
+def test_fused_chains_match_unfused_exactly(kind, monkeypatch):
+    inst = {"square16_gauss_h": lambda: I.square_lattice(16, coupling="gauss", field_sigma=0.1,
+                                                         seed=4),
+            "square15_pm": lambda: I.square_lattice(15, coupling="pm1", seed=4),
+            "potts9_gauss": lambda: I.potts_square(9, seed=4)}[kind]()
+    counts = inst["q"] == 3 or kind.endswith("pm")
+    sg = P.SpinGlass(inst, order="greedy", seed=3)
+    res_f = (sg.energy(), tuple(sg.config()[0]), sg.count(3)[0] if counts else None)
+    monkeypatch.setenv("TN_NO_FUSION", "1")
+    sg2 = P.SpinGlass(inst, order="greedy", seed=3)
+    res_u = (sg2.energy(), tuple(sg2.config()[0]), sg2.count(3)[0] if counts else None)
+    assert res_f == res_u
+
+
+def test_fused_chain_recompute_path(monkeypatch):
+    inst = I.square_lattice(16, coupling="gauss", field_sigma=0.1, seed=6)
+    a = P.SpinGlass(inst, order="greedy", seed=2)
+    sa, Ea = a.config()
+    monkeypatch.setenv("TN_CKPT_SEGMENT_BYTES", str(1 << 20))
+    b = P.SpinGlass(inst, order="greedy", seed=2)
+    sb, Eb = b.config()
+    assert Ea == Eb and np.array_equal(sa, sb)
+    o = O.solve(inst, order=I.square_sweep_order(16), count=False)
+    assert close(Ea, o["E"])
+    assert np.array_equal(P.SpinGlass.state_indices(sa, 2), o["state"])
+
+
+def test_repeated_calls_replay_graphs_identically():
+    inst = I.square_lattice(14, coupling="pm1", seed=12)
+    sg = P.SpinGlass(inst, order="greedy", seed=1)
+    first = (sg.energy(), tuple(sg.config()[0]), sg.count(3))
+    for _ in range(3):                       # eager, then capture, then replay
+        assert (sg.energy(), tuple(sg.config()[0]), sg.count(3)) == first
+    J2 = -inst["J"]
+    sg.set_couplings(J=J2)
+    o = O.solve(dict(inst, J=J2), order=I.square_sweep_order(14))
+    c, _, E = sg.count(3)
+    assert (sg.energy(), E, c) == (o["E"], o["E"], o["count"])

@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--mode", default="config", choices=["config", "energy"],
                     help="config: E_min + sigma* (the workload); energy: E_min only (profiling)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--quiet", action="store_true", help="print only value and kernel shares")
     return ap.parse_args()
 
 

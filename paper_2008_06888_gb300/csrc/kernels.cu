@@ -694,12 +694,10 @@ __device__ void trace_chain(const ChainTrace &ct, const T *X, int8_t *state, int
 // ---------------------------------------------------------------- register chains (q = 2)
 //
 // Gate kinds in a register chain: 0 replace on register bit J = ls, whose B
-// may depend on one more leg (nb = 1); 2 a diagonal gate folded into the
-// replace gate just before it (its leg 0 is the replaced leg, leg 1 optional);
-// 1 a diagonal gate applied on its own.  A leg is a register bit (lsb >= 0)
-// or fixed per thread (digit = (base >> lsbh) & 1).
+// may depend on one more leg (nb = 1); 1 a diagonal gate on one or two legs.
+// A leg is a register bit (lsb >= 0) or fixed per thread (digit =
+// (base >> lsbh) & 1).
 
-constexpr int kRegBits = 5;   // every thread owns 2^5 elements
 
 // mask / fixed-digit form of leg k: digit(e) = ((e & mask) != 0) | fixed
 __device__ __forceinline__ void leg_sel(const ChainGate &g, int k, int64_t base, int *mask,
@@ -714,49 +712,32 @@ __device__ __forceinline__ void leg_sel(const ChainGate &g, int k, int64_t base,
 }
 
 template <int RB, int J, typename T>
-__device__ __forceinline__ void rc_replace(T (&v)[1 << RB], const ChainGate *gs, int nfold,
-                                           const T *sB, int64_t base) {
-  const ChainGate &g = gs[0];
-  // B of the replace gate for each digit w of its extra leg
+__device__ __forceinline__ void rc_replace(T (&v)[1 << RB], const ChainGate &g, const T *sB,
+                                           int64_t base) {
+  // B of the replace gate for each digit w of its optional extra leg
   const int wl = g.nb > 0 ? (int)g.sBb[0] : 0;
   int wm = 0, wf = 0;
   if (g.nb > 0) leg_sel(g, 0, base, &wm, &wf);
   const T a00 = sB[0], a01 = sB[g.sBn], a10 = sB[g.sBk], a11 = sB[g.sBk + g.sBn];
-  const T b00 = sB[wl], b01 = sB[wl + g.sBn], b10 = sB[wl + g.sBk], b11 = sB[wl + g.sBk + g.sBn];
-  // folded diagonal gates: value d[v][x], x the digit of their second leg
-  T d[2][2][2];
-  int dm[2] = {0, 0}, df[2] = {0, 0};
+  if (g.nb == 0) {
 #pragma unroll
-  for (int f = 0; f < 2; ++f) {
-    if (f < nfold) {
-      const ChainGate &h = gs[1 + f];
-      const T *hB = sB + (1 + f) * kGateBMax;
-      const int s0 = (int)h.sBb[0], s1 = h.nb > 1 ? (int)h.sBb[1] : 0;
-      if (h.nb > 1) leg_sel(h, 1, base, &dm[f], &df[f]);
-      d[f][0][0] = hB[0];
-      d[f][0][1] = hB[s1];
-      d[f][1][0] = hB[s0];
-      d[f][1][1] = hB[s0 + s1];
+    for (int e = 0; e < (1 << RB); ++e) {
+      if (e & (1 << J)) continue;
+      const T a = v[e], b = v[e | (1 << J)];
+      v[e] = max(a + a00, b + a10);
+      v[e | (1 << J)] = max(a + a01, b + a11);
     }
+    return;
   }
+  const T b00 = sB[wl], b01 = sB[wl + g.sBn], b10 = sB[wl + g.sBk], b11 = sB[wl + g.sBk + g.sBn];
 #pragma unroll
   for (int e = 0; e < (1 << RB); ++e) {
     if (e & (1 << J)) continue;
     const int w = ((e & wm) != 0) | wf;
     const T m00 = w ? b00 : a00, m01 = w ? b01 : a01, m10 = w ? b10 : a10, m11 = w ? b11 : a11;
     const T a = v[e], b = v[e | (1 << J)];
-    T o0 = max(a + m00, b + m10);
-    T o1 = max(a + m01, b + m11);
-#pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      if (f < nfold) {
-        const int x = ((e & dm[f]) != 0) | df[f];
-        o0 = o0 + (x ? d[f][0][1] : d[f][0][0]);
-        o1 = o1 + (x ? d[f][1][1] : d[f][1][0]);
-      }
-    }
-    v[e] = o0;
-    v[e | (1 << J)] = o1;
+    v[e] = max(a + m00, b + m10);
+    v[e | (1 << J)] = max(a + m01, b + m11);
   }
 }
 
@@ -831,7 +812,7 @@ __device__ __forceinline__ void rc_diag(T (&v)[1 << RB], const ChainGate &g, con
 }
 
 template <typename T, int RB>
-__global__ void __launch_bounds__(256, 2) k_rchain(const ChainParams p, const T *__restrict__ X,
+__global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainParams p, const T *__restrict__ X,
                                                    const T *__restrict__ A, T *__restrict__ C) {
   __shared__ T sB[TN_CHAIN_MAX_G * kGateBMax];
   __shared__ int64_t soff[1 << RB];
@@ -850,24 +831,20 @@ __global__ void __launch_bounds__(256, 2) k_rchain(const ChainParams p, const T 
     T v[1 << RB];
 #pragma unroll
     for (int e = 0; e < (1 << RB); ++e) v[e] = A[base + voff[e]];
-    for (int gi = 0; gi < p.ngates;) {
+    for (int gi = 0; gi < p.ngates; ++gi) {
       const ChainGate &g = p.g[gi];
-      if (g.kind == 1) {
-        rc_diag<RB>(v, g, sB + gi * kGateBMax, base);
-        ++gi;
+      const T *gB = sB + gi * kGateBMax;
+      if (g.kind != 0) {
+        rc_diag<RB>(v, g, gB, base);
         continue;
       }
-      int nf = 0;
-      while (nf < 2 && gi + 1 + nf < p.ngates && p.g[gi + 1 + nf].kind == 2) ++nf;
-      const T *gB = sB + gi * kGateBMax;
       switch (g.ls) {
-        case 0: rc_replace<RB, 0>(v, &p.g[gi], nf, gB, base); break;
-        case 1: rc_replace<RB, 1>(v, &p.g[gi], nf, gB, base); break;
-        case 2: rc_replace<RB, 2>(v, &p.g[gi], nf, gB, base); break;
-        case 3: rc_replace<RB, 3>(v, &p.g[gi], nf, gB, base); break;
-        default: rc_replace<RB, RB - 1>(v, &p.g[gi], nf, gB, base); break;
+        case 0: rc_replace<RB, 0>(v, g, gB, base); break;
+        case 1: rc_replace<RB, 1>(v, g, gB, base); break;
+        case 2: rc_replace<RB, 2>(v, g, gB, base); break;
+        case 3: rc_replace<RB, 3>(v, g, gB, base); break;
+        default: rc_replace<RB, RB - 1>(v, g, gB, base); break;
       }
-      gi += 1 + nf;
     }
 #pragma unroll
     for (int e = 0; e < (1 << RB); ++e) C[base + voff[e]] = v[e];
@@ -884,6 +861,9 @@ __device__ void trace_rchain(const ChainTrace &ct, const T *X, int8_t *state, in
   const ChainParams &p = ct.p;
   const int E = p.tile;   // 32
   T *buf = reinterpret_cast<T *>(smem);
+  T *sBg = buf + (int64_t)(p.ngates + 1) * E;   // staged gate operands
+  load_gate_operands<T>(p, X, nullptr, sBg, nullptr, kGateBMax);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) {
     int64_t part = 0;
@@ -899,46 +879,28 @@ __device__ void trace_rchain(const ChainTrace &ct, const T *X, int8_t *state, in
     };
     for (int e = lane; e < E; e += 32) buf[e] = X[ct.offIn + base + p.hi_off[e]];
     __syncwarp();
-    int gi = 0, slot = 0;
-    while (gi < p.ngates) {
+    for (int gi = 0; gi < p.ngates; ++gi) {
       const ChainGate &g = p.g[gi];
-      const T *src = buf + (int64_t)slot * E;
-      T *dst = buf + (int64_t)(slot + 1) * E;
-      const T *gB = X + g.offB;
-      if (g.kind == 1) {
+      const T *src = buf + (int64_t)gi * E;
+      T *dst = buf + (int64_t)(gi + 1) * E;
+      const T *gB = sBg + gi * kGateBMax;
+      if (g.kind != 0) {
         for (int e = lane; e < E; e += 32) {
           const int x0 = digit(g, 0, e), x1 = g.nb > 1 ? digit(g, 1, e) : 0;
-          dst[e] = src[e] + gB[x0 * g.sBb[0] + (g.nb > 1 ? x1 * g.sBb[1] : 0)];
+          dst[e] = src[e] + gB[x0 * (int)g.sBb[0] + (g.nb > 1 ? x1 * (int)g.sBb[1] : 0)];
         }
-        __syncwarp();
-        ++gi;
-        ++slot;
-        continue;
-      }
-      int nf = 0;
-      while (nf < 2 && gi + 1 + nf < p.ngates && p.g[gi + 1 + nf].kind == 2) ++nf;
-      for (int e = lane; e < E; e += 32) {
-        if (e & (1 << g.ls)) continue;
-        const int e1 = e | (1 << g.ls);
-        const int w = g.nb > 0 ? digit(g, 0, e) : 0;
-        const int bo = w * (g.nb > 0 ? (int)g.sBb[0] : 0);
-        const T a = src[e], b = src[e1];
-        T o0 = max(a + gB[bo], b + gB[bo + g.sBk]);
-        T o1 = max(a + gB[bo + g.sBn], b + gB[bo + g.sBk + g.sBn]);
-        for (int f = 0; f < nf; ++f) {
-          const ChainGate &h = p.g[gi + 1 + f];
-          const T *hB = X + h.offB;
-          const int x = h.nb > 1 ? digit(h, 1, e) : 0;
-          const int s1 = h.nb > 1 ? x * (int)h.sBb[1] : 0;
-          o0 = o0 + hB[s1];
-          o1 = o1 + hB[(int)h.sBb[0] + s1];
+      } else {
+        for (int e = lane; e < E; e += 32) {
+          if (e & (1 << g.ls)) continue;
+          const int e1 = e | (1 << g.ls);
+          const int w = g.nb > 0 ? digit(g, 0, e) : 0;
+          const int bo = w * (g.nb > 0 ? (int)g.sBb[0] : 0);
+          const T a = src[e], b = src[e1];
+          dst[e] = max(a + gB[bo], b + gB[bo + g.sBk]);
+          dst[e1] = max(a + gB[bo + g.sBn], b + gB[bo + g.sBk + g.sBn]);
         }
-        dst[e] = o0;
-        dst[e1] = o1;
       }
       __syncwarp();
-      gi += 1 + nf;
-      ++slot;
     }
     if (lane == 0) {
       int x = 0;
@@ -947,23 +909,11 @@ __device__ void trace_rchain(const ChainTrace &ct, const T *X, int8_t *state, in
         if (d < 0 || d > 1) { *err = 1; d = 0; }
         x |= d << j;
       }
-      // walk the replace gates backwards (slot s holds the input of replace s)
-      int nslots = slot;
-      int gidx[TN_CHAIN_MAX_G];
-      int ns = 0;
-      for (int i = 0; i < p.ngates;) {
-        gidx[ns++] = i;
-        if (p.g[i].kind == 1) { ++i; continue; }
-        int nf = 0;
-        while (nf < 2 && i + 1 + nf < p.ngates && p.g[i + 1 + nf].kind == 2) ++nf;
-        i += 1 + nf;
-      }
-      (void)nslots;
-      for (int si = ns - 1; si >= 0; --si) {
-        const ChainGate &g = p.g[gidx[si]];
+      for (int gi = p.ngates - 1; gi >= 0; --gi) {
+        const ChainGate &g = p.g[gi];
         if (g.kind != 0) continue;
-        const T *src = buf + (int64_t)si * E;
-        const T *gB = X + g.offB;
+        const T *src = buf + (int64_t)gi * E;
+        const T *gB = sBg + gi * kGateBMax;
         const int v = (x >> g.ls) & 1;
         const int x0 = x & ~(1 << g.ls);
         const int w = g.nb > 0 ? digit(g, 0, x0) : 0;
@@ -985,14 +935,26 @@ cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, con
   if (p.outer == 0) return cudaSuccess;
   int64_t blocks = (p.outer + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  if (dt == DT_F32)
-    k_rchain<float, kRegBits><<<(int)blocks, 256, 0, st>>>(
-        p, reinterpret_cast<const float *>(arena), static_cast<const float *>(Ax),
-        static_cast<float *>(Cx));
-  else
-    k_rchain<int32_t, kRegBits><<<(int)blocks, 256, 0, st>>>(
-        p, reinterpret_cast<const int32_t *>(arena), static_cast<const int32_t *>(Ax),
-        static_cast<int32_t *>(Cx));
+  if (p.t != 4 && p.t != 5) return cudaErrorInvalidValue;
+  if (dt == DT_F32) {
+    if (p.t == 5)
+      k_rchain<float, 5><<<(int)blocks, 256, 0, st>>>(p, reinterpret_cast<const float *>(arena),
+                                                      static_cast<const float *>(Ax),
+                                                      static_cast<float *>(Cx));
+    else
+      k_rchain<float, 4><<<(int)blocks, 256, 0, st>>>(p, reinterpret_cast<const float *>(arena),
+                                                      static_cast<const float *>(Ax),
+                                                      static_cast<float *>(Cx));
+  } else {
+    if (p.t == 5)
+      k_rchain<int32_t, 5><<<(int)blocks, 256, 0, st>>>(
+          p, reinterpret_cast<const int32_t *>(arena), static_cast<const int32_t *>(Ax),
+          static_cast<int32_t *>(Cx));
+    else
+      k_rchain<int32_t, 4><<<(int)blocks, 256, 0, st>>>(
+          p, reinterpret_cast<const int32_t *>(arena), static_cast<const int32_t *>(Ax),
+          static_cast<int32_t *>(Cx));
+  }
   return cudaGetLastError();
 }
 
@@ -1035,15 +997,28 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceStep *__rest
   for (int i = threadIdx.x; i < nspins; i += blockDim.x) sst[i] = state[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // each record is copied into shared memory with one cooperative load
+  __shared__ __align__(16) unsigned long long srec[(sizeof(ChainTrace) + 7) / 8];
   for (int s = 0; s < nsteps; ++s) {
-    const TraceStep &st = steps[s];
-    if (st.chain >= 0) {
-      if (chains[st.chain].p.mode == 1)
-        trace_rchain<T>(chains[st.chain], X, sst, &serr, work, &sbase[0]);
+    const int chain = steps[s].chain;
+    {
+      const unsigned long long *src = chain >= 0
+          ? reinterpret_cast<const unsigned long long *>(&chains[chain])
+          : reinterpret_cast<const unsigned long long *>(&steps[s]);
+      const int words = (int)((chain >= 0 ? sizeof(ChainTrace) : sizeof(TraceStep)) / 8);
+      __syncthreads();
+      for (int w = threadIdx.x; w < words; w += blockDim.x) srec[w] = src[w];
+      __syncthreads();
+    }
+    if (chain >= 0) {
+      const ChainTrace &ct = *reinterpret_cast<const ChainTrace *>(srec);
+      if (ct.p.mode == 1)
+        trace_rchain<T>(ct, X, sst, &serr, work, &sbase[0]);
       else
-        trace_chain<T, Q>(chains[st.chain], X, sst, &serr, work, &sbase[0]);
+        trace_chain<T, Q>(ct, X, sst, &serr, work, &sbase[0]);
       continue;
     }
+    const TraceStep &st = *reinterpret_cast<const TraceStep *>(srec);
     if (warp < 2) {
       // warp 0 sums A's fixed legs, warp 1 B's
       const int nf = warp == 0 ? st.nfa : (st.offB >= 0 ? st.nfb : 0);
@@ -1105,7 +1080,8 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceStep *__rest
 }
 
 size_t trace_smem_bytes(const ChainParams &p, size_t elem) {
-  if (p.mode == 1) return elem * (size_t)(p.ngates + 1) * p.tile;
+  if (p.mode == 1)
+    return elem * ((size_t)(p.ngates + 1) * p.tile + (size_t)TN_CHAIN_MAX_G * kGateBMax);
   return elem * ((size_t)(p.ngates + 1) * p.tile + (size_t)TN_CHAIN_MAX_G * kGateBMax);
 }
 

@@ -448,8 +448,7 @@ struct Builder {
   std::vector<int> macro_of;    // tensor -> macro producing it
   bool fuse = true;
   bool regmode = false;         // q == 2 values: register chains (ChainParams mode 1)
-  static constexpr int kRB = 5; // register legs of a register chain
-  bool fold_diag = false;       // apply diagonal gates inside the preceding replace gate
+  int kRB = 5;                  // register legs of a register chain (4 or 5)
   int tmax = 11, wlow = 5;
   Macro open;
   bool has_open = false;
@@ -573,7 +572,6 @@ struct Builder {
     }
     cp.ngates = (int)m.gates.size();
     blocs->clear();
-    int last_replace = -1, nfold = 0;
     for (int i = 0; i < cp.ngates; ++i) {
       const CGate &g = m.gates[i];
       ChainGate &c = cp.g[i];
@@ -584,27 +582,6 @@ struct Builder {
         c.lsb[j] = pos_of(S, g.bpos[j]);
         c.lsbh[j] = R - 1 - g.bpos[j];
         c.sBb[j] = g.sBb[j];
-      }
-      // a diagonal gate right after a replace gate on one of its legs is
-      // applied inside that gate (same additions in the same order)
-      if (fold_diag && g.kind == 1 && last_replace >= 0 && nfold < 2) {
-        const int rp = m.gates[last_replace].pos;
-        const int k = pos_of(g.bpos, rp);
-        if (k >= 0) {
-          c.kind = 2;
-          if (k == 1) {
-            std::swap(c.lsb[0], c.lsb[1]);
-            std::swap(c.lsbh[0], c.lsbh[1]);
-            std::swap(c.sBb[0], c.sBb[1]);
-          }
-          ++nfold;
-        }
-      }
-      if (c.kind == 0) {
-        last_replace = i;
-        nfold = 0;
-      } else if (c.kind == 1) {
-        last_replace = -1;
       }
       c.kspin = g.kspin;
       c.sBk = g.sBk;
@@ -866,6 +843,7 @@ struct Builder {
   bool build(ProgMode mode, int64_t seg_bytes) {
     fuse = std::getenv("TN_NO_FUSION") == nullptr;
     regmode = q == 2 && P == 0 && std::getenv("TN_TILE_CHAINS") == nullptr;
+    if (const char *rb = std::getenv("TN_REG_BITS")) kRB = std::atoi(rb) == 4 ? 4 : 5;
     if (q == 3) { tmax = 7; wlow = 4; }
     emit_leaves();
     if (!forward()) return false;

@@ -158,13 +158,38 @@ tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_li
                    double *ln_count, double *E);
 
 /*
- * tn_batch_run -- many independent instances (each already built and
- *   ordered) in one batched execution: all their leaves and steps go into one
- *   persistent kernel launch, captured as a CUDA graph and replayed on later
- *   calls with the same contexts.  Outputs, per instance k: E[k];
- *   limbs[k*limbs_per ...] the count (when limbs != NULL; 3 primes + witness);
- *   status[k] a tn_status.  Returns the first non-OK status, else TN_OK.
- *   All contexts must use the same dtype and q.
+ * Batches on one context: B coupling sets on the context's graph and order
+ * (many disorder instances of one lattice).  Every kernel of the plan is
+ * launched once for all B instances (instance = one grid dimension, each with
+ * its own slice of the arena), the traceback runs one block per instance, and
+ * the launch sequence is captured as a CUDA graph per (range, B).
+ *   J: B*n_edges floats, instance-major; h: B*n_spins floats, required when
+ *   the context was built with fields and NULL otherwise; on_device: 0 host
+ *   pointers, 1 device pointers.  E: B doubles (host).  The arena grows to B
+ *   times the single-instance plan (TN_ENOMEM if it does not fit).
+ * tn_energy_batch -- E_min of each instance.
+ * tn_config_batch -- E_min and the ground state (sigma: B*n_spins int8, host,
+ *   may be NULL; same conventions as tn_config).
+ * tn_count_batch -- E_min and degeneracy of each instance with n_primes
+ *   primes + witness (as tn_count); limbs: B*limbs_per little-endian 64-bit
+ *   limbs; status[b] (may be NULL) is TN_OK, TN_EOVERFLOW or TN_EINVAL (count
+ *   needs more than limbs_per limbs).  Returns the first non-OK status.
+ */
+tn_status tn_energy_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
+                          int32_t on_device, double *E);
+tn_status tn_config_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
+                          int32_t on_device, double *E, int8_t *sigma);
+tn_status tn_count_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
+                         int32_t on_device, int32_t n_primes, uint64_t *limbs, int32_t limbs_per,
+                         double *E, int32_t *status);
+
+/*
+ * tn_batch_run -- many independent instances, each already built and ordered
+ *   (possibly of different sizes).  Contexts with the same graph, dtype and
+ *   plan are grouped and each group runs as one batch (tn_count_batch with 3
+ *   primes + witness, or tn_energy_batch when limbs == NULL) on the group's
+ *   first context.  Outputs per instance k: E[k]; limbs[k*limbs_per ...]; and
+ *   status[k].  Returns the first non-OK status, else TN_OK.
  */
 tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limbs,
                        int32_t limbs_per, int32_t *status);

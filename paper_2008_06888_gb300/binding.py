@@ -35,6 +35,12 @@ _SIGS = {
     "tn_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "tn_count": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32),
                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "tn_energy_batch": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                  C.c_void_p]),
+    "tn_config_batch": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                  C.c_void_p, C.c_void_p]),
+    "tn_count_batch": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                 C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "tn_batch_run": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                C.c_void_p]),
     "tn_plan_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -179,6 +185,49 @@ def tn_count(ctx, n_primes=3):
     return limbs_to_int(limbs[:nl.value]), ln.value, E.value
 
 
+def _batch_ptrs(J, h):
+    """(J ptr, h ptr, on_device, keep-alive) for numpy arrays or CUDA torch tensors."""
+    if hasattr(J, "data_ptr"):
+        return (C.c_void_p(J.data_ptr()), None if h is None else C.c_void_p(h.data_ptr()), 1,
+                (J, h))
+    J = np.ascontiguousarray(J, dtype=np.float32)
+    h = None if h is None else np.ascontiguousarray(h, dtype=np.float32)
+    return _ptr(J), _ptr(h), 0, (J, h)
+
+
+def tn_energy_batch(ctx, J, h=None):
+    """E_min of B coupling sets; J (B, n_edges), h (B, n_spins) or None."""
+    B = int(J.shape[0])
+    pj, ph, dev, keep = _batch_ptrs(J, h)
+    E = np.zeros(B, np.float64)
+    _check(lib().tn_energy_batch(ctx, B, pj, ph, dev, _ptr(E)), ctx)
+    return E
+
+
+def tn_config_batch(ctx, J, h=None, n_spins=None, want_sigma=True):
+    B = int(J.shape[0])
+    pj, ph, dev, keep = _batch_ptrs(J, h)
+    E = np.zeros(B, np.float64)
+    sigma = np.empty((B, n_spins), np.int8) if want_sigma else None
+    _check(lib().tn_config_batch(ctx, B, pj, ph, dev, _ptr(E), _ptr(sigma)), ctx)
+    return E, sigma
+
+
+def tn_count_batch(ctx, J, h=None, n_primes=3, limbs_per=8):
+    B = int(J.shape[0])
+    pj, ph, dev, keep = _batch_ptrs(J, h)
+    E = np.zeros(B, np.float64)
+    limbs = np.zeros(B * limbs_per, np.uint64)
+    status = np.zeros(B, np.int32)
+    st = lib().tn_count_batch(ctx, B, pj, ph, dev, n_primes, _ptr(limbs), limbs_per, _ptr(E),
+                              _ptr(status))
+    if st not in (TN_OK, TN_EOVERFLOW):
+        _check(st, ctx)
+    counts = [limbs_to_int(limbs[k * limbs_per:(k + 1) * limbs_per]) if status[k] == 0 else None
+              for k in range(B)]
+    return E, counts, status
+
+
 def tn_batch_run(ctxs, with_counts=True, limbs_per=4):
     B = len(ctxs)
     arr = (C.c_void_p * B)(*[c.value for c in ctxs])
@@ -268,6 +317,15 @@ class SpinGlass:
 
     def count(self, n_primes=3):
         return tn_count(self.ctx, n_primes)
+
+    def energy_batch(self, J, h=None):
+        return tn_energy_batch(self.ctx, J, h)
+
+    def config_batch(self, J, h=None, want_sigma=True):
+        return tn_config_batch(self.ctx, J, h, self.n, want_sigma)
+
+    def count_batch(self, J, h=None, n_primes=3, limbs_per=8):
+        return tn_count_batch(self.ctx, J, h, n_primes, limbs_per)
 
     def gradient(self, dJ=None, dh=None):
         return tn_gradient(self.ctx, self.m, self.n, dJ, dh)

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -52,6 +53,10 @@ struct tn_ctx {
   struct Pending { int kind, e0, e1; };
   std::vector<Pending> pending;
   int ev_next = 0;
+  // batch buffers (capacity bcap instances)
+  int bcap = 0;
+  float *d_Jb = nullptr, *d_hb = nullptr;
+  int8_t *d_stateb = nullptr, *d_outb = nullptr;
   // host-side program of tn_energy_noalloc and the plan fingerprint it was built for
   std::unique_ptr<Program> prog_noalloc;
   uint64_t noalloc_fp = 0;
@@ -233,9 +238,26 @@ int op_kind_slot(OpKind k) {
   return 5;
 }
 
+// What one execution of a program range works on: B instances, their
+// couplings and spin states.
+struct RunArgs {
+  Batch bt;
+  const float *J = nullptr, *h = nullptr;
+  int8_t *state = nullptr;
+};
+
+RunArgs single_args(tn_ctx *ctx) {
+  RunArgs a;
+  a.J = ctx->d_J;
+  a.h = ctx->d_h;
+  a.state = ctx->d_state;
+  return a;
+}
+
 tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_t st,
-                  bool account) {
+                  bool account, const RunArgs &ra) {
   char *ar = ctx->d_arena;
+  const Batch &bt = ra.bt;
   PrimeSet ps;
   for (int i = 0; i < TN_MAX_PRIMES; ++i) ps.c[i] = kPrimeC[i];
   auto X = [&](const Loc &l) -> void * { return l.buf < 0 ? nullptr : ar + abs_off(p, l); };
@@ -243,7 +265,7 @@ tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_
     return l.buf < 0 ? nullptr : (uint64_t *)(ar + p.bufs[l.buf].off + l.noff);
   };
   if (p.mode == PM_CONFIG && op_end > p.fwd_end)
-    CK(cudaMemsetAsync(ctx->d_state, 0xff, std::max(1, ctx->net.n), st));
+    CK(cudaMemsetAsync(ra.state, 0xff, (size_t)std::max(1, ctx->net.n) * bt.B, st));
   if (ctx->profiling && ctx->ev_next > 4096) collect_profile(ctx);
   for (int oi = op_begin; oi < op_end; ++oi) {
     const Op &op = p.ops[oi];
@@ -256,29 +278,28 @@ tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_
     }
     switch (op.kind) {
       case OP_LEAVES:
-        e = launch_leaves(p.dt, p.q, p.d_leaves, (int)p.leaves.size(), ctx->d_J, ctx->d_h, ar, p.P,
-                          st);
+        e = launch_leaves(p.dt, p.q, p.d_leaves, (int)p.leaves.size(), ra.J, ra.h, ar, p.P, bt, st);
         break;
       case OP_PERM:
-        e = launch_permute(p.perms[op.idx], X(op.in0), X(op.out), Nn(op.in0), Nn(op.out), st);
+        e = launch_permute(p.perms[op.idx], X(op.in0), X(op.out), Nn(op.in0), Nn(op.out), bt, st);
         break;
       case OP_GATE:
         e = launch_gate(p.dt, p.gates[op.idx], X(op.in0), X(op.in1), X(op.out), Nn(op.in0),
-                        Nn(op.in1), Nn(op.out), ps, st);
+                        Nn(op.in1), Nn(op.out), ps, bt, st);
         break;
       case OP_GEMM:
-        e = launch_gemm(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out), st);
+        e = launch_gemm(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out), bt, st);
         if (e == cudaSuccess && p.P > 0)
           e = launch_gemm_count(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out),
-                                Nn(op.in0), Nn(op.in1), Nn(op.out), ps, st);
+                                Nn(op.in0), Nn(op.in1), Nn(op.out), ps, bt, st);
         break;
       case OP_TRACE:
         e = launch_trace(p.dt, p.q, p.d_trace + op.trace_begin, op.trace_n, p.d_chain_traces,
-                         p.trace_smem, ar, ctx->d_state, ctx->net.n, ctx->d_err, st);
+                         p.trace_smem, ar, ra.state, ctx->net.n, ctx->d_err, bt, st);
         break;
       case OP_CHAIN:
         e = launch_chain(p.dt, p.chains[op.idx], ar, X(op.in0), Nn(op.in0), X(op.out), Nn(op.out),
-                         ps, st);
+                         ps, bt, st);
         break;
     }
     if (e != cudaSuccess)
@@ -288,8 +309,8 @@ tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_
     if (op.kind == OP_PERM && p.P > 0) nl = 2;
     if (account) {
       ctx->launches[slot] += nl;
-      ctx->prof_bytes[slot] += op.bytes;
-      ctx->prof_macs[slot] += op.macs;
+      ctx->prof_bytes[slot] += op.bytes * bt.B;
+      ctx->prof_macs[slot] += op.macs * bt.B;
     }
     if (ctx->profiling) {
       int e1 = ctx->ev_next;
@@ -300,46 +321,58 @@ tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_
   return TN_OK;
 }
 
-void account_range(tn_ctx *ctx, const Program &p, int b, int e) {
+// launches are counted once per launch (a batched launch covers every
+// instance); bytes and multiply-adds once per instance
+void account_range(tn_ctx *ctx, const Program &p, int b, int e, int B) {
   for (int oi = b; oi < e; ++oi) {
     const Op &op = p.ops[oi];
     const int slot = op_kind_slot(op.kind);
     int nl = 1;
     if ((op.kind == OP_GEMM || op.kind == OP_PERM) && p.P > 0) nl = 2;
     ctx->launches[slot] += nl;
-    ctx->prof_bytes[slot] += op.bytes;
-    ctx->prof_macs[slot] += op.macs;
+    ctx->prof_bytes[slot] += op.bytes * B;
+    ctx->prof_macs[slot] += op.macs * B;
   }
 }
 
 // Eager on the first run of a range (and whenever profiling, or with
 // TN_NO_GRAPH set); captured into a CUDA graph on the second run and
 // replayed from then on.
-tn_status run_program(tn_ctx *ctx, Program &p, int op_begin = 0, int op_end = -1) {
+tn_status run_program(tn_ctx *ctx, Program &p, int op_begin, int op_end, const RunArgs &ra) {
   if (op_end < 0) op_end = (int)p.ops.size();
   static const bool no_graph = std::getenv("TN_NO_GRAPH") != nullptr;
-  if (ctx->profiling || no_graph) return run_ops(ctx, p, op_begin, op_end, ctx->stream, true);
+  if (ctx->profiling || no_graph) return run_ops(ctx, p, op_begin, op_end, ctx->stream, true, ra);
   Program::Graph *g = nullptr;
   for (auto &x : p.graphs)
-    if (x.begin == op_begin && x.end == op_end) g = &x;
-  if (g && g->arena != ctx->d_arena) {
+    if (x.begin == op_begin && x.end == op_end && x.B == ra.bt.B && x.J == ra.J) g = &x;
+  if (g && (g->arena != ctx->d_arena || g->state != ra.state || g->h != ra.h)) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     g->exec = nullptr;
     g->runs = 0;
     g->arena = ctx->d_arena;
+    g->state = ra.state;
+    g->h = ra.h;
   }
   if (!g) {
-    p.graphs.push_back(Program::Graph{op_begin, op_end, 0, ctx->d_arena, nullptr});
+    Program::Graph ng{};
+    ng.begin = op_begin;
+    ng.end = op_end;
+    ng.B = ra.bt.B;
+    ng.arena = ctx->d_arena;
+    ng.J = ra.J;
+    ng.h = ra.h;
+    ng.state = ra.state;
+    p.graphs.push_back(ng);
     g = &p.graphs.back();
   }
   if (!g->exec && g->runs == 0) {
     g->runs = 1;
-    return run_ops(ctx, p, op_begin, op_end, ctx->stream, true);
+    return run_ops(ctx, p, op_begin, op_end, ctx->stream, true, ra);
   }
   if (!g->exec) {
     if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    tn_status s = run_ops(ctx, p, op_begin, op_end, ctx->cap_stream, false);
+    tn_status s = run_ops(ctx, p, op_begin, op_end, ctx->cap_stream, false, ra);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
     if (s != TN_OK) {
@@ -357,8 +390,12 @@ tn_status run_program(tn_ctx *ctx, Program &p, int op_begin = 0, int op_end = -1
   }
   CK(cudaGraphLaunch(g->exec, ctx->stream));
   g->runs++;
-  account_range(ctx, p, op_begin, op_end);
+  account_range(ctx, p, op_begin, op_end, ra.bt.B);
   return TN_OK;
+}
+
+tn_status run_program(tn_ctx *ctx, Program &p, int op_begin = 0, int op_end = -1) {
+  return run_program(ctx, p, op_begin, op_end, single_args(ctx));
 }
 
 double root_energy(const tn_ctx *ctx, const void *raw) {
@@ -420,6 +457,115 @@ uint64_t limbs_mod(const std::vector<uint64_t> &v, uint64_t p) {
   u128 r = 0;
   for (int i = (int)v.size() - 1; i >= 0; --i) r = ((r << 64) | v[i]) % p;
   return (uint64_t)r;
+}
+
+
+// ---- batches of coupling sets on one context (same graph, same order)
+
+int64_t batch_stride(const Program &p) { return (p.arena_bytes + 255) / 256 * 256; }
+
+tn_status ensure_arena(tn_ctx *ctx, int64_t bytes) {
+  if (bytes <= ctx->arena_cap) return TN_OK;
+  if (ctx->d_arena) CK(cudaFree(ctx->d_arena));
+  ctx->d_arena = nullptr;
+  ctx->arena_cap = 0;
+  cudaError_t e = cudaMalloc(&ctx->d_arena, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, TN_ENOMEM, "batch arena of " + std::to_string(bytes) + " bytes: " +
+                                    cudaGetErrorString(e));
+  }
+  ctx->arena_cap = bytes;
+  return TN_OK;
+}
+
+tn_status ensure_batch(tn_ctx *ctx, int B) {
+  if (B <= ctx->bcap) return TN_OK;
+  const Net &n = ctx->net;
+  if (ctx->d_Jb) CK(cudaFree(ctx->d_Jb));
+  if (ctx->d_hb) CK(cudaFree(ctx->d_hb));
+  if (ctx->d_stateb) CK(cudaFree(ctx->d_stateb));
+  if (ctx->d_outb) CK(cudaFree(ctx->d_outb));
+  ctx->d_Jb = nullptr;
+  ctx->d_hb = nullptr;
+  ctx->d_stateb = ctx->d_outb = nullptr;
+  ctx->bcap = 0;
+  CK(cudaMalloc(&ctx->d_Jb, (size_t)B * std::max(1, n.m) * sizeof(float)));
+  CK(cudaMalloc(&ctx->d_hb, (size_t)B * std::max(1, n.n) * sizeof(float)));
+  CK(cudaMalloc(&ctx->d_stateb, (size_t)B * std::max(1, n.n)));
+  CK(cudaMalloc(&ctx->d_outb, (size_t)B * std::max(1, n.n)));
+  ctx->bcap = B;
+  return TN_OK;
+}
+
+tn_status batch_setup(tn_ctx *ctx, int B, const float *J, const float *h, int on_device,
+                      ProgMode mode, int P, Program **out, RunArgs *ra) {
+  const Net &n = ctx->net;
+  if (B < 1) return fail(ctx, TN_EINVAL, "batch size must be >= 1");
+  if (n.m > 0 && !J) return fail(ctx, TN_EINVAL, "J is NULL");
+  const bool fields = !n.h.empty();
+  if (fields && !h) return fail(ctx, TN_EINVAL, "the instance has fields: h is required");
+  if (!fields && h) return fail(ctx, TN_EINVAL, "the instance was built without fields");
+  if (!on_device && ctx->dt == DT_I32) {
+    for (int64_t i = 0; i < (int64_t)B * n.m; ++i)
+      if (std::nearbyint(J[i]) != J[i] || !(std::fabs(J[i]) < (float)(1 << 20)))
+        return fail(ctx, TN_EINVAL, "INT32 context needs integral J");
+    if (h)
+      for (int64_t i = 0; i < (int64_t)B * n.n; ++i)
+        if (std::nearbyint(h[i]) != h[i] || !(std::fabs(h[i]) < (float)(1 << 20)))
+          return fail(ctx, TN_EINVAL, "INT32 context needs integral h");
+  }
+  tn_status s = ensure_device(ctx);
+  if (s != TN_OK) return s;
+  Program *p;
+  if ((s = get_program(ctx, mode, P, &p)) != TN_OK) return s;
+  const int64_t stride = batch_stride(*p);
+  if ((s = ensure_arena(ctx, stride * B)) != TN_OK) return s;
+  if ((s = ensure_batch(ctx, B)) != TN_OK) return s;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (n.m) CK(cudaMemcpyAsync(ctx->d_Jb, J, (size_t)B * n.m * sizeof(float), kind, ctx->stream));
+  if (h) CK(cudaMemcpyAsync(ctx->d_hb, h, (size_t)B * n.n * sizeof(float), kind, ctx->stream));
+  ctx->fwd_done = false;
+  ra->bt.B = B;
+  ra->bt.ib = stride;
+  ra->bt.jstride = n.m;
+  ra->bt.hstride = n.n;
+  ra->J = ctx->d_Jb;
+  ra->h = ctx->d_hb;
+  ra->state = ctx->d_stateb;
+  *out = p;
+  return TN_OK;
+}
+
+// values (4 bytes each) of the root of every instance
+tn_status batch_roots(tn_ctx *ctx, const Program &p, int B, std::vector<char> *raw) {
+  raw->assign((size_t)B * 4, 0);
+  CK(cudaMemcpy2DAsync(raw->data(), 4, ctx->d_arena + abs_off(p, p.root), batch_stride(p), 4, B,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  return TN_OK;
+}
+
+tn_status check_trace_err(tn_ctx *ctx) {
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (herr) {
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+    return fail(ctx, TN_EINVAL, "traceback met an unassigned spin (internal planning error)");
+  }
+  return TN_OK;
+}
+
+// exact count of one instance from its residues (the last one is the witness)
+tn_status count_from_residues(tn_ctx *ctx, const std::vector<uint64_t> &res, int n_primes,
+                              std::vector<uint64_t> *v) {
+  std::vector<uint64_t> r(res.begin(), res.begin() + n_primes), pr;
+  for (int i = 0; i < n_primes; ++i) pr.push_back((1ull << 61) - kPrimeC[i]);
+  *v = crt(r, pr);
+  const uint64_t pw = (1ull << 61) - kPrimeC[n_primes];
+  if (limbs_mod(*v, pw) != res[n_primes])
+    return fail(ctx, TN_EOVERFLOW, "count exceeds the product of the primes (witness mismatch)");
+  return TN_OK;
 }
 
 }  // namespace
@@ -588,7 +734,7 @@ tn_status tn_backward(tn_ctx *ctx, int8_t *sigma) {
   }
   ctx->have_state = true;
   if (sigma) {
-    CK(launch_state_out(ctx->net.q, ctx->net.n, ctx->d_state, ctx->d_out, ctx->stream));
+    CK(launch_state_out(ctx->net.q, ctx->net.n, ctx->d_state, ctx->d_out, 1, ctx->stream));
     ctx->launches[5]++;
     CK(cudaMemcpyAsync(sigma, ctx->d_out, ctx->net.n, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -607,13 +753,13 @@ tn_status tn_gradient(tn_ctx *ctx, float *dJ, float *dh, int32_t on_device) {
   if (!ctx->have_state) return fail(ctx, TN_ESTATE, "tn_config has not run");
   const Net &n = ctx->net;
   if (on_device) {
-    CK(launch_grad(n.q, n.n, n.m, ctx->d_eu, ctx->d_ev, ctx->d_state, dJ, dh, ctx->stream));
+    CK(launch_grad(n.q, n.n, n.m, ctx->d_eu, ctx->d_ev, ctx->d_state, dJ, dh, 1, ctx->stream));
     return TN_OK;
   }
   float *gJ = nullptr, *gh = nullptr;
   CK(cudaMalloc(&gJ, std::max(1, n.m) * sizeof(float)));
   CK(cudaMalloc(&gh, std::max(1, n.n) * sizeof(float)));
-  CK(launch_grad(n.q, n.n, n.m, ctx->d_eu, ctx->d_ev, ctx->d_state, gJ, gh, ctx->stream));
+  CK(launch_grad(n.q, n.n, n.m, ctx->d_eu, ctx->d_ev, ctx->d_state, gJ, gh, 1, ctx->stream));
   if (dJ && n.m) CK(cudaMemcpyAsync(dJ, gJ, n.m * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
   if (dh) CK(cudaMemcpyAsync(dh, gh, n.n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -663,20 +809,144 @@ tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_li
   return TN_OK;
 }
 
+
+tn_status tn_energy_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
+                          int32_t on_device, double *E) {
+  if (!ctx) return TN_EINVAL;
+  if (!E) return fail(ctx, TN_EINVAL, "E is NULL");
+  Program *p;
+  RunArgs ra;
+  tn_status s = batch_setup(ctx, B, J, h, on_device, PM_ENERGY, 0, &p, &ra);
+  if (s != TN_OK) return s;
+  if ((s = run_program(ctx, *p, 0, -1, ra)) != TN_OK) return s;
+  std::vector<char> raw;
+  if ((s = batch_roots(ctx, *p, B, &raw)) != TN_OK) return s;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int b = 0; b < B; ++b) E[b] = root_energy(ctx, raw.data() + 4 * b);
+  return TN_OK;
+}
+
+tn_status tn_config_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
+                          int32_t on_device, double *E, int8_t *sigma) {
+  if (!ctx) return TN_EINVAL;
+  Program *p;
+  RunArgs ra;
+  tn_status s = batch_setup(ctx, B, J, h, on_device, PM_CONFIG, 0, &p, &ra);
+  if (s != TN_OK) return s;
+  if ((s = run_program(ctx, *p, 0, -1, ra)) != TN_OK) return s;
+  std::vector<char> raw;
+  if (E && (s = batch_roots(ctx, *p, B, &raw)) != TN_OK) return s;
+  if (sigma) {
+    CK(launch_state_out(ctx->net.q, ctx->net.n, ctx->d_stateb, ctx->d_outb, B, ctx->stream));
+    ctx->launches[5]++;
+    CK(cudaMemcpyAsync(sigma, ctx->d_outb, (size_t)B * ctx->net.n, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  }
+  if ((s = check_trace_err(ctx)) != TN_OK) return s;
+  if (E)
+    for (int b = 0; b < B; ++b) E[b] = root_energy(ctx, raw.data() + 4 * b);
+  return TN_OK;
+}
+
+tn_status tn_count_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
+                         int32_t on_device, int32_t n_primes, uint64_t *limbs, int32_t limbs_per,
+                         double *E, int32_t *status) {
+  if (!ctx) return TN_EINVAL;
+  if (n_primes < 1 || n_primes > TN_MAX_PRIMES - 1)
+    return fail(ctx, TN_EINVAL, "n_primes must be in [1, 8]");
+  if (!limbs || limbs_per < 1) return fail(ctx, TN_EINVAL, "limbs buffer missing");
+  const int P = n_primes + 1;
+  Program *p;
+  RunArgs ra;
+  tn_status s = batch_setup(ctx, B, J, h, on_device, PM_COUNT, P, &p, &ra);
+  if (s != TN_OK) return s;
+  if ((s = run_program(ctx, *p, 0, -1, ra)) != TN_OK) return s;
+  std::vector<char> raw;
+  if ((s = batch_roots(ctx, *p, B, &raw)) != TN_OK) return s;
+  std::vector<uint64_t> res((size_t)P * B);
+  const char *rbase = ctx->d_arena + p->bufs[p->root.buf].off + p->root.noff;
+  for (int i = 0; i < P; ++i)
+    CK(cudaMemcpy2DAsync(res.data() + (size_t)i * B, 8, rbase + (int64_t)i * p->root.plane * 8,
+                         batch_stride(*p), 8, B, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  tn_status first = TN_OK;
+  for (int b = 0; b < B; ++b) {
+    if (E) E[b] = root_energy(ctx, raw.data() + 4 * b);
+    std::vector<uint64_t> r(P), v;
+    for (int i = 0; i < P; ++i) r[i] = res[(size_t)i * B + b];
+    tn_status sb = count_from_residues(ctx, r, n_primes, &v);
+    if (sb == TN_OK && (int)v.size() > limbs_per) {
+      sb = TN_EINVAL;
+      fail(ctx, sb, "limbs_per too small for a count");
+    }
+    uint64_t *out = limbs + (int64_t)b * limbs_per;
+    for (int i = 0; i < limbs_per; ++i) out[i] = (sb == TN_OK && i < (int)v.size()) ? v[i] : 0;
+    if (status) status[b] = sb;
+    if (sb != TN_OK && first == TN_OK) first = sb;
+  }
+  return first;
+}
+
 tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limbs,
                        int32_t limbs_per, int32_t *status) {
-  tn_status first = TN_OK;
+  if (B < 0 || (B > 0 && !ctxs)) return TN_EINVAL;
+  // group the contexts whose graph, dtype and plan coincide; each group runs
+  // as one batch on its first context
+  auto key = [](const tn_ctx *c) {
+    uint64_t f = 1469598103934665603ull;
+    auto mix = [&](uint64_t x) { f = (f ^ x) * 1099511628211ull; };
+    mix((uint64_t)c->net.n);
+    mix((uint64_t)c->net.q);
+    mix((uint64_t)c->dt);
+    mix((uint64_t)c->net.h.empty());
+    for (int e = 0; e < c->net.m; ++e) mix(((uint64_t)c->net.eu[e] << 32) | (uint32_t)c->net.ev[e]);
+    for (auto &st : c->plan.steps) mix(((uint64_t)(st.a + 7) << 40) ^ ((uint64_t)(st.b + 7) << 20) ^ (uint64_t)st.c);
+    return f;
+  };
+  std::map<uint64_t, std::vector<int>> groups;
   for (int k = 0; k < B; ++k) {
-    tn_ctx *c = ctxs[k];
+    if (!ctxs[k] || !ctxs[k]->ordered) {
+      if (status) status[k] = TN_ESTATE;
+      continue;
+    }
+    groups[key(ctxs[k])].push_back(k);
+  }
+  tn_status first = TN_OK;
+  for (int k = 0; k < B; ++k)
+    if (!ctxs[k] || !ctxs[k]->ordered) first = TN_ESTATE;
+  for (auto &kv : groups) {
+    const std::vector<int> &ids = kv.second;
+    tn_ctx *owner = ctxs[ids[0]];
+    const Net &n = owner->net;
+    const int G = (int)ids.size();
+    std::vector<float> J((size_t)G * n.m), h(n.h.empty() ? 0 : (size_t)G * n.n);
+    for (int g = 0; g < G; ++g) {
+      const Net &ng = ctxs[ids[g]]->net;
+      std::copy(ng.J.begin(), ng.J.end(), J.begin() + (size_t)g * n.m);
+      if (!h.empty()) std::copy(ng.h.begin(), ng.h.end(), h.begin() + (size_t)g * n.n);
+    }
+    std::vector<double> Eg(G);
+    std::vector<int32_t> sg(G, TN_OK);
     tn_status s;
     if (limbs) {
-      int32_t nl = limbs_per;
-      s = tn_count(c, 3, limbs + (int64_t)k * limbs_per, &nl, nullptr, E ? &E[k] : nullptr);
+      std::vector<uint64_t> lg((size_t)G * limbs_per);
+      s = tn_count_batch(owner, G, J.data(), h.empty() ? nullptr : h.data(), 0, 3, lg.data(),
+                         limbs_per, Eg.data(), sg.data());
+      for (int g = 0; g < G; ++g)
+        std::copy(lg.begin() + (size_t)g * limbs_per, lg.begin() + (size_t)(g + 1) * limbs_per,
+                  limbs + (int64_t)ids[g] * limbs_per);
     } else {
-      s = E ? tn_energy(c, &E[k]) : TN_EINVAL;
+      s = tn_energy_batch(owner, G, J.data(), h.empty() ? nullptr : h.data(), 0, Eg.data());
+      if (s != TN_OK) std::fill(sg.begin(), sg.end(), s);
     }
-    if (status) status[k] = s;
-    if (s != TN_OK && first == TN_OK) first = s;
+    if (s != TN_OK && owner != nullptr)
+      for (int g = 0; g < G; ++g)
+        if (sg[g] == TN_OK) sg[g] = s == TN_EOVERFLOW ? TN_OK : s;
+    for (int g = 0; g < G; ++g) {
+      if (E) E[ids[g]] = Eg[g];
+      if (status) status[ids[g]] = sg[g];
+      if (sg[g] != TN_OK && first == TN_OK) first = (tn_status)sg[g];
+    }
   }
   return first;
 }
@@ -785,27 +1055,28 @@ tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev,
   PrimeSet ps;
   for (int i = 0; i < TN_MAX_PRIMES; ++i) ps.c[i] = kPrimeC[i];
   auto X = [&](const Loc &l) -> void * { return l.buf < 0 ? nullptr : base + abs_off(p, l); };
+  const Batch one;
   for (const Op &op : p.ops) {
     cudaError_t e = cudaSuccess;
     switch (op.kind) {
       case OP_LEAVES:
-        e = launch_leaves(p.dt, p.q, d_leaves, (int)p.leaves.size(), J_dev, h_dev, base, 0, st);
+        e = launch_leaves(p.dt, p.q, d_leaves, (int)p.leaves.size(), J_dev, h_dev, base, 0, one, st);
         break;
       case OP_PERM:
-        e = launch_permute(p.perms[op.idx], X(op.in0), X(op.out), nullptr, nullptr, st);
+        e = launch_permute(p.perms[op.idx], X(op.in0), X(op.out), nullptr, nullptr, one, st);
         break;
       case OP_GATE:
         e = launch_gate(p.dt, p.gates[op.idx], X(op.in0), X(op.in1), X(op.out), nullptr,
-                        nullptr, nullptr, ps, st);
+                        nullptr, nullptr, ps, one, st);
         break;
       case OP_GEMM:
-        e = launch_gemm(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out), st);
+        e = launch_gemm(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out), one, st);
         break;
       case OP_TRACE:
         break;
       case OP_CHAIN:
         e = launch_chain(p.dt, p.chains[op.idx], base, X(op.in0), nullptr, X(op.out), nullptr, ps,
-                         st);
+                         one, st);
         break;
     }
     if (e != cudaSuccess)
@@ -831,6 +1102,10 @@ void tn_destroy(tn_ctx *ctx) {
     cudaFree(ctx->d_out);
     cudaFree(ctx->d_err);
   }
+  if (ctx->d_Jb) cudaFree(ctx->d_Jb);
+  if (ctx->d_hb) cudaFree(ctx->d_hb);
+  if (ctx->d_stateb) cudaFree(ctx->d_stateb);
+  if (ctx->d_outb) cudaFree(ctx->d_outb);
   if (ctx->d_arena) cudaFree(ctx->d_arena);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);

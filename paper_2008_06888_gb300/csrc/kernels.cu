@@ -5,6 +5,8 @@
 // the counts on a tie.  Counts are residues modulo 61-bit primes 2^61 - c.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "kernels.h"
@@ -55,6 +57,13 @@ static inline int grid_for(int64_t n, int threads, int max_blocks = 152 * 32) {
   return (int)b;
 }
 
+// Pointer of instance blockIdx.y in a batch whose arena slices are ib bytes apart.
+template <typename P>
+__device__ __forceinline__ P *inst_ptr(P *p, int64_t ib) {
+  return reinterpret_cast<P *>(reinterpret_cast<char *>(const_cast<void *>(
+                                   static_cast<const void *>(p))) + blockIdx.y * ib);
+}
+
 // ---------------------------------------------------------------- leaves
 
 template <typename T> __device__ __forceinline__ T to_val(float x);
@@ -66,7 +75,11 @@ template <> __device__ __forceinline__ int32_t to_val<int32_t>(float x) { return
 template <typename T>
 __global__ void k_leaves(const LeafDesc *__restrict__ d, int nleaves, int q,
                          const float *__restrict__ J, const float *__restrict__ h, char *arena,
-                         int P) {
+                         int P, int64_t jstride, int64_t hstride, int64_t ib) {
+  // instance blockIdx.y: its couplings and its slice of the arena
+  J += blockIdx.y * jstride;
+  h += blockIdx.y * hstride;
+  arena += blockIdx.y * ib;
   const int per = q * q;
   int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= (int64_t)nleaves * per) return;
@@ -102,15 +115,17 @@ __global__ void k_leaves(const LeafDesc *__restrict__ d, int nleaves, int q,
 }
 
 cudaError_t launch_leaves(Dtype dt, int q, const LeafDesc *d_leaves, int nleaves, const float *J,
-                          const float *h, char *arena, int P, cudaStream_t st) {
+                          const float *h, char *arena, int P, const Batch &bt, cudaStream_t st) {
   if (nleaves == 0) return cudaSuccess;
   int64_t total = (int64_t)nleaves * q * q;
   int threads = 256;
-  int blocks = (int)((total + threads - 1) / threads);
+  dim3 grid((unsigned)((total + threads - 1) / threads), bt.B);
   if (dt == DT_F32)
-    k_leaves<float><<<blocks, threads, 0, st>>>(d_leaves, nleaves, q, J, h, arena, P);
+    k_leaves<float><<<grid, threads, 0, st>>>(d_leaves, nleaves, q, J, h, arena, P, bt.jstride,
+                                               bt.hstride, bt.ib);
   else
-    k_leaves<int32_t><<<blocks, threads, 0, st>>>(d_leaves, nleaves, q, J, h, arena, P);
+    k_leaves<int32_t><<<grid, threads, 0, st>>>(d_leaves, nleaves, q, J, h, arena, P, bt.jstride,
+                                                 bt.hstride, bt.ib);
   return cudaGetLastError();
 }
 
@@ -122,7 +137,16 @@ __global__ void __launch_bounds__(256) k_gate(const GateParams p, const T *__res
                                               const T *__restrict__ B, T *__restrict__ C,
                                               const uint64_t *__restrict__ nA,
                                               const uint64_t *__restrict__ nB,
-                                              uint64_t *__restrict__ nC, const PrimeSet ps) {
+                                              uint64_t *__restrict__ nC, const PrimeSet ps,
+                                              int64_t ib) {
+  A = inst_ptr(A, ib);
+  C = inst_ptr(C, ib);
+  if (p.hasB) B = inst_ptr(B, ib);
+  if (COUNT) {
+    nA = inst_ptr(nA, ib);
+    nC = inst_ptr(nC, ib);
+    if (p.hasB) nB = inst_ptr(nB, ib);
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < p.outer; o += stride) {
     int64_t r = o, oa = 0, ob = 0, oc = 0;
@@ -176,26 +200,26 @@ __global__ void __launch_bounds__(256) k_gate(const GateParams p, const T *__res
 
 cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const void *xB, void *xC,
                         const uint64_t *nA, const uint64_t *nB, uint64_t *nC, const PrimeSet &ps,
-                        cudaStream_t st) {
+                        const Batch &bt, cudaStream_t st) {
   if (p.outer == 0) return cudaSuccess;
   int threads = 256;
-  int blocks = grid_for(p.outer, threads);
+  dim3 blocks(grid_for(p.outer, threads), bt.B);
   bool cnt = p.P > 0;
   if (dt == DT_F32) {
     if (cnt)
       k_gate<float, true><<<blocks, threads, 0, st>>>(p, (const float *)xA, (const float *)xB,
-                                                      (float *)xC, nA, nB, nC, ps);
+                                                      (float *)xC, nA, nB, nC, ps, bt.ib);
     else
       k_gate<float, false><<<blocks, threads, 0, st>>>(p, (const float *)xA, (const float *)xB,
-                                                       (float *)xC, nA, nB, nC, ps);
+                                                       (float *)xC, nA, nB, nC, ps, bt.ib);
   } else {
     if (cnt)
       k_gate<int32_t, true><<<blocks, threads, 0, st>>>(p, (const int32_t *)xA, (const int32_t *)xB,
-                                                        (int32_t *)xC, nA, nB, nC, ps);
+                                                        (int32_t *)xC, nA, nB, nC, ps, bt.ib);
     else
       k_gate<int32_t, false><<<blocks, threads, 0, st>>>(p, (const int32_t *)xA,
                                                          (const int32_t *)xB, (int32_t *)xC, nA, nB,
-                                                         nC, ps);
+                                                         nC, ps, bt.ib);
   }
   return cudaGetLastError();
 }
@@ -206,7 +230,11 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
 // 16 staged in shared memory.  Out-of-range operands read the tropical zero.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm(const GemmParams p, const T *__restrict__ A,
-                                              const T *__restrict__ B, T *__restrict__ C) {
+                                              const T *__restrict__ B, T *__restrict__ C,
+                                              int64_t ib) {
+  A = inst_ptr(A, ib);
+  B = inst_ptr(B, ib);
+  C = inst_ptr(C, ib);
   constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
   __shared__ T As[BK][BM + 4];
   __shared__ T Bs[BK][BN + 4];
@@ -264,15 +292,15 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmParams p, const T *__res
 }
 
 cudaError_t launch_gemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
-                        cudaStream_t st) {
+                        const Batch &bt, cudaStream_t st) {
   int64_t tiles = p.batch * ((p.M + 63) / 64) * ((p.N + 63) / 64);
   if (tiles == 0) return cudaSuccess;
-  int blocks = (int)(tiles < 152 * 16 ? tiles : 152 * 16);
+  dim3 blocks((unsigned)(tiles < 152 * 16 ? tiles : 152 * 16), bt.B);
   if (dt == DT_F32)
-    k_gemm<float><<<blocks, 256, 0, st>>>(p, (const float *)A, (const float *)B, (float *)C);
+    k_gemm<float><<<blocks, 256, 0, st>>>(p, (const float *)A, (const float *)B, (float *)C, bt.ib);
   else
     k_gemm<int32_t><<<blocks, 256, 0, st>>>(p, (const int32_t *)A, (const int32_t *)B,
-                                            (int32_t *)C);
+                                            (int32_t *)C, bt.ib);
   return cudaGetLastError();
 }
 
@@ -282,7 +310,13 @@ template <typename T>
 __global__ void k_gemm_count(const GemmParams p, const T *__restrict__ A, const T *__restrict__ B,
                              const T *__restrict__ C, const uint64_t *__restrict__ nA,
                              const uint64_t *__restrict__ nB, uint64_t *__restrict__ nC,
-                             const PrimeSet ps) {
+                             const PrimeSet ps, int64_t ib) {
+  A = inst_ptr(A, ib);
+  B = inst_ptr(B, ib);
+  C = inst_ptr(C, ib);
+  nA = inst_ptr(nA, ib);
+  nB = inst_ptr(nB, ib);
+  nC = inst_ptr(nC, ib);
   const int64_t total = p.batch * p.M * p.N;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -312,16 +346,16 @@ __global__ void k_gemm_count(const GemmParams p, const T *__restrict__ A, const 
 
 cudaError_t launch_gemm_count(Dtype dt, const GemmParams &p, const void *xA, const void *xB,
                               const void *xC, const uint64_t *nA, const uint64_t *nB, uint64_t *nC,
-                              const PrimeSet &ps, cudaStream_t st) {
+                              const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
   int64_t total = p.batch * p.M * p.N;
   if (total == 0) return cudaSuccess;
-  int blocks = grid_for(total, 256);
+  dim3 blocks(grid_for(total, 256), bt.B);
   if (dt == DT_F32)
     k_gemm_count<float><<<blocks, 256, 0, st>>>(p, (const float *)xA, (const float *)xB,
-                                                (const float *)xC, nA, nB, nC, ps);
+                                                (const float *)xC, nA, nB, nC, ps, bt.ib);
   else
     k_gemm_count<int32_t><<<blocks, 256, 0, st>>>(p, (const int32_t *)xA, (const int32_t *)xB,
-                                                  (const int32_t *)xC, nA, nB, nC, ps);
+                                                  (const int32_t *)xC, nA, nB, nC, ps, bt.ib);
   return cudaGetLastError();
 }
 
@@ -329,9 +363,12 @@ cudaError_t launch_gemm_count(Dtype dt, const GemmParams &p, const void *xA, con
 
 template <typename E>
 __global__ void k_permute(const PermParams p, const E *__restrict__ in, E *__restrict__ out,
-                          int64_t planeIn, int64_t planeOut) {
-  const E *src = in + blockIdx.y * planeIn;
-  E *dst = out + blockIdx.y * planeOut;
+                          int64_t planeIn, int64_t planeOut, int64_t ib) {
+  // blockIdx.y: residue plane, blockIdx.z: instance
+  const E *src = reinterpret_cast<const E *>(reinterpret_cast<const char *>(in) + blockIdx.z * ib) +
+                 blockIdx.y * planeIn;
+  E *dst = reinterpret_cast<E *>(reinterpret_cast<char *>(out) + blockIdx.z * ib) +
+           blockIdx.y * planeOut;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < p.total;
        o += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = o, off = 0;
@@ -345,13 +382,14 @@ __global__ void k_permute(const PermParams p, const E *__restrict__ in, E *__res
 }
 
 cudaError_t launch_permute(const PermParams &p, const void *xin, void *xout, const uint64_t *nin,
-                           uint64_t *nout, cudaStream_t st) {
+                           uint64_t *nout, const Batch &bt, cudaStream_t st) {
   if (p.total == 0) return cudaSuccess;
   int blocks = grid_for(p.total, 256);
-  k_permute<uint32_t><<<dim3(blocks, 1), 256, 0, st>>>(p, (const uint32_t *)xin, (uint32_t *)xout,
-                                                       0, 0);
+  k_permute<uint32_t><<<dim3(blocks, 1, bt.B), 256, 0, st>>>(p, (const uint32_t *)xin,
+                                                             (uint32_t *)xout, 0, 0, bt.ib);
   if (p.P > 0)
-    k_permute<uint64_t><<<dim3(blocks, p.P), 256, 0, st>>>(p, nin, nout, p.planeIn, p.planeOut);
+    k_permute<uint64_t><<<dim3(blocks, p.P, bt.B), 256, 0, st>>>(p, nin, nout, p.planeIn,
+                                                                 p.planeOut, bt.ib);
   return cudaGetLastError();
 }
 
@@ -545,7 +583,15 @@ __global__ void __launch_bounds__(256) k_chain(const ChainParams p, const T *__r
                                                const T *__restrict__ Ax,
                                                const uint64_t *__restrict__ An,
                                                T *__restrict__ Cx, uint64_t *__restrict__ Cn,
-                                               const PrimeSet ps) {
+                                               const PrimeSet ps, int64_t ib) {
+  X = inst_ptr(X, ib);
+  Ax = inst_ptr(Ax, ib);
+  Cx = inst_ptr(Cx, ib);
+  if (COUNT) {
+    Xn = inst_ptr(Xn, ib);
+    An = inst_ptr(An, ib);
+    Cn = inst_ptr(Cn, ib);
+  }
   extern __shared__ __align__(16) char smem[];
   T *s = reinterpret_cast<T *>(smem);
   T *sB = s + p.tile;
@@ -598,7 +644,7 @@ size_t chain_smem_bytes(const ChainParams &p, size_t elem) {
 template <typename T, int Q, bool COUNT>
 static cudaError_t launch_chain_t(const ChainParams &p, const char *arena, const void *Ax,
                                   const uint64_t *An, void *Cx, uint64_t *Cn, const PrimeSet &ps,
-                                  cudaStream_t st) {
+                                  const Batch &bt, cudaStream_t st) {
   size_t sm = chain_smem_bytes(p, sizeof(T));
   static size_t configured = 0;
   if (sm > 48 * 1024 && sm > configured) {
@@ -608,31 +654,31 @@ static cudaError_t launch_chain_t(const ChainParams &p, const char *arena, const
     configured = sm;
   }
   int64_t blocks = p.outer < 152 * 8 ? p.outer : 152 * 8;
-  k_chain<T, Q, COUNT><<<(int)blocks, 256, sm, st>>>(
+  k_chain<T, Q, COUNT><<<dim3((unsigned)blocks, bt.B), 256, sm, st>>>(
       p, reinterpret_cast<const T *>(arena), reinterpret_cast<const uint64_t *>(arena),
-      static_cast<const T *>(Ax), An, static_cast<T *>(Cx), Cn, ps);
+      static_cast<const T *>(Ax), An, static_cast<T *>(Cx), Cn, ps, bt.ib);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
-                          void *Cx, cudaStream_t st);
+                          void *Cx, const Batch &bt, cudaStream_t st);
 
 cudaError_t launch_chain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
                          const uint64_t *An, void *Cx, uint64_t *Cn, const PrimeSet &ps,
-                         cudaStream_t st) {
+                         const Batch &bt, cudaStream_t st) {
   if (p.outer == 0) return cudaSuccess;
-  if (p.mode == 1) return launch_rchain(dt, p, arena, Ax, Cx, st);
+  if (p.mode == 1) return launch_rchain(dt, p, arena, Ax, Cx, bt, st);
   const bool c = p.P > 0;
   if (dt == DT_F32) {
-    if (p.q == 2) return c ? launch_chain_t<float, 2, true>(p, arena, Ax, An, Cx, Cn, ps, st)
-                           : launch_chain_t<float, 2, false>(p, arena, Ax, An, Cx, Cn, ps, st);
-    return c ? launch_chain_t<float, 3, true>(p, arena, Ax, An, Cx, Cn, ps, st)
-             : launch_chain_t<float, 3, false>(p, arena, Ax, An, Cx, Cn, ps, st);
+    if (p.q == 2) return c ? launch_chain_t<float, 2, true>(p, arena, Ax, An, Cx, Cn, ps, bt, st)
+                           : launch_chain_t<float, 2, false>(p, arena, Ax, An, Cx, Cn, ps, bt, st);
+    return c ? launch_chain_t<float, 3, true>(p, arena, Ax, An, Cx, Cn, ps, bt, st)
+             : launch_chain_t<float, 3, false>(p, arena, Ax, An, Cx, Cn, ps, bt, st);
   }
-  if (p.q == 2) return c ? launch_chain_t<int32_t, 2, true>(p, arena, Ax, An, Cx, Cn, ps, st)
-                         : launch_chain_t<int32_t, 2, false>(p, arena, Ax, An, Cx, Cn, ps, st);
-  return c ? launch_chain_t<int32_t, 3, true>(p, arena, Ax, An, Cx, Cn, ps, st)
-           : launch_chain_t<int32_t, 3, false>(p, arena, Ax, An, Cx, Cn, ps, st);
+  if (p.q == 2) return c ? launch_chain_t<int32_t, 2, true>(p, arena, Ax, An, Cx, Cn, ps, bt, st)
+                         : launch_chain_t<int32_t, 2, false>(p, arena, Ax, An, Cx, Cn, ps, bt, st);
+  return c ? launch_chain_t<int32_t, 3, true>(p, arena, Ax, An, Cx, Cn, ps, bt, st)
+           : launch_chain_t<int32_t, 3, false>(p, arena, Ax, An, Cx, Cn, ps, bt, st);
 }
 
 // Traceback of one chain record by the whole block: reload the input tile,
@@ -811,26 +857,68 @@ __device__ __forceinline__ void rc_diag(T (&v)[1 << RB], const ChainGate &g, con
 #undef RC_D
 }
 
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+template <int RB>
+__device__ __forceinline__ int64_t rc_base(const ChainParams &p, int64_t tau) {
+  int64_t base = 0;
+  for (int sg = p.nseg - 1; sg >= 0; --sg) {
+    base += (tau & (p.seg_size[sg] - 1)) * p.seg_s[sg];
+    tau >>= p.seg_sh[sg];
+  }
+  return base;
+}
+
+// Every thread walks its outer indices with a two-stage pipeline: the 2^RB
+// elements of the next index are copied global -> shared memory with
+// cp.async (into the thread's own column of a [2^RB][threads] stage, so no
+// block barrier is needed) while the current ones are transformed in
+// registers and stored.
 template <typename T, int RB>
-__global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainParams p, const T *__restrict__ X,
-                                                   const T *__restrict__ A, T *__restrict__ C) {
+__global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainParams p,
+                                                                  const T *__restrict__ X,
+                                                                  const T *__restrict__ A,
+                                                                  T *__restrict__ C, int64_t ib) {
+  X = inst_ptr(X, ib);
+  A = inst_ptr(A, ib);
+  C = inst_ptr(C, ib);
   __shared__ T sB[TN_CHAIN_MAX_G * kGateBMax];
   __shared__ int64_t soff[1 << RB];
+  extern __shared__ __align__(16) char rstage[];
+  T *stage = reinterpret_cast<T *>(rstage);
   load_gate_operands<T>(p, X, nullptr, sB, nullptr, kGateBMax);
   for (int e = threadIdx.x; e < (1 << RB); e += blockDim.x) soff[e] = p.hi_off[e];
   __syncthreads();
-  // offsets are re-read at the store instead of being kept live in registers
-  const volatile int64_t *voff = soff;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t tau = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tau < p.outer; tau += stride) {
-    int64_t r = tau, base = 0;
-    for (int sg = p.nseg - 1; sg >= 0; --sg) {
-      base += (r & (p.seg_size[sg] - 1)) * p.seg_s[sg];
-      r >>= p.seg_sh[sg];
+  const int nt = blockDim.x, tid = threadIdx.x;
+  T *buf[2] = {stage, stage + (1 << RB) * nt};
+  const int64_t step = (int64_t)gridDim.x * nt;
+  int64_t tau = blockIdx.x * (int64_t)nt + tid;
+  auto issue = [&](int64_t t, T *dst) {
+    if (t < p.outer) {
+      const int64_t b = rc_base<RB>(p, t);
+#pragma unroll
+      for (int e = 0; e < (1 << RB); ++e) cp_async4(dst + e * nt + tid, A + b + soff[e]);
     }
+    cp_async_commit();
+  };
+  issue(tau, buf[0]);
+  for (int it = 0; tau < p.outer; tau += step, ++it) {
+    T *cur = buf[it & 1];
+    issue(tau + step, buf[(it + 1) & 1]);
+    cp_async_wait_prev();
+    const int64_t base = rc_base<RB>(p, tau);
     T v[1 << RB];
 #pragma unroll
-    for (int e = 0; e < (1 << RB); ++e) v[e] = A[base + voff[e]];
+    for (int e = 0; e < (1 << RB); ++e) v[e] = cur[e * nt + tid];
     for (int gi = 0; gi < p.ngates; ++gi) {
       const ChainGate &g = p.g[gi];
       const T *gB = sB + gi * kGateBMax;
@@ -847,8 +935,9 @@ __global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainPara
       }
     }
 #pragma unroll
-    for (int e = 0; e < (1 << RB); ++e) C[base + voff[e]] = v[e];
+    for (int e = 0; e < (1 << RB); ++e) C[base + soff[e]] = v[e];
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // Traceback of a register chain by one warp: lane e holds element e of the
@@ -930,32 +1019,39 @@ __device__ void trace_rchain(const ChainTrace &ct, const T *X, int8_t *state, in
   (void)sbase;
 }
 
-cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
-                          void *Cx, cudaStream_t st) {
-  if (p.outer == 0) return cudaSuccess;
-  int64_t blocks = (p.outer + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  if (p.t != 4 && p.t != 5) return cudaErrorInvalidValue;
-  if (dt == DT_F32) {
-    if (p.t == 5)
-      k_rchain<float, 5><<<(int)blocks, 256, 0, st>>>(p, reinterpret_cast<const float *>(arena),
-                                                      static_cast<const float *>(Ax),
-                                                      static_cast<float *>(Cx));
-    else
-      k_rchain<float, 4><<<(int)blocks, 256, 0, st>>>(p, reinterpret_cast<const float *>(arena),
-                                                      static_cast<const float *>(Ax),
-                                                      static_cast<float *>(Cx));
-  } else {
-    if (p.t == 5)
-      k_rchain<int32_t, 5><<<(int)blocks, 256, 0, st>>>(
-          p, reinterpret_cast<const int32_t *>(arena), static_cast<const int32_t *>(Ax),
-          static_cast<int32_t *>(Cx));
-    else
-      k_rchain<int32_t, 4><<<(int)blocks, 256, 0, st>>>(
-          p, reinterpret_cast<const int32_t *>(arena), static_cast<const int32_t *>(Ax),
-          static_cast<int32_t *>(Cx));
+template <typename T, int RB>
+static cudaError_t launch_rchain_t(const ChainParams &p, const char *arena, const void *Ax,
+                                   void *Cx, int blocks, size_t smem, const Batch &bt,
+                                   cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_rchain<T, RB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
   }
+  k_rchain<T, RB><<<dim3(blocks, bt.B), 256, smem, st>>>(
+      p, reinterpret_cast<const T *>(arena), static_cast<const T *>(Ax), static_cast<T *>(Cx),
+      bt.ib);
   return cudaGetLastError();
+}
+
+cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
+                          void *Cx, const Batch &bt, cudaStream_t st) {
+  if (p.outer == 0) return cudaSuccess;
+  if (p.t != 4 && p.t != 5) return cudaErrorInvalidValue;
+  // resident blocks only (2 or 4 per SM); each thread then pipelines several indices
+  const int per_sm = p.t == 5 ? 2 : 4;
+  int64_t blocks = (p.outer + 255) / 256;
+  const int64_t cap = std::max<int64_t>(1, 152 * per_sm / bt.B);
+  if (blocks > cap) blocks = cap;
+  const size_t smem = (size_t)2 * (1 << p.t) * 256 * 4;
+  if (dt == DT_F32) {
+    if (p.t == 5) return launch_rchain_t<float, 5>(p, arena, Ax, Cx, (int)blocks, smem, bt, st);
+    return launch_rchain_t<float, 4>(p, arena, Ax, Cx, (int)blocks, smem, bt, st);
+  }
+  if (p.t == 5) return launch_rchain_t<int32_t, 5>(p, arena, Ax, Cx, (int)blocks, smem, bt, st);
+  return launch_rchain_t<int32_t, 4>(p, arena, Ax, Cx, (int)blocks, smem, bt, st);
 }
 
 // ---------------------------------------------------------------- traceback
@@ -963,7 +1059,7 @@ cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, con
 // Steps are processed in order (the host lists them top-down).  For each, the
 // fixed legs select the slice of A and B, the block finds the first k that
 // maximises A + B, and the contracted spins take the digits of k.
-constexpr int kTraceThreads = 1024;
+constexpr int kTraceThreads = 32;   // one warp walks the records
 
 // (value, k) pair reduction keeping the larger value, the smaller k on ties.
 template <typename T>
@@ -984,30 +1080,44 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceStep *__rest
                                                          int nsteps,
                                                          const ChainTrace *__restrict__ chains,
                                                          const char *__restrict__ arena,
-                                                         int8_t *state, int nspins, int *err) {
+                                                         int8_t *state, int nspins, int *err,
+                                                         int64_t ib) {
+  // one block per instance: its arena slice and its spin state
+  arena += blockIdx.x * ib;
+  state += (int64_t)blockIdx.x * nspins;
   extern __shared__ __align__(16) char tsmem[];
   int8_t *sst = reinterpret_cast<int8_t *>(tsmem);
   char *work = tsmem + ((nspins + 15) / 16) * 16;
   const T *X = reinterpret_cast<const T *>(arena);
   __shared__ int64_t sbase[2];
-  __shared__ T sv[32];
-  __shared__ int sk[32];
   __shared__ int serr;
   if (threadIdx.x == 0) serr = 0;
   for (int i = threadIdx.x; i < nspins; i += blockDim.x) sst[i] = state[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   // each record is copied into shared memory with one cooperative load
   __shared__ __align__(16) unsigned long long srec[(sizeof(ChainTrace) + 7) / 8];
   for (int s = 0; s < nsteps; ++s) {
     const int chain = steps[s].chain;
     {
+      // all loads of the record are issued before any store (one round trip)
       const unsigned long long *src = chain >= 0
           ? reinterpret_cast<const unsigned long long *>(&chains[chain])
           : reinterpret_cast<const unsigned long long *>(&steps[s]);
       const int words = (int)((chain >= 0 ? sizeof(ChainTrace) : sizeof(TraceStep)) / 8);
+      constexpr int kPer = (int)((sizeof(ChainTrace) / 8 + kTraceThreads - 1) / kTraceThreads);
+      unsigned long long tmp[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int w = threadIdx.x + i * kTraceThreads;
+        tmp[i] = w < words ? src[w] : 0ull;
+      }
       __syncthreads();
-      for (int w = threadIdx.x; w < words; w += blockDim.x) srec[w] = src[w];
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int w = threadIdx.x + i * kTraceThreads;
+        if (w < words) srec[w] = tmp[i];
+      }
       __syncthreads();
     }
     if (chain >= 0) {
@@ -1019,24 +1129,27 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceStep *__rest
       continue;
     }
     const TraceStep &st = *reinterpret_cast<const TraceStep *>(srec);
-    if (warp < 2) {
-      // warp 0 sums A's fixed legs, warp 1 B's
-      const int nf = warp == 0 ? st.nfa : (st.offB >= 0 ? st.nfb : 0);
-      int64_t part = 0;
-      for (int i = lane; i < nf; i += 32) {
-        const int sp = warp == 0 ? st.fa_spin[i] : st.fb_spin[i];
-        int d = sst[sp];
-        if (d < 0 || d >= Q) { serr = 1; d = 0; }
-        part += (int64_t)d * (warp == 0 ? st.fa_stride[i] : st.fb_stride[i]);
-      }
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-      if (lane == 0) sbase[warp] = (warp == 0 ? st.offA : st.offB) + part;
+    // one warp: fixed legs select the slices of A and B
+    int64_t pa = 0, pb = 0;
+    for (int i = lane; i < st.nfa; i += 32) {
+      int d = sst[st.fa_spin[i]];
+      if (d < 0 || d >= Q) { serr = 1; d = 0; }
+      pa += (int64_t)d * st.fa_stride[i];
     }
-    __syncthreads();
-    const int64_t ba = sbase[0], bb = sbase[1];
+    if (st.offB >= 0)
+      for (int i = lane; i < st.nfb; i += 32) {
+        int d = sst[st.fb_spin[i]];
+        if (d < 0 || d >= Q) { serr = 1; d = 0; }
+        pb += (int64_t)d * st.fb_stride[i];
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      pa += __shfl_xor_sync(0xffffffffu, pa, o);
+      pb += __shfl_xor_sync(0xffffffffu, pb, o);
+    }
+    const int64_t ba = st.offA + pa, bb = st.offB + pb;
     T best = Lim<T>::neg();
     int bk = 0x7fffffff;
-    for (int k = threadIdx.x; k < st.Ks; k += blockDim.x) {
+    for (int k = lane; k < st.Ks; k += 32) {
       int64_t oa = ba, ob = bb;
       int r = k;
       for (int j = st.nk - 1; j >= 0; --j) {
@@ -1050,30 +1163,18 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceStep *__rest
       argmax_merge(best, bk, v, k);
     }
     for (int o = 16; o > 0; o >>= 1) {
-      T v2 = __shfl_down_sync(0xffffffffu, best, o);
-      int k2 = __shfl_down_sync(0xffffffffu, bk, o);
+      T v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      int k2 = __shfl_xor_sync(0xffffffffu, bk, o);
       argmax_merge(best, bk, v2, k2);
     }
-    if (lane == 0) { sv[warp] = best; sk[warp] = bk; }
-    __syncthreads();
-    if (warp == 0) {
-      const int nw = blockDim.x / 32;
-      best = lane < nw ? sv[lane] : Lim<T>::neg();
-      bk = lane < nw ? sk[lane] : 0x7fffffff;
-      for (int o = 16; o > 0; o >>= 1) {
-        T v2 = __shfl_down_sync(0xffffffffu, best, o);
-        int k2 = __shfl_down_sync(0xffffffffu, bk, o);
-        argmax_merge(best, bk, v2, k2);
-      }
-      if (lane == 0) {
-        int r = bk;
-        for (int j = st.nk - 1; j >= 0; --j) {
-          sst[st.k_spin[j]] = (int8_t)(r % Q);
-          r /= Q;
-        }
+    if (lane == 0) {
+      int r = bk;
+      for (int j = st.nk - 1; j >= 0; --j) {
+        sst[st.k_spin[j]] = (int8_t)(r % Q);
+        r /= Q;
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
   for (int i = threadIdx.x; i < nspins; i += blockDim.x) state[i] = sst[i];
   if (threadIdx.x == 0 && serr) *err = 1;
@@ -1090,7 +1191,7 @@ size_t trace_state_bytes(int nspins) { return ((size_t)(nspins + 15) / 16) * 16;
 template <typename T, int Q>
 static cudaError_t launch_trace_t(const TraceStep *d_steps, int nsteps, const ChainTrace *chains,
                                   size_t smem, const char *arena, int8_t *state, int nspins,
-                                  int *err, cudaStream_t st) {
+                                  int *err, const Batch &bt, cudaStream_t st) {
   smem += trace_state_bytes(nspins);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
@@ -1099,30 +1200,33 @@ static cudaError_t launch_trace_t(const TraceStep *d_steps, int nsteps, const Ch
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  k_trace<T, Q><<<1, kTraceThreads, smem, st>>>(d_steps, nsteps, chains, arena, state, nspins,
-                                                err);
+  k_trace<T, Q><<<bt.B, kTraceThreads, smem, st>>>(d_steps, nsteps, chains, arena, state, nspins,
+                                                   err, bt.ib);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trace(Dtype dt, int q, const TraceStep *d_steps, int nsteps,
                          const ChainTrace *d_chains, size_t smem, const char *arena, int8_t *state,
-                         int nspins, int *err, cudaStream_t st) {
+                         int nspins, int *err, const Batch &bt, cudaStream_t st) {
   if (nsteps == 0) return cudaSuccess;
   if (dt == DT_F32)
     return q == 2 ? launch_trace_t<float, 2>(d_steps, nsteps, d_chains, smem, arena, state, nspins,
-                                             err, st)
+                                             err, bt, st)
                   : launch_trace_t<float, 3>(d_steps, nsteps, d_chains, smem, arena, state, nspins,
-                                             err, st);
+                                             err, bt, st);
   return q == 2 ? launch_trace_t<int32_t, 2>(d_steps, nsteps, d_chains, smem, arena, state, nspins,
-                                             err, st)
+                                             err, bt, st)
                 : launch_trace_t<int32_t, 3>(d_steps, nsteps, d_chains, smem, arena, state, nspins,
-                                             err, st);
+                                             err, bt, st);
 }
 
 // ---------------------------------------------------------------- gradient / output
 
 __global__ void k_grad(int q, int n, int m, const int32_t *eu, const int32_t *ev,
                        const int8_t *state, float *dJ, float *dh) {
+  state += (int64_t)blockIdx.y * n;
+  if (dJ) dJ += (int64_t)blockIdx.y * m;
+  if (dh) dh += (int64_t)blockIdx.y * n;
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < m && dJ) {
     int a = state[eu[t]], b = state[ev[t]];
@@ -1135,21 +1239,24 @@ __global__ void k_grad(int q, int n, int m, const int32_t *eu, const int32_t *ev
 }
 
 cudaError_t launch_grad(int q, int n, int m, const int32_t *eu, const int32_t *ev,
-                        const int8_t *state, float *dJ, float *dh, cudaStream_t st) {
+                        const int8_t *state, float *dJ, float *dh, int B, cudaStream_t st) {
   int64_t tot = n > m ? n : m;
   if (tot == 0) return cudaSuccess;
-  k_grad<<<(int)((tot + 255) / 256), 256, 0, st>>>(q, n, m, eu, ev, state, dJ, dh);
+  k_grad<<<dim3((unsigned)((tot + 255) / 256), B), 256, 0, st>>>(q, n, m, eu, ev, state, dJ, dh);
   return cudaGetLastError();
 }
 
 __global__ void k_state_out(int q, int n, const int8_t *state, int8_t *out) {
+  state += (int64_t)blockIdx.y * n;
+  out += (int64_t)blockIdx.y * n;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) out[t] = (q == 2) ? (int8_t)(1 - 2 * state[t]) : state[t];
 }
 
-cudaError_t launch_state_out(int q, int n, const int8_t *state, int8_t *out, cudaStream_t st) {
+cudaError_t launch_state_out(int q, int n, const int8_t *state, int8_t *out, int B,
+                             cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_state_out<<<(n + 255) / 256, 256, 0, st>>>(q, n, state, out);
+  k_state_out<<<dim3((n + 255) / 256, B), 256, 0, st>>>(q, n, state, out);
   return cudaGetLastError();
 }
 

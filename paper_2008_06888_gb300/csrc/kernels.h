@@ -9,28 +9,35 @@ namespace tn {
 
 enum Dtype { DT_I32 = 1, DT_F32 = 2 };
 
+// A batch of B instances sharing one plan: instance b uses the arena slice
+// at b * ib bytes and the couplings J + b * jstride, h + b * hstride.
+struct Batch {
+  int B = 1;
+  int64_t ib = 0, jstride = 0, hstride = 0;
+};
+
 // Leaves (Sec. II bond / vertex tensors).  x: base of the value arena (bytes),
 // counts: when P > 0 every leaf element gets count 1 in each residue plane.
 cudaError_t launch_leaves(Dtype dt, int q, const LeafDesc *d_leaves, int nleaves, const float *J,
-                          const float *h, char *arena, int P, cudaStream_t st);
+                          const float *h, char *arena, int P, const Batch &bt, cudaStream_t st);
 
 // Gate contraction (small B); xA/xB/xC value pointers, nA/nB/nC plane-0
 // pointers (counting only).
 cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const void *xB, void *xC,
                         const uint64_t *nA, const uint64_t *nB, uint64_t *nC, const PrimeSet &ps,
-                        cudaStream_t st);
+                        const Batch &bt, cudaStream_t st);
 
 // Tiled strided batched max-plus GEMM, values only.
 cudaError_t launch_gemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
-                        cudaStream_t st);
+                        const Batch &bt, cudaStream_t st);
 // Residue planes of a counting GEMM whose values C were produced already.
 cudaError_t launch_gemm_count(Dtype dt, const GemmParams &p, const void *xA, const void *xB,
                               const void *xC, const uint64_t *nA, const uint64_t *nB, uint64_t *nC,
-                              const PrimeSet &ps, cudaStream_t st);
+                              const PrimeSet &ps, const Batch &bt, cudaStream_t st);
 
 // Permutation of a tensor (values and, when P > 0, its residue planes).
 cudaError_t launch_permute(const PermParams &p, const void *xin, void *xout, const uint64_t *nin,
-                           uint64_t *nout, cudaStream_t st);
+                           uint64_t *nout, const Batch &bt, cudaStream_t st);
 
 // Argmax traceback over steps [0, nsteps) of d_steps (Sec. III).
 // *err is set to 1 if a step meets an unassigned spin (a planning error).
@@ -39,21 +46,22 @@ cudaError_t launch_permute(const PermParams &p, const void *xin, void *xout, con
 // The spin state (nspins int8) is staged in shared memory during the walk.
 cudaError_t launch_trace(Dtype dt, int q, const TraceStep *d_steps, int nsteps,
                          const ChainTrace *d_chains, size_t smem, const char *arena, int8_t *state,
-                         int nspins, int *err, cudaStream_t st);
+                         int nspins, int *err, const Batch &bt, cudaStream_t st);
 size_t trace_smem_bytes(const ChainParams &p, size_t elem);
 
 // Fused gate chain over tiles of the big tensor (values; planes when P > 0).
 cudaError_t launch_chain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
                          const uint64_t *An, void *Cx, uint64_t *Cn, const PrimeSet &ps,
-                         cudaStream_t st);
+                         const Batch &bt, cudaStream_t st);
 size_t chain_smem_bytes(const ChainParams &p, size_t elem);
 
 // dE/dJ and dE/dh at the traced state.
 cudaError_t launch_grad(int q, int n, int m, const int32_t *eu, const int32_t *ev,
-                        const int8_t *state, float *dJ, float *dh, cudaStream_t st);
+                        const int8_t *state, float *dJ, float *dh, int B, cudaStream_t st);
 
 // Convert a state (indices) to the +-1 / 0..q-1 convention of tn_config.
-cudaError_t launch_state_out(int q, int n, const int8_t *state, int8_t *out, cudaStream_t st);
+cudaError_t launch_state_out(int q, int n, const int8_t *state, int8_t *out, int B,
+                             cudaStream_t st);
 
 // Static scratch of tn_energy_noalloc (noalloc.cu): its size, its device
 // address on the current device (looked up once per device), and the kernel

@@ -63,8 +63,10 @@ struct Program {
   double macs = 0;                   // tropical multiply-adds of the forward steps
   // CUDA graphs of op ranges, captured on the second run of a range
   struct Graph {
-    int begin, end, runs;
+    int begin, end, runs, B;
     const char *arena;
+    const float *J, *h;
+    const int8_t *state;
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;

@@ -386,3 +386,65 @@ def test_repeated_calls_replay_graphs_identically():
     o = O.solve(dict(inst, J=J2), order=I.square_sweep_order(14))
     c, _, E = sg.count(3)
     assert (sg.energy(), E, c) == (o["E"], o["E"], o["count"])
+
+
+# ------------------------------------------------------------ batches on one plan
+
+def test_config_batch_matches_single_instances():
+    base = I.square_lattice(12, coupling="gauss", field_sigma=0.1, seed=40)
+    insts = [I.square_lattice(12, coupling="gauss", field_sigma=0.1, seed=40 + k) for k in range(5)]
+    sg = P.SpinGlass(base, order="greedy", seed=1)
+    J = np.stack([x["J"] for x in insts])
+    h = np.stack([x["h"] for x in insts])
+    E, sig = sg.config_batch(J, h)
+    for k, x in enumerate(insts):
+        sg.set_couplings(J=x["J"], h=x["h"])
+        s1, E1 = sg.config()
+        assert E[k] == E1 and np.array_equal(sig[k], s1)
+    o = O.solve(insts[3], count=False)
+    assert close(E[3], o["E"])
+    assert np.array_equal(P.SpinGlass.state_indices(sig[3], 2), o["state"])
+    Eb = sg.energy_batch(J, h)
+    assert np.array_equal(Eb, E)
+
+
+def test_config_batch_device_tensors_and_graph_replay():
+    import torch
+    insts = [I.square_lattice(14, coupling="gauss", field_sigma=0.1, seed=60 + k) for k in range(4)]
+    sg = P.SpinGlass(insts[0], order="greedy", seed=2)
+    J = torch.tensor(np.stack([x["J"] for x in insts]), device="cuda")
+    h = torch.tensor(np.stack([x["h"] for x in insts]), device="cuda")
+    first = sg.config_batch(J, h)
+    for _ in range(3):
+        again = sg.config_batch(J, h)
+        assert np.array_equal(first[0], again[0]) and np.array_equal(first[1], again[1])
+    for k in (0, 3):
+        o = O.solve(insts[k], count=False)
+        assert close(first[0][k], o["E"])
+
+
+def test_count_batch_pm_and_potts():
+    insts = [I.square_lattice(9, coupling="pm1", seed=80 + k) for k in range(6)]
+    sg = P.SpinGlass(insts[0], order="greedy", seed=1)
+    E, counts, status = sg.count_batch(np.stack([x["J"] for x in insts]))
+    assert np.all(status == 0)
+    for k, x in enumerate(insts):
+        o = O.solve(x)
+        assert (E[k], counts[k]) == (o["E"], o["count"])
+    pin = [I.potts_square(6, coupling="gauss", seed=90 + k) for k in range(3)]
+    sp = P.SpinGlass(pin[0], order="sweep", seq=I.square_sweep_order(6))
+    E, counts, status = sp.count_batch(np.stack([x["J"] for x in pin]))
+    for k, x in enumerate(pin):
+        o = O.solve(x, order=I.square_sweep_order(6))
+        assert close(E[k], o["E"]) and counts[k] == o["count"]
+
+
+def test_batch_run_groups_mixed_sizes():
+    insts = I.mixed_square_batch(20, Lmin=4, Lmax=9, seed=5)
+    sgs = [P.SpinGlass(x, order="sweep", seq=I.square_sweep_order(int(round(np.sqrt(x["n"])))))
+           for x in insts]
+    st, E, counts, status = B.tn_batch_run([s.ctx for s in sgs])
+    assert st == 0 and np.all(status == 0)
+    for k, x in enumerate(insts):
+        o = O.solve(x)
+        assert E[k] == o["E"] and counts[k] == o["count"]

@@ -868,12 +868,15 @@ __device__ __forceinline__ void cp_async_wait_prev() {
   asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
-template <int RB>
-__device__ __forceinline__ int64_t rc_base(const ChainParams &p, int64_t tau) {
-  int64_t base = 0;
+// Offset of the tensor element of outer index tau (legs other than the
+// register legs); every size and stride is a power of two.
+template <typename I>
+__device__ __forceinline__ I rc_base(const ChainParams &p, int64_t tau) {
+  I base = 0;
+  I t = (I)tau;
   for (int sg = p.nseg - 1; sg >= 0; --sg) {
-    base += (tau & (p.seg_size[sg] - 1)) * p.seg_s[sg];
-    tau >>= p.seg_sh[sg];
+    base += (t & (I)(p.seg_size[sg] - 1)) << p.seg_ssh[sg];
+    t >>= p.seg_sh[sg];
   }
   return base;
 }
@@ -882,8 +885,10 @@ __device__ __forceinline__ int64_t rc_base(const ChainParams &p, int64_t tau) {
 // elements of the next index are copied global -> shared memory with
 // cp.async (into the thread's own column of a [2^RB][threads] stage, so no
 // block barrier is needed) while the current ones are transformed in
-// registers and stored.
-template <typename T, int RB>
+// registers and stored.  Element offsets of the register legs are built
+// incrementally from the RB leg strides; I is the index type (32-bit when
+// the tensor has fewer than 2^31 elements).
+template <typename T, int RB, typename I>
 __global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainParams p,
                                                                   const T *__restrict__ X,
                                                                   const T *__restrict__ A,
@@ -892,21 +897,29 @@ __global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainPara
   A = inst_ptr(A, ib);
   C = inst_ptr(C, ib);
   __shared__ T sB[TN_CHAIN_MAX_G * kGateBMax];
-  __shared__ int64_t soff[1 << RB];
   extern __shared__ __align__(16) char rstage[];
   T *stage = reinterpret_cast<T *>(rstage);
   load_gate_operands<T>(p, X, nullptr, sB, nullptr, kGateBMax);
-  for (int e = threadIdx.x; e < (1 << RB); e += blockDim.x) soff[e] = p.hi_off[e];
   __syncthreads();
+  I sS[RB];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) sS[j] = (I)p.hi_off[1 << j];
   const int nt = blockDim.x, tid = threadIdx.x;
   T *buf[2] = {stage, stage + (1 << RB) * nt};
   const int64_t step = (int64_t)gridDim.x * nt;
   int64_t tau = blockIdx.x * (int64_t)nt + tid;
   auto issue = [&](int64_t t, T *dst) {
     if (t < p.outer) {
-      const int64_t b = rc_base<RB>(p, t);
+      const T *src = A + rc_base<I>(p, t);
+      I o[1 << RB];
+      o[0] = 0;
 #pragma unroll
-      for (int e = 0; e < (1 << RB); ++e) cp_async4(dst + e * nt + tid, A + b + soff[e]);
+      for (int e = 1; e < (1 << RB); ++e) {
+        const int hb = 31 - __clz(e);
+        o[e] = o[e ^ (1 << hb)] + sS[hb];
+      }
+#pragma unroll
+      for (int e = 0; e < (1 << RB); ++e) cp_async4(dst + e * nt + tid, src + o[e]);
     }
     cp_async_commit();
   };
@@ -915,7 +928,8 @@ __global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainPara
     T *cur = buf[it & 1];
     issue(tau + step, buf[(it + 1) & 1]);
     cp_async_wait_prev();
-    const int64_t base = rc_base<RB>(p, tau);
+    const I bi = rc_base<I>(p, tau);
+    const int64_t base = bi;
     T v[1 << RB];
 #pragma unroll
     for (int e = 0; e < (1 << RB); ++e) v[e] = cur[e * nt + tid];
@@ -934,8 +948,16 @@ __global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainPara
         default: rc_replace<RB, RB - 1>(v, g, gB, base); break;
       }
     }
+    T *dst = C + bi;
+    I o[1 << RB];
+    o[0] = 0;
 #pragma unroll
-    for (int e = 0; e < (1 << RB); ++e) C[base + soff[e]] = v[e];
+    for (int e = 1; e < (1 << RB); ++e) {
+      const int hb = 31 - __clz(e);
+      o[e] = o[e ^ (1 << hb)] + sS[hb];
+    }
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) dst[o[e]] = v[e];
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
@@ -1019,21 +1041,31 @@ __device__ void trace_rchain(const ChainTrace &ct, const T *X, int8_t *state, in
   (void)sbase;
 }
 
-template <typename T, int RB>
-static cudaError_t launch_rchain_t(const ChainParams &p, const char *arena, const void *Ax,
+template <typename T, int RB, typename I>
+static cudaError_t launch_rchain_i(const ChainParams &p, const char *arena, const void *Ax,
                                    void *Cx, int blocks, size_t smem, const Batch &bt,
                                    cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_rchain<T, RB>,
+    cudaError_t e = cudaFuncSetAttribute(k_rchain<T, RB, I>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_rchain<T, RB><<<dim3(blocks, bt.B), 256, smem, st>>>(
+  k_rchain<T, RB, I><<<dim3(blocks, bt.B), 256, smem, st>>>(
       p, reinterpret_cast<const T *>(arena), static_cast<const T *>(Ax), static_cast<T *>(Cx),
       bt.ib);
   return cudaGetLastError();
+}
+
+template <typename T, int RB>
+static cudaError_t launch_rchain_t(const ChainParams &p, const char *arena, const void *Ax,
+                                   void *Cx, int blocks, size_t smem, const Batch &bt,
+                                   cudaStream_t st) {
+  // tensor size = outer * 2^RB elements
+  if (p.outer * (int64_t(1) << RB) < (int64_t(1) << 31))
+    return launch_rchain_i<T, RB, int32_t>(p, arena, Ax, Cx, blocks, smem, bt, st);
+  return launch_rchain_i<T, RB, int64_t>(p, arena, Ax, Cx, blocks, smem, bt, st);
 }
 
 cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,

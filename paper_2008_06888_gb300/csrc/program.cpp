@@ -569,6 +569,8 @@ struct Builder {
       cp.seg_size[i] = sz[i];
       cp.seg_s[i] = st[i];
       cp.seg_sh[i] = sh[i];
+      cp.seg_ssh[i] = 0;
+      while ((int64_t(1) << cp.seg_ssh[i]) < st[i]) cp.seg_ssh[i]++;
     }
     cp.ngates = (int)m.gates.size();
     blocs->clear();

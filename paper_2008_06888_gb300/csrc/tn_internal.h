@@ -130,6 +130,7 @@ struct ChainParams {
   int64_t seg_size[TN_MAX_SEG];
   int64_t seg_s[TN_MAX_SEG];
   int32_t seg_sh[TN_MAX_SEG];  // log2(seg_size) when q == 2
+  int32_t seg_ssh[TN_MAX_SEG]; // log2(seg_s) when q == 2 (register chains)
   int64_t planeA, planeC;  // plane distances of input and output
   ChainGate g[TN_CHAIN_MAX_G];
 };

@@ -31,7 +31,7 @@ import numpy as np
 __all__ = [
     "square_lattice", "chimera", "random_regular3", "potts_square",
     "mixed_square_batch", "planted", "ferromagnet", "instance_digest",
-    "square_sweep_order",
+    "square_sweep_order", "chimera_sweep_order", "potts_planted",
 ]
 
 
@@ -113,6 +113,19 @@ def chimera_edges(L):
     return np.asarray(e, dtype=np.int32).reshape(-1, 2)
 
 
+def chimera_sweep_order(L):
+    """Spin sequence sweeping the chimera by cell rows: for each row of cells,
+    first every spin of the horizontally coupled halves, then every spin of
+    the vertically coupled halves (keeps about 4L + 1 spins live)."""
+    seq = []
+    for i in range(L):
+        for j in range(L):
+            seq += [8 * (i * L + j) + k for k in range(4, 8)]
+        for j in range(L):
+            seq += [8 * (i * L + j) + k for k in range(4)]
+    return np.asarray(seq, dtype=np.int32)
+
+
 def chimera(L, coupling="pm1", seed=0):
     rng = np.random.default_rng(seed)
     edges = chimera_edges(L)
@@ -183,6 +196,18 @@ def planted(inst, seed=0):
     J = (np.abs(inst["J"]) * tau[e[:, 0]] * tau[e[:, 1]]).astype(np.float32)
     out = dict(inst, J=J, h=None, name=inst["name"] + "-planted")
     return out, tau
+
+
+def potts_planted(inst, seed=0):
+    """Potts glass whose couplings are satisfied by a random colouring tau:
+    J_uv -> |J_uv| if tau_u == tau_v else -|J_uv|.  tau is a ground state and
+    E_min = -sum of the positive couplings.  Returns (instance, tau)."""
+    rng = np.random.default_rng(seed)
+    tau = rng.integers(0, inst["q"], size=inst["n"]).astype(np.int8)
+    e = inst["edges"]
+    same = tau[e[:, 0]] == tau[e[:, 1]]
+    J = np.where(same, np.abs(inst["J"]), -np.abs(inst["J"])).astype(np.float32)
+    return dict(inst, J=J, name=inst["name"] + "-planted"), tau
 
 
 def ferromagnet(inst):

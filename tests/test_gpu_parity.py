@@ -448,3 +448,37 @@ def test_batch_run_groups_mixed_sizes():
     for k, x in enumerate(insts):
         o = O.solve(x)
         assert E[k] == o["E"] and counts[k] == o["count"]
+
+
+# ------------------------------------------------------------ full-size workloads by closed forms
+
+def test_potts18_planted_energy_state_and_counts():
+    inst, tau = I.potts_planted(I.potts_square(18, seed=7), seed=8)
+    sg = P.SpinGlass(inst, order="sweep", seq=I.square_sweep_order(18))
+    exact = -float(np.maximum(inst["J"].astype(np.float64), 0).sum())
+    st, E = gpu_state(sg)
+    assert close(E, exact)
+    assert close(O.energy(inst, st), exact)
+    c, ln, E2 = sg.count(3)
+    assert E2 == E and c >= 6 and c % 6 == 0
+
+
+def test_chimera_counts_vs_oracle_with_cell_row_order():
+    for L, seed in ((3, 1), (4, 2)):
+        inst = I.chimera(L, coupling="pm1", seed=seed)
+        o = O.solve(inst, order=I.chimera_sweep_order(L))
+        sg = P.SpinGlass(inst, order="sweep", seq=I.chimera_sweep_order(L))
+        c, ln, E = sg.count(3)
+        assert (E, c) == (o["E"], o["count"])
+        st, E2 = gpu_state(sg)
+        assert O.energy(inst, st) == o["E"]
+
+
+def test_chimera6_planted_counts():
+    inst, tau = I.planted(I.chimera(6, coupling="pm1", seed=3), seed=4)
+    sg = P.SpinGlass(inst, order="sweep", seq=I.chimera_sweep_order(6))
+    c, ln, E = sg.count(3)
+    assert E == -float(len(inst["J"])) and c == 2
+    st, E2 = gpu_state(sg)
+    sig = 1 - 2 * st.astype(np.int64)
+    assert np.all(sig == tau) or np.all(sig == -tau)

@@ -350,3 +350,20 @@ def test_planted_sign_mistake_is_caught(monkeypatch):
     inst = _inst_from_case(_cases()[2])        # antiferromagnetic triangle
     s = E.solve(inst)
     assert (s["E"], s["count"]) != (-1.0, 6)
+
+
+def test_potts_planted_colouring_is_ground_state():
+    inst, tau = I.potts_planted(I.potts_square(3, 4, seed=2), seed=3)
+    b = O.brute_force(inst)
+    assert b["E"] == pytest.approx(-float(np.maximum(inst["J"].astype(np.float64), 0).sum()))
+    assert tuple(tau.tolist()) in set(map(tuple, b["states"].tolist()))
+
+
+def test_chimera_sweep_order_is_a_permutation_and_exact():
+    for L in (1, 2, 3):
+        seq = I.chimera_sweep_order(L)
+        assert sorted(seq.tolist()) == list(range(8 * L * L))
+    inst = I.chimera(2, coupling="pm1", seed=4)
+    a = O.solve(inst, order=I.chimera_sweep_order(2))
+    b = O.solve(inst)
+    assert (a["E"], a["count"]) == (b["E"], b["count"])

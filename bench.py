@@ -51,6 +51,8 @@ def parse():
                     help="config: E_min + sigma* (the workload); energy: E_min only (profiling)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--quiet", action="store_true", help="print only value and kernel shares")
+    ap.add_argument("--gemm", action="store_true",
+                    help="max-plus GEMM microbenchmark (FP32 and INT32) instead of the workload")
     return ap.parse_args()
 
 
@@ -202,10 +204,55 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gemm(args):
+    """Max-plus GEMM through tn_maxplus_gemm: square 4096^3 and batched shapes."""
+    import torch
+    from paper_2008_06888_gb300 import binding as B
+    torch.cuda.set_device(0)
+    pk, how = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    # non-tensor FP32 peak, an FMA counted as 2 ops: 152 SMs x 128 lanes x 2 x clock
+    peak_ops = 152 * 128 * 2 * sm_max * 1e6
+    out = {}
+    clocks = Clocks(0)
+    clocks.start()
+    for dt in (torch.float32, torch.int32):
+        for (bt, M, N, K) in [(1, 4096, 4096, 4096), (64, 512, 512, 512), (16, 1024, 1024, 256)]:
+            if dt == torch.float32:
+                A = torch.randn(bt, M, K, device="cuda")
+                Bm = torch.randn(bt, K, N, device="cuda")
+            else:
+                A = torch.randint(-100, 100, (bt, M, K), device="cuda", dtype=torch.int32)
+                Bm = torch.randint(-100, 100, (bt, K, N), device="cuda", dtype=torch.int32)
+            C = torch.empty(bt, M, N, device="cuda", dtype=dt)
+            for _ in range(3):
+                B.tn_maxplus_gemm(A, Bm, C)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record()
+            for _ in range(reps):
+                B.tn_maxplus_gemm(A, Bm, C)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            macs = bt * M * N * K
+            ops = 2 * macs / (ms * 1e-3)
+            out[f"{str(dt).split('.')[-1]}_{bt}x{M}x{N}x{K}"] = {
+                "ms": ms, "tropical_Top_s": ops / 1e12, "T_MAC_s": macs / (ms * 1e-3) / 1e12,
+                "frac_of_fp32_nontensor_peak": ops / peak_ops}
+    clk = clocks.stop()
+    print(json.dumps({"gemm": out, "peak_ops_per_s": peak_ops,
+                      "peak": "152 SMs x 128 FP32 lanes x 2 (FMA = 2 ops) x max SM clock",
+                      "clocks": clk}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.gemm:
+        return run_gemm(args)
     import torch
     import torch.distributed as dist
 

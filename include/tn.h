@@ -243,6 +243,20 @@ tn_status tn_plan_info(const tn_ctx *ctx, int32_t *n_steps, int32_t *n_transpose
 tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev, float *E_dev,
                             void *cuda_stream);
 
+/*
+ * tn_maxplus_gemm -- the batched max-plus GEMM of the pairwise steps (Eq. 2,
+ *   Sec. III), exposed on raw device buffers for testing and measurement:
+ *   C[b, m, n] = max_k (A[b, m, k] + B[b, k, n]).  dtype TN_DTYPE_F32 or
+ *   TN_DTYPE_I32 (4-byte elements).  A is [batch][M][K] (transA = 0) or
+ *   [batch][K][M] (transA = 1); B is [batch][K][N] (transB = 0) or
+ *   [batch][N][K] (transB = 1); C is [batch][M][N]; all row-major, device
+ *   memory owned by the caller.  Queued on cuda_stream, not waited for.
+ *   Errors: TN_EINVAL (bad sizes, NULL), TN_ECUDA (launch); tn_last_error(NULL).
+ */
+tn_status tn_maxplus_gemm(int32_t dtype, int64_t batch, int64_t M, int64_t N, int64_t K,
+                          const void *A, int32_t transA, const void *B, int32_t transB, void *C,
+                          void *cuda_stream);
+
 /* One-line reason for the last failing call on ctx (or of tn_build when ctx
  * is NULL).  Valid until the next call on the same context. */
 const char *tn_last_error(const tn_ctx *ctx);

@@ -52,6 +52,9 @@ _SIGS = {
     "tn_profile_reset": (C.c_int, [C.c_void_p]),
     "tn_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
+    "tn_maxplus_gemm": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                  C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                                  C.c_void_p]),
     "tn_last_error": (C.c_char_p, [C.c_void_p]),
     "tn_destroy": (None, [C.c_void_p]),
 }
@@ -279,6 +282,26 @@ def tn_energy_noalloc(ctx, J_ptr, h_ptr, E_ptr, stream_handle=0):
     _check(lib().tn_energy_noalloc(ctx, C.c_void_p(J_ptr), None if h_ptr is None else
                                    C.c_void_p(h_ptr), C.c_void_p(E_ptr),
                                    C.c_void_p(stream_handle)), ctx)
+
+
+def tn_maxplus_gemm(A, B, Cout, transA=False, transB=False, stream_handle=0):
+    """Cout[b] = max-plus product of A[b] and B[b] on CUDA torch tensors (float32 or int32).
+
+    A: (batch, M, K) or, with transA, (batch, K, M); B: (batch, K, N) or, with
+    transB, (batch, N, K); Cout: (batch, M, N).  Contiguous tensors.
+    """
+    import torch
+    dt = TN_DTYPE_F32 if A.dtype == torch.float32 else TN_DTYPE_I32
+    batch = A.shape[0]
+    M = A.shape[2] if transA else A.shape[1]
+    K = A.shape[1] if transA else A.shape[2]
+    N = B.shape[1] if transB else B.shape[2]
+    _check(lib().tn_maxplus_gemm(dt, batch, M, N, K, _tptr(A), int(transA), _tptr(B),
+                                 int(transB), _tptr(Cout), C.c_void_p(stream_handle)), None)
+
+
+def _tptr(t):
+    return C.c_void_p(t.data_ptr())
 
 
 def tn_last_error(ctx):

@@ -288,7 +288,7 @@ tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_
                         Nn(op.in1), Nn(op.out), ps, bt, st);
         break;
       case OP_GEMM:
-        e = launch_gemm(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out), bt, st);
+        e = launch_mpgemm(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out), bt, st);
         if (e == cudaSuccess && p.P > 0)
           e = launch_gemm_count(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out),
                                 Nn(op.in0), Nn(op.in1), Nn(op.out), ps, bt, st);
@@ -1070,7 +1070,7 @@ tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev,
                         nullptr, nullptr, ps, one, st);
         break;
       case OP_GEMM:
-        e = launch_gemm(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out), one, st);
+        e = launch_mpgemm(p.dt, p.gemms[op.idx], X(op.in0), X(op.in1), X(op.out), one, st);
         break;
       case OP_TRACE:
         break;
@@ -1083,6 +1083,35 @@ tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev,
       return fail(ctx, TN_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   }
   CK(launch_energy_out(p.dt, X(p.root), E_dev, st));
+  return TN_OK;
+}
+
+tn_status tn_maxplus_gemm(int32_t dtype, int64_t batch, int64_t M, int64_t N, int64_t K,
+                          const void *A, int32_t transA, const void *B, int32_t transB, void *C,
+                          void *cuda_stream) {
+  if ((dtype != TN_DTYPE_F32 && dtype != TN_DTYPE_I32) || batch < 0 || M < 0 || N < 0 || K < 1)
+    return fail(nullptr, TN_EINVAL, "tn_maxplus_gemm: bad dtype or sizes");
+  if (batch * M * N == 0) return TN_OK;
+  if (!A || !B || !C) return fail(nullptr, TN_EINVAL, "tn_maxplus_gemm: NULL operand");
+  GemmParams g{};
+  g.batch = batch;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.sAb = M * K;
+  g.sAm = transA ? 1 : K;
+  g.sAk = transA ? M : 1;
+  g.sBb = K * N;
+  g.sBk = transB ? 1 : N;
+  g.sBn = transB ? K : 1;
+  g.sCb = M * N;
+  g.sCm = N;
+  g.sCn = 1;
+  Batch one;
+  cudaError_t e = launch_mpgemm(dtype == TN_DTYPE_F32 ? DT_F32 : DT_I32, g, A, B, C, one,
+                                (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess)
+    return fail(nullptr, TN_ECUDA, std::string("tn_maxplus_gemm: ") + cudaGetErrorString(e));
   return TN_OK;
 }
 

@@ -64,6 +64,18 @@ __device__ __forceinline__ P *inst_ptr(P *p, int64_t ib) {
                                    static_cast<const void *>(p))) + blockIdx.y * ib);
 }
 
+// Asynchronous 4-byte global -> shared copies (cp.async) and their groups.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
 // ---------------------------------------------------------------- leaves
 
 template <typename T> __device__ __forceinline__ T to_val(float x);
@@ -301,6 +313,139 @@ cudaError_t launch_gemm(Dtype dt, const GemmParams &p, const void *A, const void
   else
     k_gemm<int32_t><<<blocks, 256, 0, st>>>(p, (const int32_t *)A, (const int32_t *)B,
                                             (int32_t *)C, bt.ib);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- register-tiled max-plus GEMM
+//
+// 128 x 128 output tile per block of 256 threads, 8 x 8 outputs per thread,
+// k slabs of 16 staged in shared memory by cp.async (two stages).  The
+// tropical multiply-add of two consecutive k is done with two adds and one
+// three-input max (FP32), the fastest form measured on GB300; INT32 uses
+// add + max.  Out-of-range operands read the tropical zero.
+
+__device__ __forceinline__ float tmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ int32_t tmax3(int32_t a, int32_t b, int32_t c) {
+  return max(max(a, b), c);
+}
+
+constexpr int GBM = 128, GBN = 128, GBK = 16, GPAD = 4;
+
+template <typename T>
+__device__ __forceinline__ void gemm_load_tile(const GemmParams &p, const T *Ab, const T *Bb,
+                                               int64_t m0, int64_t n0, int64_t k0, T *As, T *Bs) {
+  const int tid = threadIdx.x;
+  const T *a0 = Ab + m0 * p.sAm + k0 * p.sAk;
+  const T *b0 = Bb + k0 * p.sBk + n0 * p.sBn;
+  const int64_t mr = p.M - m0, kr = p.K - k0, nr = p.N - n0;
+  // A: GBM x GBK elements into As[k][m]
+#pragma unroll 2
+  for (int r = 0; r < (GBM * GBK) / 256; ++r) {
+    const int idx = tid + r * 256;
+    int m, k;
+    if (p.sAk == 1) { m = idx / GBK; k = idx % GBK; } else { k = idx / GBM; m = idx % GBM; }
+    T *dst = As + k * (GBM + GPAD) + m;
+    if (m < mr && k < kr) cp_async4(dst, a0 + m * p.sAm + k * p.sAk);
+    else *dst = Lim<T>::neg();
+  }
+  // B: GBK x GBN elements into Bs[k][n]
+#pragma unroll 2
+  for (int r = 0; r < (GBN * GBK) / 256; ++r) {
+    const int idx = tid + r * 256;
+    int n, k;
+    if (p.sBn == 1) { k = idx / GBN; n = idx % GBN; } else { n = idx / GBK; k = idx % GBK; }
+    T *dst = Bs + k * (GBN + GPAD) + n;
+    if (n < nr && k < kr) cp_async4(dst, b0 + k * p.sBk + n * p.sBn);
+    else *dst = Lim<T>::neg();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_mpgemm(const GemmParams p, const T *__restrict__ A,
+                                                   const T *__restrict__ B, T *__restrict__ C,
+                                                   int64_t ib) {
+  A = inst_ptr(A, ib);
+  B = inst_ptr(B, ib);
+  C = inst_ptr(C, ib);
+  __shared__ __align__(16) T As[2][GBK][GBM + GPAD];
+  __shared__ __align__(16) T Bs[2][GBK][GBN + GPAD];
+  const int64_t mt = (p.M + GBM - 1) / GBM, nt = (p.N + GBN - 1) / GBN;
+  const int64_t tiles = p.batch * mt * nt;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int64_t ksteps = (p.K + GBK - 1) / GBK;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t b = t / (mt * nt);
+    const int64_t rem = t % (mt * nt);
+    const int64_t m0 = (rem / nt) * GBM, n0 = (rem % nt) * GBN;
+    const T *Ab = A + b * p.sAb;
+    const T *Bb = B + b * p.sBb;
+    T acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = Lim<T>::neg();
+    __syncthreads();
+    gemm_load_tile<T>(p, Ab, Bb, m0, n0, 0, &As[0][0][0], &Bs[0][0][0]);
+    cp_async_commit();
+    for (int64_t ks = 0; ks < ksteps; ++ks) {
+      const int cur = ks & 1;
+      if (ks + 1 < ksteps)
+        gemm_load_tile<T>(p, Ab, Bb, m0, n0, (ks + 1) * GBK, &As[cur ^ 1][0][0], &Bs[cur ^ 1][0][0]);
+      cp_async_commit();
+      cp_async_wait_prev();
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GBK; kk += 2) {
+        T a0[8], a1[8], b0[8], b1[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          a0[i] = As[cur][kk][ty * 4 + i];
+          a0[4 + i] = As[cur][kk][64 + ty * 4 + i];
+          a1[i] = As[cur][kk + 1][ty * 4 + i];
+          a1[4 + i] = As[cur][kk + 1][64 + ty * 4 + i];
+          b0[i] = Bs[cur][kk][tx * 4 + i];
+          b0[4 + i] = Bs[cur][kk][64 + tx * 4 + i];
+          b1[i] = Bs[cur][kk + 1][tx * 4 + i];
+          b1[4 + i] = Bs[cur][kk + 1][64 + tx * 4 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = tmax3(acc[i][j], a0[i] + b0[j], a1[i] + b1[j]);
+      }
+      __syncthreads();
+    }
+    T *Cb = C + b * p.sCb;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+      if (gm >= p.M) continue;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+        if (gn < p.N) Cb[gm * p.sCm + gn * p.sCn] = acc[i][j];
+      }
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+cudaError_t launch_mpgemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
+                          const Batch &bt, cudaStream_t st) {
+  const int64_t tiles = p.batch * ((p.M + GBM - 1) / GBM) * ((p.N + GBN - 1) / GBN);
+  if (tiles == 0) return cudaSuccess;
+  const int64_t cap = std::max<int64_t>(1, 152 * 2 * 4 / bt.B);
+  dim3 blocks((unsigned)(tiles < cap ? tiles : cap), bt.B);
+  if (dt == DT_F32)
+    k_mpgemm<float><<<blocks, 256, 0, st>>>(p, (const float *)A, (const float *)B, (float *)C,
+                                            bt.ib);
+  else
+    k_mpgemm<int32_t><<<blocks, 256, 0, st>>>(p, (const int32_t *)A, (const int32_t *)B,
+                                              (int32_t *)C, bt.ib);
   return cudaGetLastError();
 }
 
@@ -857,16 +1002,6 @@ __device__ __forceinline__ void rc_diag(T (&v)[1 << RB], const ChainGate &g, con
 #undef RC_D
 }
 
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_prev() {
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-}
 
 // Offset of the tensor element of outer index tau (legs other than the
 // register legs); every size and stride is a power of two.

@@ -313,10 +313,8 @@ def main():
     clocks.start()
     ms, _, total = timed(args.steps)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2008_06888_gb300 import shard
+    ms = shard.max_over_ranks(ms, world, dev)
     inst_total = args.batch * args.steps * world
     value = inst_total / (ms / 1e3)
 
@@ -330,10 +328,7 @@ def main():
         E, sigma = B.tn_config_batch(sg.ctx, Jh, hh, sg.n, want_sigma=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = shard.max_over_ranks(e2e_s, world, dev)
     e2e = {"value": inst_total / e2e_s, "unit": "instances/s",
            "h2d_bytes_per_step": args.batch * 4 * (sg.m + sg.n),
            "d2h_bytes_per_step": args.batch * (sg.n + 4)}

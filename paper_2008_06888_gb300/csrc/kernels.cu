@@ -191,8 +191,9 @@ __global__ void __launch_bounds__(256) k_gate(const GateParams p, const T *__res
             for (int i = 0; i < TN_MAX_PRIMES; ++i) {
               if (i < p.P) {
                 uint64_t na = nA[i * p.planeA + oa + p.kA[k]];
-                uint64_t t = p.hasB ? mulmod61(na, nB[i * p.planeB + ob + p.kB[k] + p.nB[n]], ps.c[i])
-                                    : na;
+                uint64_t t = (p.hasB && !p.unitB)
+                                 ? mulmod61(na, nB[i * p.planeB + ob + p.kB[k] + p.nB[n]], ps.c[i])
+                                 : na;
                 cnt[i] = gt ? t : addmod61(cnt[i], t, ps.c[i]);
               }
             }
@@ -807,11 +808,15 @@ static cudaError_t launch_chain_t(const ChainParams &p, const char *arena, const
 
 cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
                           void *Cx, const Batch &bt, cudaStream_t st);
+cudaError_t launch_rchain_count(Dtype dt, const ChainParams &p, const char *arena,
+                                const void *Ax, const uint64_t *An, void *Cx, uint64_t *Cn,
+                                const PrimeSet &ps, const Batch &bt, cudaStream_t st);
 
 cudaError_t launch_chain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
                          const uint64_t *An, void *Cx, uint64_t *Cn, const PrimeSet &ps,
                          const Batch &bt, cudaStream_t st) {
   if (p.outer == 0) return cudaSuccess;
+  if (p.mode == 1 && p.P > 0) return launch_rchain_count(dt, p, arena, Ax, An, Cx, Cn, ps, bt, st);
   if (p.mode == 1) return launch_rchain(dt, p, arena, Ax, Cx, bt, st);
   const bool c = p.P > 0;
   if (dt == DT_F32) {
@@ -1095,6 +1100,162 @@ __global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainPara
     for (int e = 0; e < (1 << RB); ++e) dst[o[e]] = v[e];
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ---- counting register chains (q = 2, P = 4 residue planes): every thread
+// keeps the 2^RB values and their 4 residues in registers.  A tie adds the
+// counts of the tied states; the gate's own counts multiply in unless it is a
+// leaf (all counts 1).
+
+template <int RB, int NP, bool UNIT, typename T>
+__device__ __forceinline__ void rcc_replace(int J, T (&v)[1 << RB], uint64_t (&n)[NP][1 << RB],
+                                            const ChainGate &g, const T *sB, const uint64_t *sBn,
+                                            int64_t base, const PrimeSet &ps) {
+  int wm = 0, wf = 0;
+  if (g.nb > 0) leg_sel(g, 0, base, &wm, &wf);
+  const int wl = g.nb > 0 ? (int)g.sBb[0] : 0;
+#pragma unroll
+  for (int e = 0; e < (1 << RB); ++e) {
+    if (e & (1 << J)) continue;
+    const int e1 = e | (1 << J);
+    const int bo = ((((e & wm) != 0) | wf) ? wl : 0);
+    const int i00 = bo, i01 = bo + (int)g.sBn, i10 = bo + (int)g.sBk, i11 = bo + (int)(g.sBk + g.sBn);
+    const T a = v[e], b = v[e1];
+    const T s00 = a + sB[i00], s10 = b + sB[i10], s01 = a + sB[i01], s11 = b + sB[i11];
+    const T o0 = max(s00, s10), o1 = max(s01, s11);
+    const bool t00 = s00 == o0, t10 = s10 == o0, t01 = s01 == o1, t11 = s11 == o1;
+#pragma unroll
+    for (int pl = 0; pl < NP; ++pl) {
+      const uint64_t c = ps.c[pl];
+      const uint64_t na = n[pl][e], nb = n[pl][e1];
+      if (UNIT) {
+        // leaf operand: counts of the tied states add (at least one is tied)
+        const uint64_t both = addmod61(na, nb, c);
+        n[pl][e] = t00 ? (t10 ? both : na) : nb;
+        n[pl][e1] = t01 ? (t11 ? both : na) : nb;
+      } else {
+        const uint64_t *bn = sBn + pl * kGateBMax;
+        const uint64_t a0 = mulmod61(na, bn[i00], c), b0 = mulmod61(nb, bn[i10], c);
+        const uint64_t a1 = mulmod61(na, bn[i01], c), b1 = mulmod61(nb, bn[i11], c);
+        n[pl][e] = t00 ? (t10 ? addmod61(a0, b0, c) : a0) : b0;
+        n[pl][e1] = t01 ? (t11 ? addmod61(a1, b1, c) : a1) : b1;
+      }
+    }
+    v[e] = o0;
+    v[e1] = o1;
+  }
+}
+
+template <int RB, int NP, typename T>
+__device__ __forceinline__ void rcc_diag(T (&v)[1 << RB], uint64_t (&n)[NP][1 << RB],
+                                         const ChainGate &g, const T *sB, const uint64_t *sBn,
+                                         int64_t base, const PrimeSet &ps) {
+  int m0 = 0, f0 = 0, m1 = 0, f1 = 0;
+  leg_sel(g, 0, base, &m0, &f0);
+  if (g.nb > 1) leg_sel(g, 1, base, &m1, &f1);
+  const int s0 = (int)g.sBb[0], s1 = g.nb > 1 ? (int)g.sBb[1] : 0;
+#pragma unroll
+  for (int e = 0; e < (1 << RB); ++e) {
+    const int x0 = ((e & m0) != 0) | f0, x1 = ((e & m1) != 0) | f1;
+    const int bo = x0 * s0 + x1 * s1;
+    v[e] = v[e] + sB[bo];
+  }
+  if (g.unitB) return;
+#pragma unroll
+  for (int e = 0; e < (1 << RB); ++e) {
+    const int x0 = ((e & m0) != 0) | f0, x1 = ((e & m1) != 0) | f1;
+    const int bo = x0 * s0 + x1 * s1;
+#pragma unroll
+    for (int pl = 0; pl < NP; ++pl)
+      n[pl][e] = mulmod61(n[pl][e], sBn[pl * kGateBMax + bo], ps.c[pl]);
+  }
+}
+
+template <typename T, int RB, int NP>
+__global__ void __launch_bounds__(256, 2) k_rchain_count(const ChainParams p,
+                                                         const T *__restrict__ X,
+                                                         const uint64_t *__restrict__ Xn,
+                                                         const T *__restrict__ A,
+                                                         const uint64_t *__restrict__ An,
+                                                         T *__restrict__ C,
+                                                         uint64_t *__restrict__ Cn,
+                                                         const PrimeSet ps, int64_t ib) {
+  X = inst_ptr(X, ib);
+  Xn = inst_ptr(Xn, ib);
+  A = inst_ptr(A, ib);
+  An = inst_ptr(An, ib);
+  C = inst_ptr(C, ib);
+  Cn = inst_ptr(Cn, ib);
+  __shared__ T sB[TN_CHAIN_MAX_G * kGateBMax];
+  __shared__ uint64_t sBn[TN_CHAIN_MAX_G * NP * kGateBMax];
+  __shared__ int64_t soff[1 << RB];
+  load_gate_operands<T>(p, X, Xn, sB, sBn, kGateBMax);
+  for (int e = threadIdx.x; e < (1 << RB); e += blockDim.x) soff[e] = p.hi_off[e];
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t tau = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tau < p.outer; tau += stride) {
+    int64_t r = tau, base = 0;
+    for (int sg = p.nseg - 1; sg >= 0; --sg) {
+      base += (r & (p.seg_size[sg] - 1)) * p.seg_s[sg];
+      r >>= p.seg_sh[sg];
+    }
+    T v[1 << RB];
+    uint64_t n[NP][1 << RB];
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+      const int64_t off = base + soff[e];
+      v[e] = A[off];
+#pragma unroll
+      for (int pl = 0; pl < NP; ++pl) n[pl][e] = An[pl * p.planeA + off];
+    }
+    for (int gi = 0; gi < p.ngates; ++gi) {
+      const ChainGate &g = p.g[gi];
+      const T *gB = sB + gi * kGateBMax;
+      const uint64_t *gBn = sBn + (int64_t)gi * NP * kGateBMax;
+      if (g.kind != 0) {
+        rcc_diag<RB, NP>(v, n, g, gB, gBn, base, ps);
+        continue;
+      }
+      if (g.unitB) {
+        switch (g.ls) {
+          case 0: rcc_replace<RB, NP, true>(0, v, n, g, gB, gBn, base, ps); break;
+          case 1: rcc_replace<RB, NP, true>(1, v, n, g, gB, gBn, base, ps); break;
+          default: rcc_replace<RB, NP, true>(2, v, n, g, gB, gBn, base, ps); break;
+        }
+      } else {
+        switch (g.ls) {
+          case 0: rcc_replace<RB, NP, false>(0, v, n, g, gB, gBn, base, ps); break;
+          case 1: rcc_replace<RB, NP, false>(1, v, n, g, gB, gBn, base, ps); break;
+          default: rcc_replace<RB, NP, false>(2, v, n, g, gB, gBn, base, ps); break;
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+      const int64_t off = base + soff[e];
+      C[off] = v[e];
+#pragma unroll
+      for (int pl = 0; pl < NP; ++pl) Cn[pl * p.planeC + off] = n[pl][e];
+    }
+  }
+}
+
+cudaError_t launch_rchain_count(Dtype dt, const ChainParams &p, const char *arena,
+                                const void *Ax, const uint64_t *An, void *Cx, uint64_t *Cn,
+                                const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
+  if (p.t != 3 || p.P != 4) return cudaErrorInvalidValue;
+  int64_t blocks = (p.outer + 255) / 256;
+  const int64_t cap = std::max<int64_t>(1, 152 * 2 * 4 / bt.B);
+  if (blocks > cap) blocks = cap;
+  if (dt == DT_F32)
+    k_rchain_count<float, 3, 4><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(
+        p, reinterpret_cast<const float *>(arena), reinterpret_cast<const uint64_t *>(arena),
+        static_cast<const float *>(Ax), An, static_cast<float *>(Cx), Cn, ps, bt.ib);
+  else
+    k_rchain_count<int32_t, 3, 4><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(
+        p, reinterpret_cast<const int32_t *>(arena), reinterpret_cast<const uint64_t *>(arena),
+        static_cast<const int32_t *>(Ax), An, static_cast<int32_t *>(Cx), Cn, ps, bt.ib);
+  return cudaGetLastError();
 }
 
 // Traceback of a register chain by one warp: lane e holds element e of the

@@ -44,8 +44,17 @@ struct Builder {
   std::vector<Loc> loc;
   std::string err;
 
+  // unit[t]: every count of tensor t is 1 (leaves, and steps that contract
+  // nothing from unit inputs: outer products and Hadamard-type steps)
+  std::vector<char> unit;
+
   Builder(const Net &n, const Plan &p, Program &r)
-      : net(n), plan(p), pr(r), q(r.q), P(r.P), order(p.legset.size()), loc(p.legset.size()) {}
+      : net(n), plan(p), pr(r), q(r.q), P(r.P), order(p.legset.size()), loc(p.legset.size()),
+        unit(p.legset.size(), 0) {
+    for (int i = 0; i < p.n_leaves; ++i) unit[i] = 1;
+    for (const PStep &st : p.steps)
+      unit[st.c] = unit[st.a] && (st.b < 0 || unit[st.b]) && st.K.empty();
+  }
 
   int64_t stride(const std::vector<int> &ord, int leg) const {
     int p = pos_of(ord, leg);
@@ -215,8 +224,9 @@ struct Builder {
     return true;
   }
 
-  void push_gate(const GateParams &g, const Loc &A, const Loc *B, const Loc &C) {
+  void push_gate(const GateParams &g, const Loc &A, const Loc *B, const Loc &C, bool unitB) {
     GateParams p = g;
+    p.unitB = unitB ? 1 : 0;
     p.planeA = A.plane;
     p.planeB = B ? B->plane : 0;
     p.planeC = C.plane;
@@ -259,7 +269,7 @@ struct Builder {
         return false;
       }
       Loc out = new_tensor(ipow(q, (int)ordC.size()));
-      push_gate(g, cur, nullptr, out);
+      push_gate(g, cur, nullptr, out, true);
       cur = out;
       cur_ord = ordC;
     } while (!Krem.empty());
@@ -355,7 +365,7 @@ struct Builder {
       std::vector<int> ordC;
       if (make_gate(order[o.A], &order[o.B], K, Nn, &g, &ordC)) {
         Loc out = new_tensor(ipow(q, (int)ordC.size()));
-        push_gate(g, loc[o.A], &loc[o.B], out);
+        push_gate(g, loc[o.A], &loc[o.B], out, unit[o.B]);
         order[st.c] = ordC;
         loc[st.c] = out;
         return;
@@ -540,7 +550,7 @@ struct Builder {
     std::vector<int> S = reg_legs(m);
     cp.mode = 1;
     cp.q = 2;
-    cp.t = kRB;
+    cp.t = kRB;          // 5 (values) or 3 (values + residue planes)
     cp.tile = 1 << kRB;
     for (int e = 0; e < cp.tile; ++e) {
       int64_t off = 0;
@@ -589,9 +599,10 @@ struct Builder {
       c.sBk = g.sBk;
       c.sBn = g.sBn;
       c.nBel = (int)tsize(g.btensor);
+      c.unitB = unit[g.btensor] ? 1 : 0;
       blocs->push_back(loc[g.btensor]);
     }
-    cp.P = 0;
+    cp.P = P;
     return cp;
   }
 
@@ -844,8 +855,10 @@ struct Builder {
 
   bool build(ProgMode mode, int64_t seg_bytes) {
     fuse = std::getenv("TN_NO_FUSION") == nullptr;
-    regmode = q == 2 && P == 0 && std::getenv("TN_TILE_CHAINS") == nullptr;
+    // register chains: q = 2 values, or q = 2 counts with 3 primes + witness
+    regmode = q == 2 && (P == 0 || P == 4) && std::getenv("TN_TILE_CHAINS") == nullptr;
     if (const char *rb = std::getenv("TN_REG_BITS")) kRB = std::atoi(rb) == 4 ? 4 : 5;
+    if (P > 0) kRB = 3;
     if (q == 3) { tmax = 7; wlow = 4; }
     emit_leaves();
     if (!forward()) return false;

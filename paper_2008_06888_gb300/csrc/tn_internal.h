@@ -26,6 +26,7 @@ struct GateParams {
   int32_t seg_sh[TN_MAX_SEG];    // log2(seg_size) when every size is a power of two, else -1
   int Ks, Ns;
   int hasB;                      // 0: unary reduction, B == tropical one (0)
+  int unitB;                     // every count of B is 1: ties only add counts
   int64_t kA[TN_GATE_MAX_K];
   int64_t kB[TN_GATE_MAX_K];
   int64_t nB[TN_GATE_MAX_N];
@@ -105,6 +106,7 @@ struct ChainGate {
   int32_t lsh;       // log2(ls) when q == 2
   int32_t lsbh[2];   // log2(lsb) when q == 2
   int32_t nBel;      // elements of B
+  int32_t unitB;     // 1: every count of B is 1 (a leaf), ties only add counts
   int64_t offB;      // element offset of B's values in the arena
   int64_t offBn;     // u64 offset of B's residue plane 0 in the arena (counting)
   int64_t planeB;    // elements between B's residue planes

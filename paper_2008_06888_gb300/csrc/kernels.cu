@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <stdint.h>
 
 #include "kernels.h"
@@ -211,6 +212,83 @@ __global__ void __launch_bounds__(256) k_gate(const GateParams p, const T *__res
   }
 }
 
+// Values-only gate contraction with the numbers of contracted and new states
+// known at compile time (the common 1 / 2 cases): offsets held in registers,
+// two outer indices per thread for independent loads.
+template <typename T, int KS, int NS>
+__global__ void __launch_bounds__(256) k_gate_t(const GateParams p, const T *__restrict__ A,
+                                                const T *__restrict__ B, T *__restrict__ C,
+                                                int64_t ib) {
+  A = inst_ptr(A, ib);
+  C = inst_ptr(C, ib);
+  if (p.hasB) B = inst_ptr(B, ib);
+  int64_t kA[KS], kB[KS], nB[NS], nC[NS];
+#pragma unroll
+  for (int k = 0; k < KS; ++k) { kA[k] = p.kA[k]; kB[k] = p.kB[k]; }
+#pragma unroll
+  for (int n = 0; n < NS; ++n) { nB[n] = p.nB[n]; nC[n] = p.nC[n]; }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t o0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o0 < p.outer; o0 += 2 * stride) {
+    int64_t oa[2], ob[2], oc[2];
+    bool live[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t o = o0 + u * stride;
+      live[u] = o < p.outer;
+      int64_t r = live[u] ? o : 0;
+      oa[u] = ob[u] = oc[u] = 0;
+      for (int s = p.nseg - 1; s >= 0; --s) {
+        int64_t i;
+        if (p.seg_sh[s] >= 0) {
+          i = r & (p.seg_size[s] - 1);
+          r >>= p.seg_sh[s];
+        } else {
+          i = r % p.seg_size[s];
+          r /= p.seg_size[s];
+        }
+        oa[u] += i * p.seg_sA[s];
+        ob[u] += i * p.seg_sB[s];
+        oc[u] += i * p.seg_sC[s];
+      }
+    }
+    T a[2][KS];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int k = 0; k < KS; ++k) a[u][k] = live[u] ? A[oa[u] + kA[k]] : T(0);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!live[u]) continue;
+#pragma unroll
+      for (int n = 0; n < NS; ++n) {
+        T best = a[u][0] + (p.hasB ? B[ob[u] + kB[0] + nB[n]] : T(0));
+#pragma unroll
+        for (int k = 1; k < KS; ++k)
+          best = max(best, a[u][k] + (p.hasB ? B[ob[u] + kB[k] + nB[n]] : T(0)));
+        C[oc[u] + nC[n]] = best;
+      }
+    }
+  }
+}
+
+template <typename T>
+static bool launch_gate_t(const GateParams &p, const T *A, const T *B, T *C, dim3 blocks,
+                          int threads, int64_t ib, cudaStream_t st) {
+#define TN_GATE_CASE(KS_, NS_)                                                                 \
+  if (p.Ks == KS_ && p.Ns == NS_) {                                                            \
+    k_gate_t<T, KS_, NS_><<<blocks, threads, 0, st>>>(p, A, B, C, ib);                         \
+    return true;                                                                               \
+  }
+  TN_GATE_CASE(1, 1)
+  TN_GATE_CASE(1, 2)
+  TN_GATE_CASE(2, 1)
+  TN_GATE_CASE(2, 2)
+  TN_GATE_CASE(4, 1)
+  TN_GATE_CASE(1, 4)
+#undef TN_GATE_CASE
+  return false;
+}
+
 cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const void *xB, void *xC,
                         const uint64_t *nA, const uint64_t *nB, uint64_t *nC, const PrimeSet &ps,
                         const Batch &bt, cudaStream_t st) {
@@ -218,6 +296,15 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
   int threads = 256;
   dim3 blocks(grid_for(p.outer, threads), bt.B);
   bool cnt = p.P > 0;
+  if (!cnt) {
+    dim3 b2(grid_for((p.outer + 1) / 2, threads), bt.B);
+    const bool done = dt == DT_F32
+                          ? launch_gate_t<float>(p, (const float *)xA, (const float *)xB,
+                                                 (float *)xC, b2, threads, bt.ib, st)
+                          : launch_gate_t<int32_t>(p, (const int32_t *)xA, (const int32_t *)xB,
+                                                   (int32_t *)xC, b2, threads, bt.ib, st);
+    if (done) return cudaGetLastError();
+  }
   if (dt == DT_F32) {
     if (cnt)
       k_gate<float, true><<<blocks, threads, 0, st>>>(p, (const float *)xA, (const float *)xB,
@@ -1028,8 +1115,8 @@ __device__ __forceinline__ I rc_base(const ChainParams &p, int64_t tau) {
 // registers and stored.  Element offsets of the register legs are built
 // incrementally from the RB leg strides; I is the index type (32-bit when
 // the tensor has fewer than 2^31 elements).
-template <typename T, int RB, typename I>
-__global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainParams p,
+template <typename T, int RB, typename I, int STAGES, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_rchain(const ChainParams p,
                                                                   const T *__restrict__ X,
                                                                   const T *__restrict__ A,
                                                                   T *__restrict__ C, int64_t ib) {
@@ -1045,7 +1132,6 @@ __global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainPara
 #pragma unroll
   for (int j = 0; j < RB; ++j) sS[j] = (I)p.hi_off[1 << j];
   const int nt = blockDim.x, tid = threadIdx.x;
-  T *buf[2] = {stage, stage + (1 << RB) * nt};
   const int64_t step = (int64_t)gridDim.x * nt;
   int64_t tau = blockIdx.x * (int64_t)nt + tid;
   auto issue = [&](int64_t t, T *dst) {
@@ -1063,11 +1149,17 @@ __global__ void __launch_bounds__(256, RB >= 5 ? 2 : 4) k_rchain(const ChainPara
     }
     cp_async_commit();
   };
-  issue(tau, buf[0]);
+  auto slot = [&](int it) { return stage + (it % STAGES) * (1 << RB) * nt; };
+#pragma unroll
+  for (int s = 0; s < STAGES - 1; ++s) issue(tau + s * step, slot(s));
   for (int it = 0; tau < p.outer; tau += step, ++it) {
-    T *cur = buf[it & 1];
-    issue(tau + step, buf[(it + 1) & 1]);
-    cp_async_wait_prev();
+    T *cur = slot(it);
+    issue(tau + (STAGES - 1) * step, slot(it + STAGES - 1));
+    // all but the STAGES - 1 most recent groups are complete: the current slot is ready
+    if (STAGES == 3)
+      asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+    else
+      cp_async_wait_prev();
     const I bi = rc_base<I>(p, tau);
     const int64_t base = bi;
     T v[1 << RB];
@@ -1337,21 +1429,32 @@ __device__ void trace_rchain(const ChainTrace &ct, const T *X, int8_t *state, in
   (void)sbase;
 }
 
-template <typename T, int RB, typename I>
-static cudaError_t launch_rchain_i(const ChainParams &p, const char *arena, const void *Ax,
-                                   void *Cx, int blocks, size_t smem, const Batch &bt,
-                                   cudaStream_t st) {
+template <typename T, int RB, typename I, int STAGES, int MINB>
+static cudaError_t launch_rchain_s(const ChainParams &p, const char *arena, const void *Ax,
+                                   void *Cx, int blocks, const Batch &bt, cudaStream_t st) {
+  const size_t smem = (size_t)STAGES * (1 << RB) * 256 * sizeof(T);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_rchain<T, RB, I>,
+    cudaError_t e = cudaFuncSetAttribute(k_rchain<T, RB, I, STAGES, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_rchain<T, RB, I><<<dim3(blocks, bt.B), 256, smem, st>>>(
+  k_rchain<T, RB, I, STAGES, MINB><<<dim3(blocks, bt.B), 256, smem, st>>>(
       p, reinterpret_cast<const T *>(arena), static_cast<const T *>(Ax), static_cast<T *>(Cx),
       bt.ib);
   return cudaGetLastError();
+}
+
+template <typename T, int RB, typename I>
+static cudaError_t launch_rchain_i(const ChainParams &p, const char *arena, const void *Ax,
+                                   void *Cx, int blocks, size_t smem, const Batch &bt,
+                                   cudaStream_t st) {
+  (void)smem;
+  static const int minb = std::getenv("TN_RCHAIN_MINB") ? std::atoi(std::getenv("TN_RCHAIN_MINB"))
+                                                        : 2;
+  if (RB >= 5 && minb == 3) return launch_rchain_s<T, RB, I, 2, 3>(p, arena, Ax, Cx, blocks, bt, st);
+  return launch_rchain_s<T, RB, I, 2, RB >= 5 ? 2 : 4>(p, arena, Ax, Cx, blocks, bt, st);
 }
 
 template <typename T, int RB>
@@ -1369,7 +1472,9 @@ cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, con
   if (p.outer == 0) return cudaSuccess;
   if (p.t != 4 && p.t != 5) return cudaErrorInvalidValue;
   // resident blocks only (2 or 4 per SM); each thread then pipelines several indices
-  const int per_sm = p.t == 5 ? 2 : 4;
+  static const int minb = std::getenv("TN_RCHAIN_MINB") ? std::atoi(std::getenv("TN_RCHAIN_MINB"))
+                                                        : 2;
+  const int per_sm = p.t == 5 ? (minb == 3 ? 3 : 2) : 4;
   int64_t blocks = (p.outer + 255) / 256;
   const int64_t cap = std::max<int64_t>(1, 152 * per_sm / bt.B);
   if (blocks > cap) blocks = cap;

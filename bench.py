@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--mode", default="config", choices=["config", "energy"],
                     help="config: E_min + sigma* (the workload); energy: E_min only (profiling)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--restarts", type=int, default=ORDER_RESTARTS,
+                    help="greedy restarts of the (untimed) order search")
     ap.add_argument("--quiet", action="store_true", help="print only value and kernel shares")
     ap.add_argument("--workload", default="square24", choices=["square24", "mixed"],
                     help="mixed: batch of +-J lattices with L uniform in 8..20, E_min + count")
@@ -314,7 +316,7 @@ def main():
     from paper_2008_06888_gb300 import binding as B
 
     insts = make_instances(rank, args.batch, args.L)
-    sg = P.SpinGlass(insts[0], order="greedy", seed=ORDER_SEED, restarts=ORDER_RESTARTS)
+    sg = P.SpinGlass(insts[0], order="greedy", seed=ORDER_SEED, restarts=args.restarts)
     stream = torch.cuda.current_stream(dev)
     sg.set_stream(stream.cuda_stream)
     # couplings of the whole batch, resident in HBM: (B, n_edges) and (B, n_spins)

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -628,7 +629,23 @@ tn_status tn_order(tn_ctx *ctx, int32_t method, const int32_t *seq, int32_t seq_
     ok = tree_from_sweep(ctx->net, s, &t, &err);
   } else if (method == TN_ORDER_GREEDY) {
     CostModel cm;
-    ok = tree_greedy(ctx->net, seed, restarts, cm, &t, &err);
+    // rank candidates by their lowered (fused) energy program on GB300 rates
+    Dtype dt = ctx->dt;
+    auto score = [&](const Plan &pl) -> double {
+      Program pg;
+      std::string e2;
+      if (!build_program(ctx->net, pl, PM_ENERGY, dt, 0, 0, &pg, &e2)) return INFINITY;
+      double tsec = 0;
+      for (const Op &op : pg.ops) {
+        tsec += 2.0e-6;  // launch / latency floor per kernel in a graph
+        if (op.kind == OP_CHAIN) tsec += op.bytes / 3.4e12;
+        else if (op.kind == OP_GEMM) tsec += std::max(op.macs / 1.2e13, op.bytes / 3.0e12);
+        else tsec += op.bytes / 2.5e12;
+      }
+      return tsec;
+    };
+    ok = tree_greedy(ctx->net, seed, restarts, cm, &t, &err,
+                     std::getenv("TN_GREEDY_STEP_COST") ? nullptr : std::function<double(const Plan &)>(score));
   } else if (method == TN_ORDER_TREE) {
     if (seq_len % 2 || (seq_len > 0 && !seq)) return fail(ctx, TN_EINVAL, "tree: odd length");
     for (int i = 0; i < seq_len; i += 2) t.steps.push_back({seq[i], seq[i + 1]});

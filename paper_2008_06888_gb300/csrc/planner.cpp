@@ -213,7 +213,7 @@ double plan_cost(const Plan &p, int q, const CostModel &cm) {
 }
 
 bool tree_greedy(const Net &net, uint64_t seed, int restarts, const CostModel &cm, Tree *t,
-                 std::string *err) {
+                 std::string *err, const std::function<double(const Plan &)> &score) {
   std::mt19937_64 rng(seed);
   std::uniform_real_distribution<double> U(0.0, 1.0);
   double best = INFINITY;
@@ -230,7 +230,7 @@ bool tree_greedy(const Net &net, uint64_t seed, int restarts, const CostModel &c
     std::string e2;
     if (!classify(net, cand, &p, &e2)) { *err = e2; return false; }
     if (p.log2_peak > 34.0) continue;
-    double c = plan_cost(p, net.q, cm);
+    double c = score ? score(p) : plan_cost(p, net.q, cm);
     if (c < best) { best = c; *t = cand; }
   }
   if (!std::isfinite(best)) { *err = "greedy: every tree exceeds 2^34 elements"; return false; }

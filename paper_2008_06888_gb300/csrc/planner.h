@@ -2,6 +2,7 @@
 // classification (the pairwise contraction tree of Sec. III).
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -57,8 +58,10 @@ struct CostModel {
 // smallest first, which contracts the spin).
 bool tree_from_sweep(const Net &net, const std::vector<int> &seq, Tree *t, std::string *err);
 // Randomized greedy (log-size score with Gumbel noise), best of `restarts`.
+// `score` (optional) ranks a classified candidate (lower is better); without it
+// the per-step cost model is used.
 bool tree_greedy(const Net &net, uint64_t seed, int restarts, const CostModel &cm, Tree *t,
-                 std::string *err);
+                 std::string *err, const std::function<double(const Plan &)> &score = nullptr);
 // Validate a user tree and classify every step (inserts unary reductions).
 bool classify(const Net &net, const Tree &t, Plan *plan, std::string *err);
 double plan_cost(const Plan &p, int q, const CostModel &cm);

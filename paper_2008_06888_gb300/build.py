@@ -16,6 +16,7 @@ LIB = os.path.join(HERE, "libtn.so")
 SOURCES = ["kernels.cu", "noalloc.cu", "planner.cpp", "program.cpp", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+          "-Xcompiler", "-pthread",
           "-I" + os.path.join(os.path.dirname(HERE), "include")]
 
 
@@ -62,7 +63,7 @@ def build(force=False, verbose_ptxas=False):
             if log.strip():
                 print(log, file=sys.stderr)
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
+    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart", "-Xcompiler", "-pthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -11,11 +11,13 @@
 #include "planner.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <queue>
 #include <random>
 #include <set>
+#include <thread>
 
 namespace tn {
 
@@ -214,26 +216,50 @@ double plan_cost(const Plan &p, int q, const CostModel &cm) {
 
 bool tree_greedy(const Net &net, uint64_t seed, int restarts, const CostModel &cm, Tree *t,
                  std::string *err, const std::function<double(const Plan &)> &score) {
-  std::mt19937_64 rng(seed);
-  std::uniform_real_distribution<double> U(0.0, 1.0);
-  double best = INFINITY;
-  Tree cand;
   if (restarts < 1) restarts = 1;
-  for (int r = 0; r < restarts; ++r) {
-    double temp = 0, alpha = 1;
-    if (r > 0) {
-      temp = std::exp(std::log(1e-3) + U(rng) * (std::log(1.0) - std::log(1e-3)));
-      alpha = std::exp(std::log(0.1) + U(rng) * (std::log(4.0) - std::log(0.1)));
+  // restart r draws (temperature, cost weight) and its own generator from the
+  // seed alone, so the result does not depend on how restarts are spread over
+  // host threads
+  std::vector<double> temp(restarts, 0.0), alpha(restarts, 1.0);
+  {
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    for (int r = 1; r < restarts; ++r) {
+      temp[r] = std::exp(std::log(1e-3) + U(rng) * (std::log(1.0) - std::log(1e-3)));
+      alpha[r] = std::exp(std::log(0.1) + U(rng) * (std::log(4.0) - std::log(0.1)));
     }
-    greedy_once(net, rng, temp, alpha, &cand);
-    Plan p;
-    std::string e2;
-    if (!classify(net, cand, &p, &e2)) { *err = e2; return false; }
-    if (p.log2_peak > 34.0) continue;
-    double c = score ? score(p) : plan_cost(p, net.q, cm);
-    if (c < best) { best = c; *t = cand; }
   }
-  if (!std::isfinite(best)) { *err = "greedy: every tree exceeds 2^34 elements"; return false; }
+  std::vector<double> cost(restarts, INFINITY);
+  std::vector<Tree> trees(restarts);
+  std::vector<std::string> errs(restarts);
+  std::atomic<int> next(0);
+  auto worker = [&]() {
+    for (;;) {
+      const int r = next.fetch_add(1);
+      if (r >= restarts) return;
+      std::mt19937_64 rng(seed * 0x9E3779B97F4A7C15ull + (uint64_t)r * 0xBF58476D1CE4E5B9ull + 1);
+      greedy_once(net, rng, temp[r], alpha[r], &trees[r]);
+      Plan p;
+      if (!classify(net, trees[r], &p, &errs[r])) continue;
+      if (p.log2_peak > 34.0) continue;
+      cost[r] = score ? score(p) : plan_cost(p, net.q, cm);
+    }
+  };
+  unsigned nth = std::thread::hardware_concurrency();
+  if (nth == 0) nth = 1;
+  nth = std::min<unsigned>(nth, 32);
+  nth = std::min<unsigned>(nth, (unsigned)restarts);
+  std::vector<std::thread> pool;
+  for (unsigned i = 1; i < nth; ++i) pool.emplace_back(worker);
+  worker();
+  for (auto &th : pool) th.join();
+  int best = -1;
+  for (int r = 0; r < restarts; ++r) {
+    if (!errs[r].empty()) { *err = errs[r]; return false; }
+    if (std::isfinite(cost[r]) && (best < 0 || cost[r] < cost[best])) best = r;
+  }
+  if (best < 0) { *err = "greedy: every tree exceeds 2^34 elements"; return false; }
+  *t = trees[best];
   return true;
 }
 

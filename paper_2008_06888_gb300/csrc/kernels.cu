@@ -522,12 +522,132 @@ __global__ void __launch_bounds__(256, 2) k_mpgemm(const GemmParams p, const T *
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// Fast path for A = [batch][M][K] and B = [batch][K][N] (both row-major, K and N
+// multiples of 4, whole 128 x 128 x 16 tiles): each k slab moves as 16-byte
+// cp.async chunks, A staged k-contiguous (As[m][k]) and read as 4-k vectors.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 t; };
+template <> struct Vec2<int32_t> { typedef int2 t; };
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 t; };
+template <> struct Vec4<int32_t> { typedef int4 t; };
+
+constexpr int GAK = GBK + 4;   // padded row of As[m][k]
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_mpgemm16(const GemmParams p, const T *__restrict__ A,
+                                                     const T *__restrict__ B, T *__restrict__ C,
+                                                     int64_t ib) {
+  A = inst_ptr(A, ib);
+  B = inst_ptr(B, ib);
+  C = inst_ptr(C, ib);
+  __shared__ __align__(16) T As[2][GBM][GAK];
+  __shared__ __align__(16) T Bs[2][GBK][GBN + GPAD];
+  const int64_t mt = p.M / GBM, nt = p.N / GBN;
+  const int64_t tiles = p.batch * mt * nt;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int64_t ksteps = p.K / GBK;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t b = t / (mt * nt);
+    const int64_t rem = t % (mt * nt);
+    const int64_t m0 = (rem / nt) * GBM, n0 = (rem % nt) * GBN;
+    const T *Ab = A + b * p.sAb + m0 * p.sAm;
+    const T *Bb = B + b * p.sBb + n0;
+    auto load = [&](int64_t ks, int buf) {
+      // A: 128 rows x 16 k = 512 chunks of 4; B: 16 rows x 128 n = 512 chunks of 4
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int c = tid + r * 256;
+        const int am = c / 4, ak = (c % 4) * 4;
+        cp_async16(&As[buf][am][ak], Ab + am * p.sAm + ks * GBK + ak);
+        const int bk = c / 32, bn = (c % 32) * 4;
+        cp_async16(&Bs[buf][bk][bn], Bb + (ks * GBK + bk) * p.sBk + bn);
+      }
+      cp_async_commit();
+    };
+    T acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = Lim<T>::neg();
+    __syncthreads();
+    load(0, 0);
+    for (int64_t ks = 0; ks < ksteps; ++ks) {
+      const int cur = ks & 1;
+      if (ks + 1 < ksteps) load(ks + 1, cur ^ 1);
+      else cp_async_commit();
+      cp_async_wait_prev();
+      __syncthreads();
+#pragma unroll
+      for (int kq = 0; kq < GBK; kq += 2) {
+        // rows ty*4+i and 64+ty*4+i at k = kq, kq+1 (one 8-byte load per row)
+        T a0[8], a1[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int m = i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+          const typename Vec2<T>::t v = *reinterpret_cast<const typename Vec2<T>::t *>(&As[cur][m][kq]);
+          a0[i] = v.x;
+          a1[i] = v.y;
+        }
+        T b0[8], b1[8];
+        {
+          typedef typename Vec4<T>::t V4;
+          const V4 u0 = *reinterpret_cast<const V4 *>(&Bs[cur][kq][tx * 4]);
+          const V4 u1 = *reinterpret_cast<const V4 *>(&Bs[cur][kq][64 + tx * 4]);
+          const V4 w0 = *reinterpret_cast<const V4 *>(&Bs[cur][kq + 1][tx * 4]);
+          const V4 w1 = *reinterpret_cast<const V4 *>(&Bs[cur][kq + 1][64 + tx * 4]);
+          b0[0] = u0.x; b0[1] = u0.y; b0[2] = u0.z; b0[3] = u0.w;
+          b0[4] = u1.x; b0[5] = u1.y; b0[6] = u1.z; b0[7] = u1.w;
+          b1[0] = w0.x; b1[1] = w0.y; b1[2] = w0.z; b1[3] = w0.w;
+          b1[4] = w1.x; b1[5] = w1.y; b1[6] = w1.z; b1[7] = w1.w;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = tmax3(acc[i][j], a0[i] + b0[j], a1[i] + b1[j]);
+      }
+      __syncthreads();
+    }
+    T *Cb = C + b * p.sCb;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+        Cb[gm * p.sCm + gn * p.sCn] = acc[i][j];
+      }
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+static bool mpgemm16_ok(const GemmParams &p, const void *A, const void *B) {
+  return p.sAk == 1 && p.sBn == 1 && p.M % GBM == 0 && p.N % GBN == 0 && p.K % GBK == 0 &&
+         p.sAm % 4 == 0 && p.sBk % 4 == 0 && p.sAb % 4 == 0 && p.sBb % 4 == 0 &&
+         (reinterpret_cast<uintptr_t>(A) % 16) == 0 && (reinterpret_cast<uintptr_t>(B) % 16) == 0;
+}
+
 cudaError_t launch_mpgemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
                           const Batch &bt, cudaStream_t st) {
   const int64_t tiles = p.batch * ((p.M + GBM - 1) / GBM) * ((p.N + GBN - 1) / GBN);
   if (tiles == 0) return cudaSuccess;
   const int64_t cap = std::max<int64_t>(1, 152 * 2 * 4 / bt.B);
   dim3 blocks((unsigned)(tiles < cap ? tiles : cap), bt.B);
+  if (mpgemm16_ok(p, A, B) && bt.ib % 16 == 0 && std::getenv("TN_GEMM_SCALAR") == nullptr) {
+    if (dt == DT_F32)
+      k_mpgemm16<float><<<blocks, 256, 0, st>>>(p, (const float *)A, (const float *)B, (float *)C,
+                                                bt.ib);
+    else
+      k_mpgemm16<int32_t><<<blocks, 256, 0, st>>>(p, (const int32_t *)A, (const int32_t *)B,
+                                                  (int32_t *)C, bt.ib);
+    return cudaGetLastError();
+  }
   if (dt == DT_F32)
     k_mpgemm<float><<<blocks, 256, 0, st>>>(p, (const float *)A, (const float *)B, (float *)C,
                                             bt.ib);
@@ -643,9 +763,6 @@ __device__ __forceinline__ int gate_boff(const ChainGate &g, int x) {
   return o;
 }
 
-template <typename T> struct Vec2;
-template <> struct Vec2<float> { typedef float2 t; };
-template <> struct Vec2<int32_t> { typedef int2 t; };
 
 // q = 2 replace gate whose B is a plain 2x2 matrix (no tile legs): the
 // matrix sits in registers and pairs are moved as 2-vectors.
@@ -1194,6 +1311,189 @@ __global__ void __launch_bounds__(256, MINB) k_rchain(const ChainParams p,
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// ---- folded register chains (q = 2, values): table gates.
+//
+// Tables are built once per block: value i of table gate t is the sum of its
+// components, component c reading original gate cg[c]'s operand at the offset
+// given by the index bits of its legs.  Components are summed in order, so
+// the traceback rebuilds bit-identical tables.
+
+template <typename T>
+__device__ __forceinline__ void build_tables(const ChainParams &p, const T *X, T *sT) {
+  for (int k = 0; k < p.ntg; ++k) {
+    const TGate &t = p.tg[k];
+    const int sz = 8 << t.nf;
+    for (int i = threadIdx.x; i < sz; i += blockDim.x) {
+      T acc = T(0);
+      for (int c = 0; c < t.ncomp; ++c) {
+        const ChainGate &g = p.g[t.cg[c]];
+        const int64_t st[4] = {g.sBk, g.sBn, g.sBb[0], g.sBb[1]};
+        int64_t o = 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+          if (t.cbit[c][l] >= 0) o += (int64_t)((i >> t.cbit[c][l]) & 1) * st[l];
+        acc = c == 0 ? X[g.offB + o] : acc + X[g.offB + o];
+      }
+      sT[t.toff + i] = acc;
+    }
+  }
+}
+
+// replace on register bit J with an optional extra register leg K: the
+// table slice for the thread's fixed digits is lo (K digit 0) / hi (1), each
+// (x=0,x'=0), (1,0), (0,1), (1,1).
+template <int RB, int J, int K, typename T, typename V>
+__device__ __forceinline__ void tc_rep(T (&v)[1 << RB], const V &lo, const V &hi) {
+  if constexpr (J < RB && K < RB) {
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+      if (e & (1 << J)) continue;
+      const int e1 = e | (1 << J);
+      const bool k = K >= 0 ? ((e >> (K < 0 ? 0 : K)) & 1) != 0 : false;
+      const T t0 = k ? hi.x : lo.x, t1 = k ? hi.y : lo.y, t2 = k ? hi.z : lo.z,
+              t3 = k ? hi.w : lo.w;
+      const T a = v[e], b = v[e1];
+      v[e] = max(a + t0, b + t1);
+      v[e1] = max(a + t2, b + t3);
+    }
+  }
+}
+
+// diagonal table gate on register legs J (index bit 0) and K (bit 1)
+template <int RB, int J, int K, typename T, typename V>
+__device__ __forceinline__ void tc_diag(T (&v)[1 << RB], const V &lo) {
+  if constexpr (J < RB && K < RB) {
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+      const int x0 = J >= 0 ? (e >> (J < 0 ? 0 : J)) & 1 : 0;
+      const int x1 = K >= 0 ? (e >> (K < 0 ? 0 : K)) & 1 : 0;
+      v[e] = v[e] + (x1 ? (x0 ? lo.w : lo.z) : (x0 ? lo.y : lo.x));
+    }
+  }
+}
+
+template <int RB, typename T, typename V>
+__device__ __forceinline__ void tc_apply(int code, T (&v)[1 << RB], const V &lo, const V &hi) {
+#define TC_R(J, K) case (J) * 6 + (K) + 1: tc_rep<RB, J, K>(v, lo, hi); break;
+#define TC_RJ(J) TC_R(J, -1) TC_R(J, 0) TC_R(J, 1) TC_R(J, 2) TC_R(J, 3) TC_R(J, 4)
+#define TC_D(J, K) case 30 + ((J) + 1) * 6 + (K) + 1: tc_diag<RB, J, K>(v, lo); break;
+  switch (code) {
+    TC_RJ(0) TC_RJ(1) TC_RJ(2) TC_RJ(3) TC_RJ(4)
+    TC_D(-1, -1)
+    TC_D(0, -1) TC_D(1, -1) TC_D(2, -1) TC_D(3, -1) TC_D(4, -1)
+    TC_D(0, 1) TC_D(0, 2) TC_D(0, 3) TC_D(0, 4)
+    TC_D(1, 2) TC_D(1, 3) TC_D(1, 4)
+    TC_D(2, 3) TC_D(2, 4)
+    TC_D(3, 4)
+    default: break;
+  }
+#undef TC_R
+#undef TC_RJ
+#undef TC_D
+}
+
+// digits of the fixed legs -> table slice offset (8 values per slice)
+template <typename I>
+__device__ __forceinline__ int tc_slice(const int4 &d, I base) {
+  const int s0 = d.z & 0xff, s1 = (d.z >> 8) & 0xff, s2 = (d.z >> 16) & 0xff;
+  const int f = (int)((base >> s0) & 1) | ((int)((base >> s1) & 1) << 1) |
+                ((int)((base >> s2) & 1) << 2);
+  return d.y + f * 8;
+}
+
+// The register-chain pipeline of k_rchain with table gates: the descriptor of
+// gate gi+2 and the table slice of gate gi+1 are loaded while gate gi runs.
+template <typename T, int RB, typename I, int STAGES, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_tchain(const ChainParams p,
+                                                      const T *__restrict__ X,
+                                                      const T *__restrict__ A,
+                                                      T *__restrict__ C, int64_t ib) {
+  typedef typename Vec4<T>::t V;
+  X = inst_ptr(X, ib);
+  A = inst_ptr(A, ib);
+  C = inst_ptr(C, ib);
+  __shared__ __align__(16) T sT[TN_CHAIN_MAX_G * TN_TG_TABLE];
+  __shared__ int4 sD[TN_CHAIN_MAX_G + 2];
+  extern __shared__ __align__(16) char rstage[];
+  T *stage = reinterpret_cast<T *>(rstage);
+  build_tables<T>(p, X, sT);
+  if (threadIdx.x < TN_CHAIN_MAX_G + 2) {
+    const int k = threadIdx.x;
+    int4 d = make_int4(-1, 0, 0, 0);
+    if (k < p.ntg) {
+      const TGate &t = p.tg[k];
+      const int zb = (int)sizeof(I) * 8 - 1;   // a digit that is always 0
+      int sh[TN_TG_MAXF];
+      for (int i = 0; i < TN_TG_MAXF; ++i) sh[i] = i < t.nf ? t.fsh[i] : zb;
+      d = make_int4(t.code, t.toff, sh[0] | (sh[1] << 8) | (sh[2] << 16), 0);
+    }
+    sD[k] = d;
+  }
+  __syncthreads();
+  I sS[RB];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) sS[j] = (I)p.hi_off[1 << j];
+  const int nt = blockDim.x, tid = threadIdx.x;
+  const int64_t step = (int64_t)gridDim.x * nt;
+  int64_t tau = blockIdx.x * (int64_t)nt + tid;
+  auto issue = [&](int64_t t, T *dst) {
+    if (t < p.outer) {
+      const T *src = A + rc_base<I>(p, t);
+      I o[1 << RB];
+      o[0] = 0;
+#pragma unroll
+      for (int e = 1; e < (1 << RB); ++e) {
+        const int hb = 31 - __clz(e);
+        o[e] = o[e ^ (1 << hb)] + sS[hb];
+      }
+#pragma unroll
+      for (int e = 0; e < (1 << RB); ++e) cp_async4(dst + e * nt + tid, src + o[e]);
+    }
+    cp_async_commit();
+  };
+  auto slot = [&](int it) { return stage + (it % STAGES) * (1 << RB) * nt; };
+#pragma unroll
+  for (int s2 = 0; s2 < STAGES - 1; ++s2) issue(tau + s2 * step, slot(s2));
+  const int ntg = p.ntg;
+  for (int it = 0; tau < p.outer; tau += step, ++it) {
+    T *cur = slot(it);
+    issue(tau + (STAGES - 1) * step, slot(it + STAGES - 1));
+    if (STAGES == 3)
+      asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+    else
+      cp_async_wait_prev();
+    const I bi = rc_base<I>(p, tau);
+    T v[1 << RB];
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) v[e] = cur[e * nt + tid];
+    int4 d0 = sD[0], d1 = sD[1];
+    int a0 = tc_slice<I>(d0, bi);
+    V lo = *reinterpret_cast<const V *>(sT + a0), hi = *reinterpret_cast<const V *>(sT + a0 + 4);
+    for (int gi = 0; gi < ntg; ++gi) {
+      const int4 d2 = sD[gi + 2];
+      const int a1 = tc_slice<I>(d1, bi);
+      const V lo1 = *reinterpret_cast<const V *>(sT + a1);
+      const V hi1 = *reinterpret_cast<const V *>(sT + a1 + 4);
+      tc_apply<RB>(d0.x, v, lo, hi);
+      d0 = d1;
+      d1 = d2;
+      lo = lo1;
+      hi = hi1;
+    }
+    T *dst = C + bi;
+    I o[1 << RB];
+    o[0] = 0;
+#pragma unroll
+    for (int e = 1; e < (1 << RB); ++e) {
+      const int hb = 31 - __clz(e);
+      o[e] = o[e ^ (1 << hb)] + sS[hb];
+    }
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) dst[o[e]] = v[e];
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // ---- counting register chains (q = 2, P = 4 residue planes): every thread
 // keeps the 2^RB values and their 4 residues in registers.  A tie adds the
 // counts of the tied states; the gate's own counts multiply in unless it is a
@@ -1354,6 +1654,79 @@ cudaError_t launch_rchain_count(Dtype dt, const ChainParams &p, const char *aren
 // 2^t elements of the fixed outer index; the gates are replayed (every
 // intermediate kept in shared memory) with the forward's operation order,
 // then lane 0 undoes each replace gate with the first-index argmax.
+// Traceback of a folded register chain: the 32 elements selected by the
+// outer spins are recomputed through the table gates in a warp (the same
+// sums as the forward kernel), then walked backwards through the replace
+// gates; ties keep the contracted digit 0.
+template <typename T>
+__device__ void trace_tchain(const ChainTrace &ct, const T *X, int8_t *state, int *err, T *buf,
+                             T *sT) {
+  const ChainParams &p = ct.p;
+  const int E = p.tile;
+  build_tables<T>(p, X, sT);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    int64_t part = 0;
+    for (int i = lane; i < ct.nout; i += 32) {
+      int d = state[ct.out_spin[i]];
+      if (d < 0 || d > 1) { *err = 1; d = 0; }
+      part += (int64_t)d * ct.out_stride[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const int64_t base = part;
+    auto slice = [&](const TGate &t) {
+      int f = 0;
+      for (int i = 0; i < t.nf; ++i) f |= (int)((base >> t.fsh[i]) & 1) << i;
+      return sT + t.toff + f * 8;
+    };
+    for (int e = lane; e < E; e += 32) buf[e] = X[ct.offIn + base + p.hi_off[e]];
+    __syncwarp();
+    for (int gi = 0; gi < p.ntg; ++gi) {
+      const TGate &t = p.tg[gi];
+      const T *src = buf + (int64_t)gi * E;
+      T *dst = buf + (int64_t)(gi + 1) * E;
+      const T *tab = slice(t);
+      for (int e = lane; e < E; e += 32) {
+        if (t.kind != 0) {
+          const int x0 = t.J >= 0 ? (e >> t.J) & 1 : 0, x1 = t.K >= 0 ? (e >> t.K) & 1 : 0;
+          dst[e] = src[e] + tab[x0 | (x1 << 1)];
+        } else if (!(e & (1 << t.J))) {
+          const int e1 = e | (1 << t.J);
+          const int k = t.K >= 0 ? (e >> t.K) & 1 : 0;
+          const T a = src[e], b = src[e1];
+          dst[e] = max(a + tab[k * 4 + 0], b + tab[k * 4 + 1]);
+          dst[e1] = max(a + tab[k * 4 + 2], b + tab[k * 4 + 3]);
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      int x = 0;
+      for (int j = 0; j < p.t; ++j) {
+        int d = state[ct.local_spin[j]];
+        if (d < 0 || d > 1) { *err = 1; d = 0; }
+        x |= d << j;
+      }
+      for (int gi = p.ntg - 1; gi >= 0; --gi) {
+        const TGate &t = p.tg[gi];
+        if (t.kind != 0) continue;
+        const T *src = buf + (int64_t)gi * E;
+        const T *tab = slice(t);
+        const int v = (x >> t.J) & 1;
+        const int x0 = x & ~(1 << t.J);
+        const int k = t.K >= 0 ? (x0 >> t.K) & 1 : 0;
+        const T c0 = src[x0] + tab[k * 4 + v * 2 + 0];
+        const T c1 = src[x0 | (1 << t.J)] + tab[k * 4 + v * 2 + 1];
+        const int u = c1 > c0 ? 1 : 0;
+        state[t.kspin] = (int8_t)u;
+        x = x0 | (u << t.J);
+      }
+    }
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __device__ void trace_rchain(const ChainTrace &ct, const T *X, int8_t *state, int *err,
                              char *smem, int64_t *sbase) {
@@ -1361,6 +1734,10 @@ __device__ void trace_rchain(const ChainTrace &ct, const T *X, int8_t *state, in
   const int E = p.tile;   // 32
   T *buf = reinterpret_cast<T *>(smem);
   T *sBg = buf + (int64_t)(p.ngates + 1) * E;   // staged gate operands
+  if (p.ntg > 0) {
+    trace_tchain<T>(ct, X, state, err, buf, sBg);
+    return;
+  }
   load_gate_operands<T>(p, X, nullptr, sBg, nullptr, kGateBMax);
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -1439,6 +1816,19 @@ static cudaError_t launch_rchain_s(const ChainParams &p, const char *arena, cons
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
+  }
+  if (RB == 5 && p.ntg > 0) {
+    static bool tconfigured = false;
+    if (!tconfigured) {
+      cudaError_t e = cudaFuncSetAttribute(k_tchain<T, RB, I, STAGES, MINB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      tconfigured = true;
+    }
+    k_tchain<T, RB, I, STAGES, MINB><<<dim3(blocks, bt.B), 256, smem, st>>>(
+        p, reinterpret_cast<const T *>(arena), static_cast<const T *>(Ax), static_cast<T *>(Cx),
+        bt.ib);
+    return cudaGetLastError();
   }
   k_rchain<T, RB, I, STAGES, MINB><<<dim3(blocks, bt.B), 256, smem, st>>>(
       p, reinterpret_cast<const T *>(arena), static_cast<const T *>(Ax), static_cast<T *>(Cx),
@@ -1615,7 +2005,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceStep *__rest
 
 size_t trace_smem_bytes(const ChainParams &p, size_t elem) {
   if (p.mode == 1)
-    return elem * ((size_t)(p.ngates + 1) * p.tile + (size_t)TN_CHAIN_MAX_G * kGateBMax);
+    return elem * ((size_t)(p.ngates + 1) * p.tile + (size_t)TN_CHAIN_MAX_G * TN_TG_TABLE);
   return elem * ((size_t)(p.ngates + 1) * p.tile + (size_t)TN_CHAIN_MAX_G * kGateBMax);
 }
 

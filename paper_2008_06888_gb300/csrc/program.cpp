@@ -35,6 +35,147 @@ int pos_of(const std::vector<int> &v, int x) {
   return -1;
 }
 
+// ---- folding a register chain's diagonal gates into its replace gates.
+//
+// A diagonal term D that does not depend on the digit a replace gate
+// eliminates commutes with that gate's max, and one that depends on the
+// digit the gate creates can be added after it: so D is added into the
+// table of the replace gate that last created one of D's register legs
+// ("post"), else of the first one that later eliminates one of them ("pre"),
+// provided D's other legs keep their spins in between.  Terms on fixed legs
+// only are per-thread constants and go into any replace gate.  Diagonal
+// gates that fit nowhere remain table gates of their own.
+
+static bool tg_fixed_bit(TGate &t, int sh, int8_t *bit) {
+  for (int i = 0; i < t.nf; ++i)
+    if (t.fsh[i] == sh) { *bit = (int8_t)(3 + i); return true; }
+  if (t.nf >= TN_TG_MAXF) return false;
+  t.fsh[t.nf] = (int8_t)sh;
+  *bit = (int8_t)(3 + t.nf);
+  t.nf++;
+  return true;
+}
+
+// add diagonal gate d of cp into replace table t; jbit: table bit of the leg
+// on t's register bit J (0 pre, 1 post)
+static bool tg_add_diag(const ChainParams &cp, int d, TGate &t, int jbit) {
+  if (t.ncomp >= TN_TG_MAXC) return false;
+  TGate u = t;
+  const ChainGate &g = cp.g[d];
+  const int c = u.ncomp;
+  u.cg[c] = (int8_t)d;
+  u.cbit[c][0] = u.cbit[c][1] = u.cbit[c][2] = u.cbit[c][3] = -1;
+  for (int l = 0; l < g.nb; ++l) {
+    int8_t bit;
+    if (g.lsb[l] < 0) {
+      if (!tg_fixed_bit(u, g.lsbh[l], &bit)) return false;
+    } else if (g.lsb[l] == u.J) {
+      if (jbit < 0) return false;
+      bit = (int8_t)jbit;
+    } else {
+      if (u.K >= 0 && u.K != g.lsb[l]) return false;
+      u.K = (int8_t)g.lsb[l];
+      bit = 2;
+    }
+    u.cbit[c][2 + l] = bit;
+  }
+  u.ncomp++;
+  t = u;
+  return true;
+}
+
+static void fold_reg_chain(ChainParams &cp) {
+  const int n = cp.ngates;
+  std::vector<TGate> tg;
+  std::vector<int> at;               // position of each table gate in the chain
+  std::vector<int> of(n, -1);        // replace gate -> its table gate
+  for (int i = 0; i < n; ++i) {
+    const ChainGate &g = cp.g[i];
+    if (g.kind != 0) continue;
+    TGate t{};
+    t.kind = 0;
+    t.J = (int8_t)g.ls;
+    t.K = -1;
+    t.kspin = g.kspin;
+    t.cg[0] = (int8_t)i;
+    t.cbit[0][0] = 0;
+    t.cbit[0][1] = 1;
+    t.cbit[0][2] = t.cbit[0][3] = -1;
+    if (g.nb > 0) {
+      if (g.lsb[0] >= 0) {
+        t.K = (int8_t)g.lsb[0];
+        t.cbit[0][2] = 2;
+      } else {
+        tg_fixed_bit(t, g.lsbh[0], &t.cbit[0][2]);
+      }
+    }
+    t.ncomp = 1;
+    of[i] = (int)tg.size();
+    tg.push_back(t);
+    at.push_back(i);
+  }
+  auto last_rep = [&](int r, int p) {
+    for (int i = p - 1; i >= 0; --i)
+      if (cp.g[i].kind == 0 && cp.g[i].ls == r) return i;
+    return -1;
+  };
+  for (int d = 0; d < n; ++d) {
+    const ChainGate &g = cp.g[d];
+    if (g.kind != 1) continue;
+    std::vector<int> regs;
+    for (int l = 0; l < g.nb; ++l)
+      if (g.lsb[l] >= 0) regs.push_back(g.lsb[l]);
+    bool done = false;
+    if (regs.empty()) {
+      for (size_t k = 0; k < tg.size() && !done; ++k) done = tg_add_diag(cp, d, tg[k], -1);
+    } else {
+      int cs = -1;
+      for (int r : regs) cs = std::max(cs, last_rep(r, d));
+      if (cs >= 0) done = tg_add_diag(cp, d, tg[of[cs]], 1);
+      if (!done) {
+        for (int j = d + 1; j < n; ++j) {
+          if (cp.g[j].kind != 0) continue;
+          if (std::find(regs.begin(), regs.end(), cp.g[j].ls) == regs.end()) continue;
+          done = tg_add_diag(cp, d, tg[of[j]], 0);
+          break;
+        }
+      }
+    }
+    if (done) continue;
+    TGate t{};
+    t.kind = 1;
+    t.J = regs.size() > 0 ? (int8_t)regs[0] : (int8_t)-1;
+    t.K = regs.size() > 1 ? (int8_t)regs[1] : (int8_t)-1;
+    if (t.K >= 0 && t.K < t.J) std::swap(t.J, t.K);
+    t.kspin = -1;
+    t.cg[0] = (int8_t)d;
+    t.cbit[0][0] = t.cbit[0][1] = t.cbit[0][2] = t.cbit[0][3] = -1;
+    for (int l = 0; l < g.nb; ++l) {
+      int8_t bit = -1;
+      if (g.lsb[l] < 0) tg_fixed_bit(t, g.lsbh[l], &bit);   // at most 2 of 3 slots
+      else bit = g.lsb[l] == t.J ? 0 : 1;
+      t.cbit[0][2 + l] = bit;
+    }
+    t.ncomp = 1;
+    tg.push_back(t);
+    at.push_back(d);
+  }
+  std::vector<int> ord(tg.size());
+  for (size_t k = 0; k < ord.size(); ++k) ord[k] = (int)k;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return at[a] < at[b]; });
+  int off = 0;
+  cp.ntg = (int)tg.size();
+  for (size_t k = 0; k < ord.size(); ++k) {
+    TGate t = tg[ord[k]];
+    for (int i = t.nf; i < TN_TG_MAXF; ++i) t.fsh[i] = 62;   // a digit that is always 0
+    t.code = t.kind == 0 ? (int16_t)(t.J * 6 + (t.K + 1)) : (int16_t)(30 + (t.J + 1) * 6 + (t.K + 1));
+    t.toff = (int16_t)off;
+    off += 8 << t.nf;
+    cp.tg[k] = t;
+  }
+  cp.ttotal = off;
+}
+
 struct Builder {
   const Net &net;
   const Plan &plan;
@@ -458,6 +599,7 @@ struct Builder {
   std::vector<int> macro_of;    // tensor -> macro producing it
   bool fuse = true;
   bool regmode = false;         // q == 2 values: register chains (ChainParams mode 1)
+  bool fold = true;             // fold diagonal gates into replace tables (values only)
   int kRB = 5;                  // register legs of a register chain (4 or 5)
   int tmax = 11, wlow = 5;
   Macro open;
@@ -603,6 +745,7 @@ struct Builder {
       blocs->push_back(loc[g.btensor]);
     }
     cp.P = P;
+    if (P == 0 && fold) fold_reg_chain(cp);
     return cp;
   }
 
@@ -857,6 +1000,7 @@ struct Builder {
     fuse = std::getenv("TN_NO_FUSION") == nullptr;
     // register chains: q = 2 values, or q = 2 counts with 3 primes + witness
     regmode = q == 2 && (P == 0 || P == 4) && std::getenv("TN_TILE_CHAINS") == nullptr;
+    fold = std::getenv("TN_NO_FOLD") == nullptr;
     if (const char *rb = std::getenv("TN_REG_BITS")) kRB = std::atoi(rb) == 4 ? 4 : 5;
     if (P > 0) kRB = 3;
     if (q == 3) { tmax = 7; wlow = 4; }
@@ -941,10 +1085,13 @@ bool build_program(const Net &net, const Plan &plan, ProgMode mode, Dtype dt, in
   }
   plan_memory(*pr);
   if (const char *dump = std::getenv("TN_DUMP_PROGRAM")) {
-    if (*dump == '1') {
+    // "1": every program built; "c": only traceback / counting programs
+    if (*dump == '1' || (*dump == 'c' && mode != PM_ENERGY)) {
+      std::fprintf(stderr, "program mode %d ops %zu\n", (int)mode, pr->ops.size());
       for (size_t i = 0; i < pr->ops.size(); ++i) {
         const Op &o = pr->ops[i];
-        std::fprintf(stderr, "op %zu kind %d in0 %lld in1 %lld out %lld", i, (int)o.kind,
+        std::fprintf(stderr, "op %zu kind %d bytes %.0f in0 %lld in1 %lld out %lld", i, (int)o.kind,
+                     o.bytes,
                      (long long)(o.in0.buf >= 0 ? o.in0.plane : -1),
                      (long long)(o.in1.buf >= 0 ? o.in1.plane : -1),
                      (long long)(o.out.buf >= 0 ? o.out.plane : -1));

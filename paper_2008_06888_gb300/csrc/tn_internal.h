@@ -114,6 +114,33 @@ struct ChainGate {
   int64_t sBb[2];    // B strides of the tile legs
 };
 
+// Folded register-chain gate (q = 2, values only).  Every diagonal gate that
+// shares a leg with a replace gate of the same chain is added into that
+// replace gate's operand (a term that does not depend on the eliminated digit
+// commutes with the max), so a chain becomes a short list of table gates.
+// A table gate reads one table of 8 << nf values:
+//   index bit 0: contracted digit x (replace) / register leg J (diagonal)
+//   index bit 1: new digit x'       (replace) / register leg K (diagonal)
+//   index bit 2: register leg K     (replace; 0 when K < 0)
+//   index bits 3..: digits of the fixed legs, (base >> fsh[i]) & 1
+// The table is the sum of its components: component c is original gate
+// cg[c]'s operand B, read at the offset sum over its legs l (contracted,
+// new, tile leg 0, tile leg 1) of digit(index bit cbit[c][l]) * stride(l).
+#define TN_TG_MAXC 8
+#define TN_TG_MAXF 3
+#define TN_TG_TABLE 64       // largest table (8 << TN_TG_MAXF values)
+struct TGate {
+  int8_t kind;                  // 0 replace, 1 diagonal
+  int8_t J, K;                  // register legs (-1: none)
+  int8_t nf, ncomp;
+  int8_t fsh[TN_TG_MAXF];       // shifts of the fixed legs' digits in base
+  int8_t cg[TN_TG_MAXC];        // original gate of each component
+  int8_t cbit[TN_TG_MAXC][4];   // table bit of each of its legs (-1: absent)
+  int16_t code;                 // kernel dispatch code of (kind, J, K)
+  int16_t toff;                 // table offset (values) in shared memory
+  int32_t kspin;                // replace: contracted spin (traceback)
+};
+
 // mode 1 (q = 2 only, "register chains"): every thread owns the 2^t elements
 // that differ in the chain's replaced legs (the register legs; t = RB); the
 // replace gate's ls is a register-bit index, a B leg is a register bit
@@ -135,6 +162,9 @@ struct ChainParams {
   int32_t seg_ssh[TN_MAX_SEG]; // log2(seg_s) when q == 2 (register chains)
   int64_t planeA, planeC;  // plane distances of input and output
   ChainGate g[TN_CHAIN_MAX_G];
+  int32_t ntg;             // folded table gates (mode 1, P == 0); 0: use g[]
+  int32_t ttotal;          // values of all their tables
+  TGate tg[TN_CHAIN_MAX_G];
 };
 
 // Traceback record of a chain: the tile of the chain input selected by the

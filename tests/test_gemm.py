@@ -18,7 +18,7 @@ def built():
 
 
 SHAPES = [(1, 1, 1, 1), (2, 5, 7, 3), (1, 128, 128, 16), (3, 130, 67, 33), (1, 257, 129, 80),
-          (4, 64, 300, 17), (1, 1, 500, 257)]
+          (4, 64, 300, 17), (1, 1, 500, 257), (2, 256, 384, 48)]
 
 
 @pytest.mark.parametrize("dtype", ["float32", "int32"])

@@ -16,6 +16,13 @@ namespace tn {
 
 // ---------------------------------------------------------------- helpers
 
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 t; };
+template <> struct Vec2<int32_t> { typedef int2 t; };
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 t; };
+template <> struct Vec4<int32_t> { typedef int4 t; };
+
 template <typename T> struct Lim;
 template <> struct Lim<float> {
   __device__ __forceinline__ static float neg() { return -INFINITY; }
@@ -289,6 +296,161 @@ static bool launch_gate_t(const GateParams &p, const T *A, const T *B, T *C, dim
   return false;
 }
 
+// ---- streaming q = 2 gate contractions (values).
+//
+// When every size is a power of two, C keeps A's leg order with the K leg
+// removed and the N leg (if any) innermost, an output index is
+// (j, n) with j the outer index: A's offset is j with a 0/1 digit inserted at
+// bit pk of the contracted leg, and B reduces to a table over (k, n) and at
+// most two batch digits of j.  Each thread maps 4 consecutive j to one or
+// two 16-byte loads of A per digit and one or two 16-byte stores of C.
+struct Gate2 {
+  int pk;          // bit of the contracted leg in A's offset (KS == 2)
+  int nbd;         // batch legs (digits of j read by B)
+  int pb[2];       // their bits in j
+  int64_t sb[2];   // their strides in B
+};
+
+template <typename T, int KS, int NS>
+__global__ void __launch_bounds__(256) k_gate2(const GateParams p, const Gate2 g,
+                                               const T *__restrict__ A, const T *__restrict__ B,
+                                               T *__restrict__ C, int64_t ib) {
+  typedef typename Vec4<T>::t V;
+  A = inst_ptr(A, ib);
+  C = inst_ptr(C, ib);
+  if (p.hasB) B = inst_ptr(B, ib);
+  __shared__ T sBt[16];   // index: bd0 | bd1 << 1 | k << 2 | n << 3
+  if (threadIdx.x < 16) {
+    const int i = threadIdx.x, b0 = i & 1, b1 = (i >> 1) & 1, k = (i >> 2) & 1, n = (i >> 3) & 1;
+    T v = T(0);
+    if (p.hasB && k < KS && n < NS && (b0 == 0 || g.nbd > 0) && (b1 == 0 || g.nbd > 1))
+      v = B[p.kB[k] + p.nB[n] + b0 * g.sb[0] + b1 * g.sb[1]];
+    sBt[i] = v;
+  }
+  __syncthreads();
+  const int pb0 = g.nbd > 0 ? g.pb[0] : 62, pb1 = g.nbd > 1 ? g.pb[1] : 62;
+  const int pk = g.pk;
+  const int64_t nq = p.outer >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t0 < nq; t0 += 2 * stride) {
+    T a[2][KS][4];
+    bool live[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t t = t0 + u * stride;
+      live[u] = t < nq;
+      const int64_t j0 = (live[u] ? t : 0) << 2;
+      if (KS == 1) {
+        const V v = *reinterpret_cast<const V *>(A + j0);
+        a[u][0][0] = v.x; a[u][0][1] = v.y; a[u][0][2] = v.z; a[u][0][3] = v.w;
+      } else if (pk >= 2) {
+        const int64_t lo = j0 & ((int64_t(1) << pk) - 1);
+        const int64_t base = ((j0 >> pk) << (pk + 1)) | lo;
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          const V v = *reinterpret_cast<const V *>(A + base + ((int64_t)k << pk));
+          a[u][k][0] = v.x; a[u][k][1] = v.y; a[u][k][2] = v.z; a[u][k][3] = v.w;
+        }
+      } else {
+        // the contracted leg is one of the two lowest bits: 8 contiguous values
+        const V v0 = *reinterpret_cast<const V *>(A + 2 * j0);
+        const V v1 = *reinterpret_cast<const V *>(A + 2 * j0 + 4);
+        const T blk[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4)
+#pragma unroll
+          for (int k = 0; k < KS; ++k)
+            a[u][k][q4] = pk == 0 ? blk[2 * q4 + k] : blk[((q4 >> 1) << 2) | (k << 1) | (q4 & 1)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!live[u]) continue;
+      const int64_t j0 = (t0 + u * stride) << 2;
+      T out[4 * NS];
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const int64_t j = j0 + q4;
+        const int bd = (int)((j >> pb0) & 1) | ((int)((j >> pb1) & 1) << 1);
+#pragma unroll
+        for (int n = 0; n < NS; ++n) {
+          T best = a[u][0][q4] + sBt[bd | (n << 3)];
+#pragma unroll
+          for (int k = 1; k < KS; ++k) best = max(best, a[u][k][q4] + sBt[bd | (k << 2) | (n << 3)]);
+          out[NS * q4 + n] = best;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < NS; ++h) {
+        V v;
+        v.x = out[4 * h + 0]; v.y = out[4 * h + 1]; v.z = out[4 * h + 2]; v.w = out[4 * h + 3];
+        *reinterpret_cast<V *>(C + NS * j0 + 4 * h) = v;
+      }
+    }
+  }
+}
+
+// Whether a (values) gate has the streaming q = 2 form; fills g.
+static bool gate2_form(const GateParams &p, const void *A, const void *B, const void *C,
+                       int64_t ib, size_t elem, Gate2 *g) {
+  if (p.P > 0 || p.outer < 4 || (p.outer & 3)) return false;
+  if (!((p.Ks == 1 || p.Ks == 2) && (p.Ns == 1 || p.Ns == 2))) return false;
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(C)) % 16 ||
+      (ib * (int64_t)elem) % 16)
+    return false;
+  (void)B;
+  *g = Gate2{};
+  g->pk = 0;
+  if (p.Ks == 2) {
+    if (p.kA[0] != 0 || p.kA[1] <= 0 || (p.kA[1] & (p.kA[1] - 1))) return false;
+    while ((int64_t(1) << g->pk) < p.kA[1]) g->pk++;
+  }
+  if (p.Ns == 2 && (p.nC[0] != 0 || p.nC[1] != 1)) return false;
+  // segments slowest first: dense in C (times Ns), A = C's layout with pk inserted
+  int64_t js = 1;
+  for (int s = p.nseg - 1; s >= 0; --s) {
+    if (p.seg_sh[s] < 0) return false;
+    if (p.seg_sC[s] != js * p.Ns) return false;
+    const int64_t a = (p.Ks == 2 && js >= (int64_t(1) << g->pk)) ? 2 * js : js;
+    if (p.Ks == 2 && js < (int64_t(1) << g->pk) && js * p.seg_size[s] > (int64_t(1) << g->pk))
+      return false;
+    if (p.seg_sA[s] != a) return false;
+    if (p.seg_sB[s] != 0) {
+      if (!p.hasB || p.seg_size[s] != 2 || g->nbd >= 2) return false;
+      int b = 0;
+      while ((int64_t(1) << b) < js) ++b;
+      g->pb[g->nbd] = b;
+      g->sb[g->nbd] = p.seg_sB[s];
+      g->nbd++;
+    }
+    js *= p.seg_size[s];
+  }
+  return js == p.outer;
+}
+
+template <typename T>
+static bool launch_gate2(const GateParams &p, const T *A, const T *B, T *C, const Batch &bt,
+                         cudaStream_t st) {
+  Gate2 g;
+  if (std::getenv("TN_NO_GATE2") || !gate2_form(p, A, B, C, bt.ib, sizeof(T), &g)) return false;
+  const int64_t nq = p.outer >> 2;
+  int64_t blocks = (nq + 511) / 512;
+  const int64_t cap = std::max<int64_t>(1, 152 * 8 / bt.B);
+  if (blocks > cap) blocks = cap;
+  dim3 grid((unsigned)blocks, bt.B);
+#define TN_G2(KS_, NS_)                                                            \
+  if (p.Ks == KS_ && p.Ns == NS_) {                                                \
+    k_gate2<T, KS_, NS_><<<grid, 256, 0, st>>>(p, g, A, B, C, bt.ib);              \
+    return true;                                                                   \
+  }
+  TN_G2(1, 1)
+  TN_G2(1, 2)
+  TN_G2(2, 1)
+  TN_G2(2, 2)
+#undef TN_G2
+  return false;
+}
+
 cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const void *xB, void *xC,
                         const uint64_t *nA, const uint64_t *nB, uint64_t *nC, const PrimeSet &ps,
                         const Batch &bt, cudaStream_t st) {
@@ -297,6 +459,12 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
   dim3 blocks(grid_for(p.outer, threads), bt.B);
   bool cnt = p.P > 0;
   if (!cnt) {
+    const bool streamed = dt == DT_F32
+                              ? launch_gate2<float>(p, (const float *)xA, (const float *)xB,
+                                                    (float *)xC, bt, st)
+                              : launch_gate2<int32_t>(p, (const int32_t *)xA, (const int32_t *)xB,
+                                                      (int32_t *)xC, bt, st);
+    if (streamed) return cudaGetLastError();
     dim3 b2(grid_for((p.outer + 1) / 2, threads), bt.B);
     const bool done = dt == DT_F32
                           ? launch_gate_t<float>(p, (const float *)xA, (const float *)xB,
@@ -529,13 +697,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
-
-template <typename T> struct Vec2;
-template <> struct Vec2<float> { typedef float2 t; };
-template <> struct Vec2<int32_t> { typedef int2 t; };
-template <typename T> struct Vec4;
-template <> struct Vec4<float> { typedef float4 t; };
-template <> struct Vec4<int32_t> { typedef int4 t; };
 
 constexpr int GAK = GBK + 4;   // padded row of As[m][k]
 

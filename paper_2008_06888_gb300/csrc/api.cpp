@@ -17,6 +17,7 @@
 #include "kernels.h"
 #include "planner.h"
 #include "program.h"
+#include "jit.h"
 
 using namespace tn;
 
@@ -188,6 +189,13 @@ tn_status get_program(tn_ctx *ctx, ProgMode mode, int P, Program **out) {
                     p.chain_traces.size() * sizeof(ChainTrace), cudaMemcpyHostToDevice));
     }
     if (mode == PM_COUNT) ctx->prog_P = P;
+    // large value chains run as kernels compiled for their gate sequence; if
+    // that fails they stay on the interpreting kernel (TN_JIT_STRICT: error)
+    std::string jerr;
+    if (!jit_chains(p.chains, p.dt, &p.chain_jit, &jerr)) {
+      p.chain_jit.assign(p.chains.size(), nullptr);
+      if (std::getenv("TN_JIT_STRICT")) return fail(ctx, TN_ECUDA, jerr);
+    }
   }
   Program &p = *slot;
   if (p.arena_bytes > ctx->arena_cap) {
@@ -299,8 +307,12 @@ tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_
                          p.trace_smem, ar, ra.state, ctx->net.n, ctx->d_err, bt, st);
         break;
       case OP_CHAIN:
-        e = launch_chain(p.dt, p.chains[op.idx], ar, X(op.in0), Nn(op.in0), X(op.out), Nn(op.out),
-                         ps, bt, st);
+        if (op.idx < (int)p.chain_jit.size() && p.chain_jit[op.idx])
+          e = launch_jit_chain(p.chain_jit[op.idx], p.chains[op.idx], ar, X(op.in0), X(op.out), bt,
+                               st);
+        else
+          e = launch_chain(p.dt, p.chains[op.idx], ar, X(op.in0), Nn(op.in0), X(op.out),
+                           Nn(op.out), ps, bt, st);
         break;
     }
     if (e != cudaSuccess)

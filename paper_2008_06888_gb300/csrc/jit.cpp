@@ -1,0 +1,319 @@
+// jit.cpp -- straight-line register-chain kernels compiled at run time.
+//
+// The interpreting kernel (k_tchain) reads each table gate's descriptor and
+// dispatches on its register legs for every outer index.  Here every large
+// chain gets its own kernel: the source below spells out the chain's gates
+// on 32 named registers, with the outer-index decoding and the register-leg
+// offsets as constants.  Tables are built by the same device function as in
+// the interpreter and every gate does the same additions and maxima in the
+// same order, so the results are bit-identical to the interpreter's (and the
+// traceback, which replays chains through the interpreter's tables, sees the
+// same values).
+#include "jit.h"
+
+#include <dlfcn.h>
+#include <nvrtc.h>
+#include <sys/stat.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <thread>
+
+namespace tn {
+
+#include "jit_headers.inc"   // kJitTnInternal, kJitChainDev: header texts for NVRTC
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRB = 5;
+
+uint64_t fnv1a(const std::string &s, uint64_t h = 1469598103934665603ull) {
+  for (unsigned char c : s) {
+    h ^= c;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+std::string cache_dir() {
+  if (const char *d = std::getenv("TN_JIT_CACHE")) return d;
+  Dl_info info;
+  if (dladdr(reinterpret_cast<const void *>(&fnv1a), &info) && info.dli_fname) {
+    std::string f = info.dli_fname;
+    const size_t sl = f.rfind('/');
+    if (sl != std::string::npos) return f.substr(0, sl) + "/_jit_cache";
+  }
+  return "";
+}
+
+bool read_file(const std::string &path, std::string *out) {
+  std::ifstream in(path, std::ios::binary);
+  if (!in) return false;
+  std::ostringstream ss;
+  ss << in.rdbuf();
+  *out = ss.str();
+  return !out->empty();
+}
+
+void write_file_atomic(const std::string &path, const std::string &data) {
+  const std::string tmp = path + ".tmp" + std::to_string((unsigned long long)std::hash<std::thread::id>()(std::this_thread::get_id()));
+  {
+    std::ofstream out(tmp, std::ios::binary);
+    if (!out) return;
+    out.write(data.data(), (std::streamsize)data.size());
+    if (!out) return;
+  }
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+// NVRTC: source -> cubin for sm_103a
+bool compile(const std::string &src, const std::string &name, std::string *cubin,
+             std::string *err) {
+  nvrtcProgram prog;
+  const char *hdrs[2] = {kJitTnInternal, kJitChainDev};
+  const char *names[2] = {"tn_internal.h", "chain_dev.cuh"};
+  if (nvrtcCreateProgram(&prog, src.c_str(), (name + ".cu").c_str(), 2, hdrs, names) !=
+      NVRTC_SUCCESS) {
+    *err = "nvrtcCreateProgram failed";
+    return false;
+  }
+  const char *opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "--ptxas-options=-v"};
+  const bool verbose = std::getenv("TN_JIT_VERBOSE") != nullptr;
+  const nvrtcResult r = nvrtcCompileProgram(prog, verbose ? 4 : 3, opts);
+  if (verbose && r == NVRTC_SUCCESS) {
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string log(n, '\0');
+    if (n) nvrtcGetProgramLog(prog, &log[0]);
+    std::fprintf(stderr, "%s: %s\n", name.c_str(), log.c_str());
+  }
+  if (r != NVRTC_SUCCESS) {
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string log(n, '\0');
+    if (n) nvrtcGetProgramLog(prog, &log[0]);
+    *err = std::string("nvrtc: ") + nvrtcGetErrorString(r) + "\n" + log;
+    nvrtcDestroyProgram(&prog);
+    return false;
+  }
+  size_t n = 0;
+  nvrtcGetCUBINSize(prog, &n);
+  cubin->assign(n, '\0');
+  nvrtcGetCUBIN(prog, &(*cubin)[0]);
+  nvrtcDestroyProgram(&prog);
+  return n > 0;
+}
+
+struct Loaded {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kernel = nullptr;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, uint64_t>, Loaded> g_loaded;   // (device, source hash)
+
+bool worth(const ChainParams &p) {
+  static const long long min_el = [] {
+    const char *s = std::getenv("TN_JIT_MIN_ELEMENTS");
+    return s ? std::atoll(s) : (1ll << 20);
+  }();
+  return p.mode == 1 && p.P == 0 && p.t == kRB && p.ntg > 0 && p.outer * 32 >= min_el;
+}
+
+}  // namespace
+
+std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &name) {
+  const bool f32 = dt == DT_F32;
+  const char *T = f32 ? "float" : "int";
+  const char *MX = f32 ? "fmaxf" : "max";
+  const bool i32 = p.outer * 32 < (int64_t(1) << 31);
+  std::ostringstream o;
+  o << "#include \"chain_dev.cuh\"\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << kThreads << ", 2)\n"
+    << name << "(const ChainParams p, const " << T << " *__restrict__ X, const " << T
+    << " *__restrict__ A, " << T << " *__restrict__ C, long long ib) {\n"
+    << "  using namespace tn;\n"
+    << "  typedef " << T << " T;\n"
+    << "  typedef " << (i32 ? "int" : "long long") << " I;\n"
+    << "  typedef Vec4<T>::t V;\n"
+    << "  X = inst_ptr(X, ib);\n  A = inst_ptr(A, ib);\n  C = inst_ptr(C, ib);\n"
+    << "  __shared__ __align__(16) T sT[" << std::max(8, (int)p.ttotal) << "];\n"
+    << "  extern __shared__ __align__(16) char rstage[];\n"
+    << "  T *stage = reinterpret_cast<T *>(rstage);\n"
+    << "  const int tid = threadIdx.x;\n"
+    << "  const long long step = (long long)gridDim.x * " << kThreads << ";\n"
+    << "  long long tau = blockIdx.x * " << kThreads << "LL + tid;\n";
+  // outer index -> element offset (segments slowest first)
+  o << "  auto base = [](long long t) -> I {\n    I b = 0, u = (I)t;\n";
+  for (int sg = p.nseg - 1; sg >= 0; --sg)
+    o << "    b += (u & (I)" << (p.seg_size[sg] - 1) << ") << " << p.seg_ssh[sg] << ";\n"
+      << "    u >>= " << p.seg_sh[sg] << ";\n";
+  o << "    return b;\n  };\n";
+  const int E = 1 << kRB, S = E * kThreads;
+  o << "  auto issue = [&](long long t, int s) {\n"
+    << "    if (t < " << p.outer << "LL) {\n"
+    << "      const T *src = A + base(t);\n"
+    << "      T *dst = stage + s * " << S << " + tid;\n";
+  for (int e = 0; e < E; ++e)
+    o << "      cp_async4(dst + " << e * kThreads << ", src + " << p.hi_off[e] << ");\n";
+  o << "    }\n    cp_async_commit();\n  };\n"
+    << "  issue(tau, 0);\n"
+    << "  build_tables<T>(p, X, sT);\n"
+    << "  __syncthreads();\n"
+    << "  for (int it = 0; tau < " << p.outer << "LL; tau += step, ++it) {\n"
+    << "    const int cur = it & 1;\n"
+    << "    issue(tau + step, cur ^ 1);\n"
+    << "    cp_async_wait_prev();\n"
+    << "    const I bi = base(tau);\n"
+    << "    const T *sv = stage + cur * " << S << " + tid;\n";
+  for (int e = 0; e < E; ++e) o << "    T v" << e << " = sv[" << e * kThreads << "];\n";
+  for (int k = 0; k < p.ntg; ++k) {
+    const TGate &t = p.tg[k];
+    o << "    {  // table gate " << k << (t.kind == 0 ? ": replace" : ": diagonal") << "\n";
+    std::ostringstream f;
+    if (t.nf == 0) f << "0";
+    for (int i = 0; i < t.nf; ++i) {
+      if (i) f << " | ";
+      f << "((int)((bi >> " << (int)t.fsh[i] << ") & 1) << " << i << ")";
+    }
+    o << "      const int f = " << f.str() << ";\n"
+      << "      const V lo = *reinterpret_cast<const V *>(sT + " << t.toff << " + f * 8);\n";
+    if (t.kind == 0) {
+      if (t.K >= 0) o << "      const V hi = *reinterpret_cast<const V *>(sT + " << t.toff << " + f * 8 + 4);\n";
+      for (int e = 0; e < E; ++e) {
+        if (e & (1 << t.J)) continue;
+        const int e1 = e | (1 << t.J);
+        const char *tb = (t.K >= 0 && ((e >> t.K) & 1)) ? "hi" : "lo";
+        o << "      { const T a = v" << e << ", b = v" << e1 << "; v" << e << " = " << MX << "(a + "
+          << tb << ".x, b + " << tb << ".y); v" << e1 << " = " << MX << "(a + " << tb
+          << ".z, b + " << tb << ".w); }\n";
+      }
+    } else {
+      for (int e = 0; e < E; ++e) {
+        const int x0 = t.J >= 0 ? (e >> t.J) & 1 : 0, x1 = t.K >= 0 ? (e >> t.K) & 1 : 0;
+        const char *c = x1 ? (x0 ? "w" : "z") : (x0 ? "y" : "x");
+        o << "      v" << e << " = v" << e << " + lo." << c << ";\n";
+      }
+    }
+    o << "    }\n";
+  }
+  o << "    T *dst = C + bi;\n";
+  for (int e = 0; e < E; ++e) o << "    dst[" << p.hi_off[e] << "] = v" << e << ";\n";
+  o << "  }\n  asm volatile(\"cp.async.wait_all;\\n\" ::: \"memory\");\n}\n";
+  return o.str();
+}
+
+bool jit_chains(const std::vector<ChainParams> &chains, Dtype dt, std::vector<const void *> *out,
+                std::string *err) {
+  out->assign(chains.size(), nullptr);
+  if (std::getenv("TN_NO_JIT")) return true;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    *err = "no CUDA device for the chain kernels";
+    return false;
+  }
+  int nvrtc_major = 0, nvrtc_minor = 0;
+  nvrtcVersion(&nvrtc_major, &nvrtc_minor);
+  const std::string tag = "sm_103a nvrtc " + std::to_string(nvrtc_major) + "." +
+                          std::to_string(nvrtc_minor) + "\n";
+  struct Job {
+    size_t idx;
+    uint64_t h;
+    std::string name, src, cubin, err;
+    bool ok = false;
+  };
+  std::vector<Job> jobs;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (size_t i = 0; i < chains.size(); ++i) {
+      if (!worth(chains[i])) continue;
+      Job j;
+      j.idx = i;
+      const std::string probe = jit_chain_source(chains[i], dt, "tn_chain");
+      j.h = fnv1a(tag + probe);
+      char nm[40];
+      std::snprintf(nm, sizeof(nm), "tn_chain_%016llx", (unsigned long long)j.h);
+      j.name = nm;
+      auto it = g_loaded.find({dev, j.h});
+      if (it != g_loaded.end()) {
+        (*out)[i] = reinterpret_cast<const void *>(it->second.kernel);
+        continue;
+      }
+      j.src = jit_chain_source(chains[i], dt, j.name);
+      jobs.push_back(std::move(j));
+    }
+  }
+  if (jobs.empty()) return true;
+  const std::string dir = cache_dir();
+  if (!dir.empty()) mkdir(dir.c_str(), 0755);
+  std::atomic<size_t> next{0};
+  auto work = [&]() {
+    for (size_t k; (k = next.fetch_add(1)) < jobs.size();) {
+      Job &j = jobs[k];
+      const std::string path = dir.empty() ? "" : dir + "/" + j.name + ".cubin";
+      if (!path.empty() && read_file(path, &j.cubin)) {
+        j.ok = true;
+        continue;
+      }
+      j.ok = compile(j.src, j.name, &j.cubin, &j.err);
+      if (j.ok && !path.empty()) write_file_atomic(path, j.cubin);
+    }
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nth = std::min<size_t>(jobs.size(), std::min(32u, hw));
+  std::vector<std::thread> pool;
+  for (size_t t = 1; t < nth; ++t) pool.emplace_back(work);
+  work();
+  for (auto &t : pool) t.join();
+  std::lock_guard<std::mutex> lk(g_mu);
+  const size_t smem = 2 * 32 * kThreads * 4;
+  for (Job &j : jobs) {
+    if (!j.ok) {
+      *err = "chain kernel " + j.name + ": " + j.err;
+      return false;
+    }
+    auto it = g_loaded.find({dev, j.h});
+    if (it == g_loaded.end()) {
+      Loaded L;
+      cudaError_t e = cudaLibraryLoadData(&L.lib, j.cubin.data(), nullptr, nullptr, 0, nullptr,
+                                          nullptr, 0);
+      if (e == cudaSuccess) e = cudaLibraryGetKernel(&L.kernel, L.lib, j.name.c_str());
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void *>(L.kernel),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        *err = "loading chain kernel " + j.name + ": " + cudaGetErrorString(e);
+        return false;
+      }
+      it = g_loaded.emplace(std::make_pair(dev, j.h), L).first;
+    }
+    (*out)[j.idx] = reinterpret_cast<const void *>(it->second.kernel);
+  }
+  return true;
+}
+
+cudaError_t launch_jit_chain(const void *kernel, const ChainParams &p, const char *arena,
+                             const void *Ax, void *Cx, const Batch &bt, cudaStream_t st) {
+  if (p.outer == 0) return cudaSuccess;
+  int64_t blocks = (p.outer + kThreads - 1) / kThreads;
+  const int64_t cap = std::max<int64_t>(1, 152 * 2 / bt.B);
+  if (blocks > cap) blocks = cap;
+  const size_t smem = 2 * 32 * kThreads * 4;
+  ChainParams pc = p;
+  const void *X = arena;
+  const void *A = Ax;
+  void *C = Cx;
+  long long ib = bt.ib;
+  void *args[] = {&pc, &X, &A, &C, &ib};
+  return cudaLaunchKernel(kernel, dim3((unsigned)blocks, bt.B), dim3(kThreads), args, smem, st);
+}
+
+}  // namespace tn

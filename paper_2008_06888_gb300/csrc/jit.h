@@ -1,0 +1,33 @@
+// jit.h -- register chains compiled at run time.
+//
+// A register chain (q = 2, values, folded table gates) is a fixed sequence of
+// table gates over the 32 register elements of a thread.  For large chains
+// the program builder asks for a kernel specialised to that sequence: the
+// gates, the register-leg offsets and the outer-index decoding become
+// constants, so the chain runs as straight-line code without per-gate
+// dispatch.  Kernels are compiled with NVRTC for sm_103a (one program per
+// chain, in parallel), loaded with cudaLibraryLoadData and cached in memory
+// and on disk by a hash of their source.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "tn_internal.h"
+
+namespace tn {
+
+// Kernel handles (cudaKernel_t as const void *) for every chain that is
+// worth compiling; nullptr elsewhere (the interpreting kernel runs those).
+// Returns false with *err set if compilation or loading failed.
+bool jit_chains(const std::vector<ChainParams> &chains, Dtype dt, std::vector<const void *> *out,
+                std::string *err);
+
+// Source of the specialised kernel `name` for one chain (exposed for tests).
+std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &name);
+
+// Launch a compiled chain kernel with the interpreting kernel's grid.
+cudaError_t launch_jit_chain(const void *kernel, const ChainParams &p, const char *arena,
+                             const void *Ax, void *Cx, const Batch &bt, cudaStream_t st);
+
+}  // namespace tn

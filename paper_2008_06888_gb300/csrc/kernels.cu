@@ -11,17 +11,11 @@
 #include <stdint.h>
 
 #include "kernels.h"
+#include "chain_dev.cuh"
 
 namespace tn {
 
 // ---------------------------------------------------------------- helpers
-
-template <typename T> struct Vec2;
-template <> struct Vec2<float> { typedef float2 t; };
-template <> struct Vec2<int32_t> { typedef int2 t; };
-template <typename T> struct Vec4;
-template <> struct Vec4<float> { typedef float4 t; };
-template <> struct Vec4<int32_t> { typedef int4 t; };
 
 template <typename T> struct Lim;
 template <> struct Lim<float> {
@@ -63,25 +57,6 @@ static inline int grid_for(int64_t n, int threads, int max_blocks = 152 * 32) {
   if (b < 1) b = 1;
   if (b > max_blocks) b = max_blocks;
   return (int)b;
-}
-
-// Pointer of instance blockIdx.y in a batch whose arena slices are ib bytes apart.
-template <typename P>
-__device__ __forceinline__ P *inst_ptr(P *p, int64_t ib) {
-  return reinterpret_cast<P *>(reinterpret_cast<char *>(const_cast<void *>(
-                                   static_cast<const void *>(p))) + blockIdx.y * ib);
-}
-
-// Asynchronous 4-byte global -> shared copies (cp.async) and their groups.
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_prev() {
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
 // ---------------------------------------------------------------- leaves
@@ -1479,27 +1454,6 @@ __global__ void __launch_bounds__(256, MINB) k_rchain(const ChainParams p,
 // given by the index bits of its legs.  Components are summed in order, so
 // the traceback rebuilds bit-identical tables.
 
-template <typename T>
-__device__ __forceinline__ void build_tables(const ChainParams &p, const T *X, T *sT) {
-  for (int k = 0; k < p.ntg; ++k) {
-    const TGate &t = p.tg[k];
-    const int sz = 8 << t.nf;
-    for (int i = threadIdx.x; i < sz; i += blockDim.x) {
-      T acc = T(0);
-      for (int c = 0; c < t.ncomp; ++c) {
-        const ChainGate &g = p.g[t.cg[c]];
-        const int64_t st[4] = {g.sBk, g.sBn, g.sBb[0], g.sBb[1]};
-        int64_t o = 0;
-#pragma unroll
-        for (int l = 0; l < 4; ++l)
-          if (t.cbit[c][l] >= 0) o += (int64_t)((i >> t.cbit[c][l]) & 1) * st[l];
-        acc = c == 0 ? X[g.offB + o] : acc + X[g.offB + o];
-      }
-      sT[t.toff + i] = acc;
-    }
-  }
-}
-
 // replace on register bit J with an optional extra register leg K: the
 // table slice for the thread's fixed digits is lo (K digit 0) / hi (1), each
 // (x=0,x'=0), (1,0), (0,1), (1,1).
@@ -1520,37 +1474,33 @@ __device__ __forceinline__ void tc_rep(T (&v)[1 << RB], const V &lo, const V &hi
   }
 }
 
-// diagonal table gate on register legs J (index bit 0) and K (bit 1)
-template <int RB, int J, int K, typename T, typename V>
-__device__ __forceinline__ void tc_diag(T (&v)[1 << RB], const V &lo) {
-  if constexpr (J < RB && K < RB) {
+// diagonal table gate on register legs J (index bit 0) and K (bit 1), -1 for
+// none; rare after folding, so one body with the legs read at run time
+template <int RB, typename T, typename V>
+__device__ __forceinline__ void tc_diag(T (&v)[1 << RB], int code, const V &lo) {
+  const int J = (code - 30) / 6 - 1, K = (code - 30) % 6 - 1;
+  const int mj = J >= 0 ? 1 << J : 0, mk = K >= 0 ? 1 << K : 0;
 #pragma unroll
-    for (int e = 0; e < (1 << RB); ++e) {
-      const int x0 = J >= 0 ? (e >> (J < 0 ? 0 : J)) & 1 : 0;
-      const int x1 = K >= 0 ? (e >> (K < 0 ? 0 : K)) & 1 : 0;
-      v[e] = v[e] + (x1 ? (x0 ? lo.w : lo.z) : (x0 ? lo.y : lo.x));
-    }
+  for (int e = 0; e < (1 << RB); ++e) {
+    const bool x0 = (e & mj) != 0, x1 = (e & mk) != 0;
+    v[e] = v[e] + (x1 ? (x0 ? lo.w : lo.z) : (x0 ? lo.y : lo.x));
   }
 }
 
 template <int RB, typename T, typename V>
 __device__ __forceinline__ void tc_apply(int code, T (&v)[1 << RB], const V &lo, const V &hi) {
 #define TC_R(J, K) case (J) * 6 + (K) + 1: tc_rep<RB, J, K>(v, lo, hi); break;
-#define TC_RJ(J) TC_R(J, -1) TC_R(J, 0) TC_R(J, 1) TC_R(J, 2) TC_R(J, 3) TC_R(J, 4)
-#define TC_D(J, K) case 30 + ((J) + 1) * 6 + (K) + 1: tc_diag<RB, J, K>(v, lo); break;
   switch (code) {
-    TC_RJ(0) TC_RJ(1) TC_RJ(2) TC_RJ(3) TC_RJ(4)
-    TC_D(-1, -1)
-    TC_D(0, -1) TC_D(1, -1) TC_D(2, -1) TC_D(3, -1) TC_D(4, -1)
-    TC_D(0, 1) TC_D(0, 2) TC_D(0, 3) TC_D(0, 4)
-    TC_D(1, 2) TC_D(1, 3) TC_D(1, 4)
-    TC_D(2, 3) TC_D(2, 4)
-    TC_D(3, 4)
-    default: break;
+    TC_R(0, -1) TC_R(0, 1) TC_R(0, 2) TC_R(0, 3) TC_R(0, 4)
+    TC_R(1, -1) TC_R(1, 0) TC_R(1, 2) TC_R(1, 3) TC_R(1, 4)
+    TC_R(2, -1) TC_R(2, 0) TC_R(2, 1) TC_R(2, 3) TC_R(2, 4)
+    TC_R(3, -1) TC_R(3, 0) TC_R(3, 1) TC_R(3, 2) TC_R(3, 4)
+    TC_R(4, -1) TC_R(4, 0) TC_R(4, 1) TC_R(4, 2) TC_R(4, 3)
+    default:
+      if (code >= 30) tc_diag<RB>(v, code, lo);
+      break;
   }
 #undef TC_R
-#undef TC_RJ
-#undef TC_D
 }
 
 // digits of the fixed legs -> table slice offset (8 values per slice)
@@ -1574,23 +1524,9 @@ __global__ void __launch_bounds__(256, MINB) k_tchain(const ChainParams p,
   A = inst_ptr(A, ib);
   C = inst_ptr(C, ib);
   __shared__ __align__(16) T sT[TN_CHAIN_MAX_G * TN_TG_TABLE];
-  __shared__ int4 sD[TN_CHAIN_MAX_G + 2];
+  __shared__ int4 sD[TN_CHAIN_MAX_G + 3];
   extern __shared__ __align__(16) char rstage[];
   T *stage = reinterpret_cast<T *>(rstage);
-  build_tables<T>(p, X, sT);
-  if (threadIdx.x < TN_CHAIN_MAX_G + 2) {
-    const int k = threadIdx.x;
-    int4 d = make_int4(-1, 0, 0, 0);
-    if (k < p.ntg) {
-      const TGate &t = p.tg[k];
-      const int zb = (int)sizeof(I) * 8 - 1;   // a digit that is always 0
-      int sh[TN_TG_MAXF];
-      for (int i = 0; i < TN_TG_MAXF; ++i) sh[i] = i < t.nf ? t.fsh[i] : zb;
-      d = make_int4(t.code, t.toff, sh[0] | (sh[1] << 8) | (sh[2] << 16), 0);
-    }
-    sD[k] = d;
-  }
-  __syncthreads();
   I sS[RB];
 #pragma unroll
   for (int j = 0; j < RB; ++j) sS[j] = (I)p.hi_off[1 << j];
@@ -1613,8 +1549,23 @@ __global__ void __launch_bounds__(256, MINB) k_tchain(const ChainParams p,
     cp_async_commit();
   };
   auto slot = [&](int it) { return stage + (it % STAGES) * (1 << RB) * nt; };
+  // the first inputs are in flight while the tables are built
 #pragma unroll
   for (int s2 = 0; s2 < STAGES - 1; ++s2) issue(tau + s2 * step, slot(s2));
+  build_tables<T>(p, X, sT);
+  if (threadIdx.x < TN_CHAIN_MAX_G + 3) {
+    const int k = threadIdx.x;
+    int4 d = make_int4(-1, 0, 0, 0);
+    if (k < p.ntg) {
+      const TGate &t = p.tg[k];
+      const int zb = (int)sizeof(I) * 8 - 1;   // a digit that is always 0
+      int sh[TN_TG_MAXF];
+      for (int i = 0; i < TN_TG_MAXF; ++i) sh[i] = i < t.nf ? t.fsh[i] : zb;
+      d = make_int4(t.code, t.toff, sh[0] | (sh[1] << 8) | (sh[2] << 16), 0);
+    }
+    sD[k] = d;
+  }
+  __syncthreads();
   const int ntg = p.ntg;
   for (int it = 0; tau < p.outer; tau += step, ++it) {
     T *cur = slot(it);
@@ -1627,19 +1578,25 @@ __global__ void __launch_bounds__(256, MINB) k_tchain(const ChainParams p,
     T v[1 << RB];
 #pragma unroll
     for (int e = 0; e < (1 << RB); ++e) v[e] = cur[e * nt + tid];
-    int4 d0 = sD[0], d1 = sD[1];
-    int a0 = tc_slice<I>(d0, bi);
-    V lo = *reinterpret_cast<const V *>(sT + a0), hi = *reinterpret_cast<const V *>(sT + a0 + 4);
-    for (int gi = 0; gi < ntg; ++gi) {
-      const int4 d2 = sD[gi + 2];
-      const int a1 = tc_slice<I>(d1, bi);
-      const V lo1 = *reinterpret_cast<const V *>(sT + a1);
-      const V hi1 = *reinterpret_cast<const V *>(sT + a1 + 4);
-      tc_apply<RB>(d0.x, v, lo, hi);
-      d0 = d1;
-      d1 = d2;
-      lo = lo1;
-      hi = hi1;
+    // two gates per trip: gate gi runs on (loA, hiA) while gate gi+1's slice
+    // loads into (loB, hiB), and the other way round
+    int4 dA = sD[0], dB = sD[1];
+    int a = tc_slice<I>(dA, bi);
+    V loA = *reinterpret_cast<const V *>(sT + a), hiA = *reinterpret_cast<const V *>(sT + a + 4);
+    for (int gi = 0; gi < ntg; gi += 2) {
+      a = tc_slice<I>(dB, bi);
+      const V loB = *reinterpret_cast<const V *>(sT + a);
+      const V hiB = *reinterpret_cast<const V *>(sT + a + 4);
+      const int4 dA2 = sD[gi + 2];
+      tc_apply<RB>(dA.x, v, loA, hiA);
+      if (gi + 1 >= ntg) break;
+      a = tc_slice<I>(dA2, bi);
+      loA = *reinterpret_cast<const V *>(sT + a);
+      hiA = *reinterpret_cast<const V *>(sT + a + 4);
+      const int4 dB2 = sD[gi + 3];
+      tc_apply<RB>(dB.x, v, loB, hiB);
+      dA = dA2;
+      dB = dB2;
     }
     T *dst = C + bi;
     I o[1 << RB];

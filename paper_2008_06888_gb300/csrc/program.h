@@ -46,6 +46,7 @@ struct Program {
   std::vector<GemmParams> gemms;
   std::vector<PermParams> perms;
   std::vector<ChainParams> chains;                  // fused gate chains
+  std::vector<const void *> chain_jit;              // their compiled kernels (nullptr: interpreted)
   std::vector<std::vector<Loc>> chain_blocs;        // their gate operands
   std::vector<ChainTrace> chain_traces;             // traceback records of chains
   std::vector<Loc> ctrace_in;

@@ -1,7 +1,17 @@
 // tn_internal.h -- structures shared by the host planner/executor and the
 // CUDA kernels of libtn.so.  Not part of the public ABI (include/tn.h).
 #pragma once
+#ifdef __CUDACC_RTC__
+// runtime-compiled chain kernels: no C library headers
+typedef signed char int8_t;
+typedef short int16_t;
+typedef int int32_t;
+typedef long long int64_t;
+typedef unsigned int uint32_t;
+typedef unsigned long long uint64_t;
+#else
 #include <stdint.h>
+#endif
 
 #define TN_MAX_SEG 10        // outer-index segments of a gate contraction
 #define TN_GATE_MAX_K 64     // contracted states of a gate contraction

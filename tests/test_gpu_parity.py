@@ -504,3 +504,21 @@ def test_chimera6_planted_counts():
     st, E2 = gpu_state(sg)
     sig = 1 - 2 * st.astype(np.int64)
     assert np.all(sig == tau) or np.all(sig == -tau)
+
+
+@pytest.mark.parametrize("coupling", ["pm1", "gauss"])
+def test_compiled_chain_kernels_match_interpreter(coupling, monkeypatch):
+    """Chains of 2^20+ elements run as kernels compiled for their gate
+    sequence; they do the interpreter's additions and maxima in the same
+    order, so E_min and sigma* agree bit for bit."""
+    inst = I.square_lattice(22, coupling=coupling,
+                            field_sigma=0.1 if coupling == "gauss" else None, seed=31)
+    a = P.SpinGlass(inst, order="greedy", seed=4)
+    sa, Ea = a.config()
+    Ea2 = a.energy()
+    monkeypatch.setenv("TN_NO_JIT", "1")
+    b = P.SpinGlass(inst, order="greedy", seed=4)
+    sb, Eb = b.config()
+    Eb2 = b.energy()
+    assert Ea == Eb and Ea2 == Eb2 and np.array_equal(sa, sb)
+    check_energy(inst, O.energy(inst, P.SpinGlass.state_indices(sa, 2)), Ea)

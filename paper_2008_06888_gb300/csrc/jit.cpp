@@ -129,6 +129,42 @@ bool worth(const ChainParams &p) {
 
 }  // namespace
 
+bool tile_map(const ChainParams &p, TileMap *tm) {
+  if (p.mode != 1 || p.t != kRB || p.outer % 32) return false;
+  int regpos[kRB];
+  for (int b = 0; b < kRB; ++b) {
+    int q = 0;
+    while ((int64_t(1) << q) < p.hi_off[1 << b]) ++q;
+    regpos[b] = q;
+  }
+  auto reg_of = [&](int pos) {
+    for (int b = 0; b < kRB; ++b)
+      if (regpos[b] == pos) return b;
+    return -1;
+  };
+  *tm = TileMap{};
+  int m = 0;
+  for (int q = 0; q < 5; ++q) m += reg_of(q) < 0;
+  int k = 0;
+  for (int q = 0; q < 5; ++q)
+    if (reg_of(q) >= 0) tm->gbit[reg_of(q)] = 1 << (m + k++);
+  int rank = 0;
+  for (int q = 0; (int)tm->tpos.size() < 5 + kRB && q < 62; ++q) {
+    const int b = reg_of(q);
+    if (b >= 0) {
+      tm->tpos.push_back(q);
+      tm->cbit.push_back((1 << (5 + b)) ^ tm->gbit[b]);
+    } else if (rank++ < 5) {
+      tm->tpos.push_back(q);
+      tm->cbit.push_back(1 << (rank - 1));
+    }
+  }
+  if ((int)tm->tpos.size() != 5 + kRB) return false;
+  for (int j = 0; j < 5; ++j)
+    if (tm->tpos[j] != j) return false;   // positions 0..4 are always tile bits
+  return true;
+}
+
 std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &name) {
   const bool f32 = dt == DT_F32;
   const char *T = f32 ? "float" : "int";
@@ -157,23 +193,71 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
       << "    u >>= " << p.seg_sh[sg] << ";\n";
   o << "    return b;\n  };\n";
   const int E = 1 << kRB, S = E * kThreads;
-  o << "  auto issue = [&](long long t, int s) {\n"
-    << "    if (t < " << p.outer << "LL) {\n"
-    << "      const T *src = A + base(t);\n"
-    << "      T *dst = stage + s * " << S << " + tid;\n";
-  for (int e = 0; e < E; ++e)
-    o << "      cp_async4(dst + " << e * kThreads << ", src + " << p.hi_off[e] << ");\n";
-  o << "    }\n    cp_async_commit();\n  };\n"
-    << "  issue(tau, 0);\n"
+  // Tile of a warp: its 32 outer indices x the 32 register elements.  Its 10
+  // index bits (word w, memory order) always include memory positions 0..4,
+  // so word w = lane + 32 i lies at tile base + lane + Ci: lane copies words
+  // lane + 32 i and every copy instruction of the warp reads 128 contiguous
+  // bytes.  In the warp's shared-memory tile, element (lane rank bits tau,
+  // register index e) sits at (e << 5) | (tau ^ g(e)); g swizzles the
+  // register bits among memory positions 0..4 so that the copies and the
+  // reads by owner are free of bank conflicts.  Word w's slot D(w) is linear
+  // (XOR) in w's bits.  Only the warp itself touches its tile (__syncwarp).
+  TileMap tm;
+  const bool coalesce = std::getenv("TN_JIT_SCATTER") == nullptr && tile_map(p, &tm);
+  const int *gbit = tm.gbit;
+  const std::vector<int> &cbit = tm.cbit;
+  const std::vector<int> &tpos = tm.tpos;
+  if (coalesce) {
+    o << "  const int lane = tid & 31;\n"
+      << "  T *const wstage = stage + (tid >> 5) * 1024;\n"
+      << "  const int Dt = 0";
+    for (int j = 0; j < 5; ++j) o << " ^ (-((lane >> " << j << ") & 1) & " << cbit[j] << ")";
+    o << ";\n";
+    o << "  auto issue = [&](long long t, int s) {\n"
+      << "    if (t < " << p.outer << "LL) {\n"
+      << "      const T *src = A + base(t - lane) + lane;\n"
+      << "      T *dst = wstage + s * " << S << ";\n";
+    for (int i = 0; i < E; ++i) {
+      int64_t Ci = 0;
+      int Di = 0;
+      for (int k2 = 0; k2 < kRB; ++k2)
+        if ((i >> k2) & 1) {
+          Ci += int64_t(1) << tpos[5 + k2];
+          Di ^= cbit[5 + k2];
+        }
+      o << "      cp_async4(dst + (Dt ^ " << Di << "), src + " << Ci << ");\n";
+    }
+    o << "    }\n    cp_async_commit();\n  };\n";
+  } else {
+    o << "  auto issue = [&](long long t, int s) {\n"
+      << "    if (t < " << p.outer << "LL) {\n"
+      << "      const T *src = A + base(t);\n"
+      << "      T *dst = stage + s * " << S << " + tid;\n";
+    for (int e = 0; e < E; ++e)
+      o << "      cp_async4(dst + " << e * kThreads << ", src + " << p.hi_off[e] << ");\n";
+    o << "    }\n    cp_async_commit();\n  };\n";
+  }
+  o << "  issue(tau, 0);\n"
     << "  build_tables<T>(p, X, sT);\n"
     << "  __syncthreads();\n"
     << "  for (int it = 0; tau < " << p.outer << "LL; tau += step, ++it) {\n"
     << "    const int cur = it & 1;\n"
     << "    issue(tau + step, cur ^ 1);\n"
-    << "    cp_async_wait_prev();\n"
-    << "    const I bi = base(tau);\n"
-    << "    const T *sv = stage + cur * " << S << " + tid;\n";
-  for (int e = 0; e < E; ++e) o << "    T v" << e << " = sv[" << e * kThreads << "];\n";
+    << "    cp_async_wait_prev();\n";
+  if (coalesce) o << "    __syncwarp();\n";   // words of the tile come from other lanes
+  o << "    const I bi = base(tau);\n"
+    << "    const T *sv = " << (coalesce ? "wstage" : "stage") << " + cur * " << S << ";\n";
+  for (int e = 0; e < E; ++e) {
+    if (coalesce) {
+      int g = 0;
+      for (int b = 0; b < kRB; ++b)
+        if ((e >> b) & 1) g ^= gbit[b];
+      o << "    T v" << e << " = sv[" << (e << 5) << " + (lane ^ " << g << ")];\n";
+    } else {
+      o << "    T v" << e << " = sv[" << e * kThreads << " + tid];\n";
+    }
+  }
+  if (coalesce) o << "    __syncwarp();\n";   // the slot is refilled by the next issue
   for (int k = 0; k < p.ntg; ++k) {
     const TGate &t = p.tg[k];
     o << "    {  // table gate " << k << (t.kind == 0 ? ": replace" : ": diagonal") << "\n";

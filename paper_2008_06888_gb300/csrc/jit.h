@@ -23,6 +23,18 @@ namespace tn {
 bool jit_chains(const std::vector<ChainParams> &chains, Dtype dt, std::vector<const void *> *out,
                 std::string *err);
 
+// Coalesced tile copies of a compiled chain.  A warp's tile is its 32 outer
+// indices x 32 register elements; tile word bit j sits at memory position
+// tpos[j] (tpos[j] == j for j < 5).  Word w goes to slot XOR_j{cbit[j] : bit
+// j of w set} of the warp's tile; element (lane rank bits tau, register
+// index e) is at slot (e << 5) | (tau ^ XOR_b{gbit[b] : bit b of e}).
+struct TileMap {
+  int gbit[5] = {0, 0, 0, 0, 0};
+  std::vector<int> cbit;
+  std::vector<int> tpos;
+};
+bool tile_map(const ChainParams &p, TileMap *tm);
+
 // Source of the specialised kernel `name` for one chain (exposed for tests).
 std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &name);
 

@@ -288,8 +288,33 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     }
     o << "    }\n";
   }
-  o << "    T *dst = C + bi;\n";
-  for (int e = 0; e < E; ++e) o << "    dst[" << p.hi_off[e] << "] = v" << e << ";\n";
+  if (coalesce && std::getenv("TN_JIT_SCATTER_STORES") == nullptr) {
+    // outputs go through the warp's tile (its slot was read above) and leave
+    // as whole 128-byte lines: lane stores tile words lane + 32 i
+    o << "    T *sw = wstage + cur * " << S << ";\n";
+    for (int e = 0; e < E; ++e) {
+      int g = 0;
+      for (int b = 0; b < kRB; ++b)
+        if ((e >> b) & 1) g ^= gbit[b];
+      o << "    sw[" << (e << 5) << " + (lane ^ " << g << ")] = v" << e << ";\n";
+    }
+    o << "    __syncwarp();\n"
+      << "    T *dst = C + base(tau - lane) + lane;\n";
+    for (int i = 0; i < E; ++i) {
+      int64_t Ci = 0;
+      int Di = 0;
+      for (int k2 = 0; k2 < kRB; ++k2)
+        if ((i >> k2) & 1) {
+          Ci += int64_t(1) << tpos[5 + k2];
+          Di ^= cbit[5 + k2];
+        }
+      o << "    dst[" << Ci << "] = sw[Dt ^ " << Di << "];\n";
+    }
+    o << "    __syncwarp();\n";   // the tile is refilled by a later issue
+  } else {
+    o << "    T *dst = C + bi;\n";
+    for (int e = 0; e < E; ++e) o << "    dst[" << p.hi_off[e] << "] = v" << e << ";\n";
+  }
   o << "  }\n  asm volatile(\"cp.async.wait_all;\\n\" ::: \"memory\");\n}\n";
   return o.str();
 }

@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=48)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--L", type=int, default=24, help="lattice side (profiling runs only)")
     ap.add_argument("--mode", default="config", choices=["config", "energy"],
@@ -134,19 +134,27 @@ class Clocks:
                 "samples": len(sm)}
 
 
+CHAIN_SOURCES = ("kernels.cu", "chain_dev.cuh", "jit.cpp")   # define every chain kernel
+
+
+def sources_hash():
+    h = hashlib.sha256()
+    for f in CHAIN_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2008_06888_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profiles(kind):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source still matches."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel sources still match."""
     path = os.path.join(ROOT, "profiles", f"{kind}_kernel_square24.md")
-    src = os.path.join(ROOT, "paper_2008_06888_gb300", "csrc", "kernels.cu")
-    if not (os.path.exists(path) and os.path.exists(src)):
+    if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernels.cu sha256[:16]") != h:
+    if vals.get("chain sources sha256[:16]") != sources_hash():
         return None
     try:
         return float(vals["dram bytes per launch"])

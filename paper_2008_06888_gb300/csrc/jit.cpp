@@ -3,7 +3,7 @@
 // The interpreting kernel (k_tchain) reads each table gate's descriptor and
 // dispatches on its register legs for every outer index.  Here every large
 // chain gets its own kernel: the source below spells out the chain's gates
-// on 32 named registers, with the outer-index decoding and the register-leg
+// on 2^RB named registers, with the outer-index decoding and the register-leg
 // offsets as constants.  Tables are built by the same device function as in
 // the interpreter and every gate does the same additions and maxima in the
 // same order, so the results are bit-identical to the interpreter's (and the
@@ -31,8 +31,10 @@ namespace tn {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kRB = 5;
+// threads per block and resident blocks per SM of a chain with RB register legs
+int threads_for(int RB) { return RB >= 6 ? 128 : 256; }
+int blocks_per_sm(int RB) { return RB >= 6 ? 3 : 2; }
+size_t smem_for(int RB) { return (size_t)2 * (32 << RB) * (threads_for(RB) / 32) * 4; }
 
 uint64_t fnv1a(const std::string &s, uint64_t h = 1469598103934665603ull) {
   for (unsigned char c : s) {
@@ -124,21 +126,23 @@ bool worth(const ChainParams &p) {
     const char *s = std::getenv("TN_JIT_MIN_ELEMENTS");
     return s ? std::atoll(s) : (1ll << 20);
   }();
-  return p.mode == 1 && p.P == 0 && p.t == kRB && p.ntg > 0 && p.outer * 32 >= min_el;
+  return p.mode == 1 && p.P == 0 && (p.t == 5 || p.t == 6) && p.ntg > 0 &&
+         p.outer * p.tile >= min_el;
 }
 
 }  // namespace
 
 bool tile_map(const ChainParams &p, TileMap *tm) {
-  if (p.mode != 1 || p.t != kRB || p.outer % 32) return false;
-  int regpos[kRB];
-  for (int b = 0; b < kRB; ++b) {
+  const int RB = p.t;
+  if (p.mode != 1 || RB < 5 || RB > 6 || p.outer % 32) return false;
+  int regpos[6];
+  for (int b = 0; b < RB; ++b) {
     int q = 0;
     while ((int64_t(1) << q) < p.hi_off[1 << b]) ++q;
     regpos[b] = q;
   }
   auto reg_of = [&](int pos) {
-    for (int b = 0; b < kRB; ++b)
+    for (int b = 0; b < RB; ++b)
       if (regpos[b] == pos) return b;
     return -1;
   };
@@ -149,7 +153,7 @@ bool tile_map(const ChainParams &p, TileMap *tm) {
   for (int q = 0; q < 5; ++q)
     if (reg_of(q) >= 0) tm->gbit[reg_of(q)] = 1 << (m + k++);
   int rank = 0;
-  for (int q = 0; (int)tm->tpos.size() < 5 + kRB && q < 62; ++q) {
+  for (int q = 0; (int)tm->tpos.size() < 5 + RB && q < 62; ++q) {
     const int b = reg_of(q);
     if (b >= 0) {
       tm->tpos.push_back(q);
@@ -159,7 +163,7 @@ bool tile_map(const ChainParams &p, TileMap *tm) {
       tm->cbit.push_back(1 << (rank - 1));
     }
   }
-  if ((int)tm->tpos.size() != 5 + kRB) return false;
+  if ((int)tm->tpos.size() != 5 + RB) return false;
   for (int j = 0; j < 5; ++j)
     if (tm->tpos[j] != j) return false;   // positions 0..4 are always tile bits
   return true;
@@ -169,10 +173,11 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
   const bool f32 = dt == DT_F32;
   const char *T = f32 ? "float" : "int";
   const char *MX = f32 ? "fmaxf" : "max";
-  const bool i32 = p.outer * 32 < (int64_t(1) << 31);
+  const int RB = p.t, NT = threads_for(RB);
+  const bool i32 = p.outer * p.tile < (int64_t(1) << 31);
   std::ostringstream o;
   o << "#include \"chain_dev.cuh\"\n"
-    << "extern \"C\" __global__ void __launch_bounds__(" << kThreads << ", 2)\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << NT << ", " << blocks_per_sm(RB) << ")\n"
     << name << "(const ChainParams p, const " << T << " *__restrict__ X, const " << T
     << " *__restrict__ A, " << T << " *__restrict__ C, long long ib) {\n"
     << "  using namespace tn;\n"
@@ -184,22 +189,22 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     << "  extern __shared__ __align__(16) char rstage[];\n"
     << "  T *stage = reinterpret_cast<T *>(rstage);\n"
     << "  const int tid = threadIdx.x;\n"
-    << "  const long long step = (long long)gridDim.x * " << kThreads << ";\n"
-    << "  long long tau = blockIdx.x * " << kThreads << "LL + tid;\n";
+    << "  const long long step = (long long)gridDim.x * " << NT << ";\n"
+    << "  long long tau = blockIdx.x * " << NT << "LL + tid;\n";
   // outer index -> element offset (segments slowest first)
   o << "  auto base = [](long long t) -> I {\n    I b = 0, u = (I)t;\n";
   for (int sg = p.nseg - 1; sg >= 0; --sg)
     o << "    b += (u & (I)" << (p.seg_size[sg] - 1) << ") << " << p.seg_ssh[sg] << ";\n"
       << "    u >>= " << p.seg_sh[sg] << ";\n";
   o << "    return b;\n  };\n";
-  const int E = 1 << kRB, S = E * kThreads;
-  // Tile of a warp: its 32 outer indices x the 32 register elements.  Its 10
-  // index bits (word w, memory order) always include memory positions 0..4,
-  // so word w = lane + 32 i lies at tile base + lane + Ci: lane copies words
-  // lane + 32 i and every copy instruction of the warp reads 128 contiguous
-  // bytes.  In the warp's shared-memory tile, element (lane rank bits tau,
-  // register index e) sits at (e << 5) | (tau ^ g(e)); g swizzles the
-  // register bits among memory positions 0..4 so that the copies and the
+  const int E = 1 << RB, S = E * NT, W = 32 * E;   // states, slot and warp tile (values)
+  // Tile of a warp: its 32 outer indices x the 2^RB register states.  Its
+  // 5 + RB index bits (word w, memory order) always include memory positions
+  // 0..4, so word w = lane + 32 i lies at tile base + lane + Ci: lane copies
+  // words lane + 32 i and every copy instruction of the warp reads 128
+  // contiguous bytes.  In the warp's shared-memory tile, element (lane rank
+  // bits tau, register index e) sits at (e << 5) | (tau ^ g(e)); g swizzles
+  // the register bits among memory positions 0..4 so that the copies and the
   // reads by owner are free of bank conflicts.  Word w's slot D(w) is linear
   // (XOR) in w's bits.  Only the warp itself touches its tile (__syncwarp).
   TileMap tm;
@@ -209,7 +214,7 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
   const std::vector<int> &tpos = tm.tpos;
   if (coalesce) {
     o << "  const int lane = tid & 31;\n"
-      << "  T *const wstage = stage + (tid >> 5) * 1024;\n"
+      << "  T *const wstage = stage + (tid >> 5) * " << W << ";\n"
       << "  const int Dt = 0";
     for (int j = 0; j < 5; ++j) o << " ^ (-((lane >> " << j << ") & 1) & " << cbit[j] << ")";
     o << ";\n";
@@ -220,7 +225,7 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     for (int i = 0; i < E; ++i) {
       int64_t Ci = 0;
       int Di = 0;
-      for (int k2 = 0; k2 < kRB; ++k2)
+      for (int k2 = 0; k2 < RB; ++k2)
         if ((i >> k2) & 1) {
           Ci += int64_t(1) << tpos[5 + k2];
           Di ^= cbit[5 + k2];
@@ -234,7 +239,7 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
       << "      const T *src = A + base(t);\n"
       << "      T *dst = stage + s * " << S << " + tid;\n";
     for (int e = 0; e < E; ++e)
-      o << "      cp_async4(dst + " << e * kThreads << ", src + " << p.hi_off[e] << ");\n";
+      o << "      cp_async4(dst + " << e * NT << ", src + " << p.hi_off[e] << ");\n";
     o << "    }\n    cp_async_commit();\n  };\n";
   }
   o << "  issue(tau, 0);\n"
@@ -250,11 +255,11 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
   for (int e = 0; e < E; ++e) {
     if (coalesce) {
       int g = 0;
-      for (int b = 0; b < kRB; ++b)
+      for (int b = 0; b < RB; ++b)
         if ((e >> b) & 1) g ^= gbit[b];
       o << "    T v" << e << " = sv[" << (e << 5) << " + (lane ^ " << g << ")];\n";
     } else {
-      o << "    T v" << e << " = sv[" << e * kThreads << " + tid];\n";
+      o << "    T v" << e << " = sv[" << e * NT << " + tid];\n";
     }
   }
   if (coalesce) o << "    __syncwarp();\n";   // the slot is refilled by the next issue
@@ -294,7 +299,7 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     o << "    T *sw = wstage + cur * " << S << ";\n";
     for (int e = 0; e < E; ++e) {
       int g = 0;
-      for (int b = 0; b < kRB; ++b)
+      for (int b = 0; b < RB; ++b)
         if ((e >> b) & 1) g ^= gbit[b];
       o << "    sw[" << (e << 5) << " + (lane ^ " << g << ")] = v" << e << ";\n";
     }
@@ -303,7 +308,7 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     for (int i = 0; i < E; ++i) {
       int64_t Ci = 0;
       int Di = 0;
-      for (int k2 = 0; k2 < kRB; ++k2)
+      for (int k2 = 0; k2 < RB; ++k2)
         if ((i >> k2) & 1) {
           Ci += int64_t(1) << tpos[5 + k2];
           Di ^= cbit[5 + k2];
@@ -382,8 +387,8 @@ bool jit_chains(const std::vector<ChainParams> &chains, Dtype dt, std::vector<co
   work();
   for (auto &t : pool) t.join();
   std::lock_guard<std::mutex> lk(g_mu);
-  const size_t smem = 2 * 32 * kThreads * 4;
   for (Job &j : jobs) {
+    const size_t smem = smem_for(chains[j.idx].t);
     if (!j.ok) {
       *err = "chain kernel " + j.name + ": " + j.err;
       return false;
@@ -412,17 +417,17 @@ bool jit_chains(const std::vector<ChainParams> &chains, Dtype dt, std::vector<co
 cudaError_t launch_jit_chain(const void *kernel, const ChainParams &p, const char *arena,
                              const void *Ax, void *Cx, const Batch &bt, cudaStream_t st) {
   if (p.outer == 0) return cudaSuccess;
-  int64_t blocks = (p.outer + kThreads - 1) / kThreads;
-  const int64_t cap = std::max<int64_t>(1, 152 * 2 / bt.B);
+  const int NT = threads_for(p.t);
+  int64_t blocks = (p.outer + NT - 1) / NT;
+  const int64_t cap = std::max<int64_t>(1, 152 * blocks_per_sm(p.t) / bt.B);
   if (blocks > cap) blocks = cap;
-  const size_t smem = 2 * 32 * kThreads * 4;
   ChainParams pc = p;
   const void *X = arena;
   const void *A = Ax;
   void *C = Cx;
   long long ib = bt.ib;
   void *args[] = {&pc, &X, &A, &C, &ib};
-  return cudaLaunchKernel(kernel, dim3((unsigned)blocks, bt.B), dim3(kThreads), args, smem, st);
+  return cudaLaunchKernel(kernel, dim3((unsigned)blocks, bt.B), dim3(NT), args, smem_for(p.t), st);
 }
 
 }  // namespace tn

@@ -23,13 +23,14 @@ namespace tn {
 bool jit_chains(const std::vector<ChainParams> &chains, Dtype dt, std::vector<const void *> *out,
                 std::string *err);
 
-// Coalesced tile copies of a compiled chain.  A warp's tile is its 32 outer
-// indices x 32 register elements; tile word bit j sits at memory position
-// tpos[j] (tpos[j] == j for j < 5).  Word w goes to slot XOR_j{cbit[j] : bit
-// j of w set} of the warp's tile; element (lane rank bits tau, register
-// index e) is at slot (e << 5) | (tau ^ XOR_b{gbit[b] : bit b of e}).
+// Coalesced tile copies of a compiled chain with RB register legs (5 or 6).
+// A warp's tile is its 32 outer indices x 2^RB register states; tile word
+// bit j sits at memory position tpos[j] (tpos[j] == j for j < 5).  Word w goes
+// to slot XOR_j{cbit[j] : bit j of w set} of the warp's tile; element (lane
+// rank bits tau, register index e) is at slot
+// (e << 5) | (tau ^ XOR_b{gbit[b] : bit b of e}).
 struct TileMap {
-  int gbit[5] = {0, 0, 0, 0, 0};
+  int gbit[6] = {0, 0, 0, 0, 0, 0};
   std::vector<int> cbit;
   std::vector<int> tpos;
 };

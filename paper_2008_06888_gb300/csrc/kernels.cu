@@ -1478,7 +1478,7 @@ __device__ __forceinline__ void tc_rep(T (&v)[1 << RB], const V &lo, const V &hi
 // none; rare after folding, so one body with the legs read at run time
 template <int RB, typename T, typename V>
 __device__ __forceinline__ void tc_diag(T (&v)[1 << RB], int code, const V &lo) {
-  const int J = (code - 30) / 6 - 1, K = (code - 30) % 6 - 1;
+  const int J = (code - 42) / 7 - 1, K = (code - 42) % 7 - 1;
   const int mj = J >= 0 ? 1 << J : 0, mk = K >= 0 ? 1 << K : 0;
 #pragma unroll
   for (int e = 0; e < (1 << RB); ++e) {
@@ -1487,17 +1487,20 @@ __device__ __forceinline__ void tc_diag(T (&v)[1 << RB], int code, const V &lo) 
   }
 }
 
+// dispatch: replace on J with extra leg K is code J * 7 + K + 1; diagonal
+// gates are 42 + (J + 1) * 7 + K + 1
 template <int RB, typename T, typename V>
 __device__ __forceinline__ void tc_apply(int code, T (&v)[1 << RB], const V &lo, const V &hi) {
-#define TC_R(J, K) case (J) * 6 + (K) + 1: tc_rep<RB, J, K>(v, lo, hi); break;
+#define TC_R(J, K) case (J) * 7 + (K) + 1: tc_rep<RB, J, K>(v, lo, hi); break;
   switch (code) {
-    TC_R(0, -1) TC_R(0, 1) TC_R(0, 2) TC_R(0, 3) TC_R(0, 4)
-    TC_R(1, -1) TC_R(1, 0) TC_R(1, 2) TC_R(1, 3) TC_R(1, 4)
-    TC_R(2, -1) TC_R(2, 0) TC_R(2, 1) TC_R(2, 3) TC_R(2, 4)
-    TC_R(3, -1) TC_R(3, 0) TC_R(3, 1) TC_R(3, 2) TC_R(3, 4)
-    TC_R(4, -1) TC_R(4, 0) TC_R(4, 1) TC_R(4, 2) TC_R(4, 3)
+    TC_R(0, -1) TC_R(0, 1) TC_R(0, 2) TC_R(0, 3) TC_R(0, 4) TC_R(0, 5)
+    TC_R(1, -1) TC_R(1, 0) TC_R(1, 2) TC_R(1, 3) TC_R(1, 4) TC_R(1, 5)
+    TC_R(2, -1) TC_R(2, 0) TC_R(2, 1) TC_R(2, 3) TC_R(2, 4) TC_R(2, 5)
+    TC_R(3, -1) TC_R(3, 0) TC_R(3, 1) TC_R(3, 2) TC_R(3, 4) TC_R(3, 5)
+    TC_R(4, -1) TC_R(4, 0) TC_R(4, 1) TC_R(4, 2) TC_R(4, 3) TC_R(4, 5)
+    TC_R(5, -1) TC_R(5, 0) TC_R(5, 1) TC_R(5, 2) TC_R(5, 3) TC_R(5, 4)
     default:
-      if (code >= 30) tc_diag<RB>(v, code, lo);
+      if (code >= 42) tc_diag<RB>(v, code, lo);
       break;
   }
 #undef TC_R
@@ -1514,8 +1517,8 @@ __device__ __forceinline__ int tc_slice(const int4 &d, I base) {
 
 // The register-chain pipeline of k_rchain with table gates: the descriptor of
 // gate gi+2 and the table slice of gate gi+1 are loaded while gate gi runs.
-template <typename T, int RB, typename I, int STAGES, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_tchain(const ChainParams p,
+template <typename T, int RB, typename I, int STAGES, int MINB, int NT = 256>
+__global__ void __launch_bounds__(NT, MINB) k_tchain(const ChainParams p,
                                                       const T *__restrict__ X,
                                                       const T *__restrict__ A,
                                                       T *__restrict__ C, int64_t ib) {
@@ -1975,9 +1978,40 @@ static cudaError_t launch_rchain_t(const ChainParams &p, const char *arena, cons
   return launch_rchain_i<T, RB, int64_t>(p, arena, Ax, Cx, blocks, smem, bt, st);
 }
 
+// six register legs (64 states per thread): blocks of 128 threads, three per SM
+template <typename T, typename I>
+static cudaError_t launch_tchain6(const ChainParams &p, const char *arena, const void *Ax, void *Cx,
+                                  const Batch &bt, cudaStream_t st) {
+  constexpr int NT = 128;
+  const size_t smem = (size_t)2 * 64 * NT * sizeof(T);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_tchain<T, 6, I, 2, 3, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int64_t blocks = (p.outer + NT - 1) / NT;
+  const int64_t cap = std::max<int64_t>(1, 152 * 3 / bt.B);
+  if (blocks > cap) blocks = cap;
+  k_tchain<T, 6, I, 2, 3, NT><<<dim3((unsigned)blocks, bt.B), NT, smem, st>>>(
+      p, reinterpret_cast<const T *>(arena), static_cast<const T *>(Ax), static_cast<T *>(Cx),
+      bt.ib);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, const void *Ax,
                           void *Cx, const Batch &bt, cudaStream_t st) {
   if (p.outer == 0) return cudaSuccess;
+  if (p.t == 6) {
+    if (p.ntg == 0) return cudaErrorInvalidValue;   // six legs need the folded tables
+    const bool i32 = p.outer * 64 < (int64_t(1) << 31);
+    if (dt == DT_F32)
+      return i32 ? launch_tchain6<float, int32_t>(p, arena, Ax, Cx, bt, st)
+                 : launch_tchain6<float, int64_t>(p, arena, Ax, Cx, bt, st);
+    return i32 ? launch_tchain6<int32_t, int32_t>(p, arena, Ax, Cx, bt, st)
+               : launch_tchain6<int32_t, int64_t>(p, arena, Ax, Cx, bt, st);
+  }
   if (p.t != 4 && p.t != 5) return cudaErrorInvalidValue;
   // resident blocks only (2 or 4 per SM); each thread then pipelines several indices
   static const int minb = std::getenv("TN_RCHAIN_MINB") ? std::atoi(std::getenv("TN_RCHAIN_MINB"))

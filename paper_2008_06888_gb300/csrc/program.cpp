@@ -168,7 +168,8 @@ static void fold_reg_chain(ChainParams &cp) {
   for (size_t k = 0; k < ord.size(); ++k) {
     TGate t = tg[ord[k]];
     for (int i = t.nf; i < TN_TG_MAXF; ++i) t.fsh[i] = 62;   // a digit that is always 0
-    t.code = t.kind == 0 ? (int16_t)(t.J * 6 + (t.K + 1)) : (int16_t)(30 + (t.J + 1) * 6 + (t.K + 1));
+    // dispatch code: replace J * 7 + K + 1 (< 42), diagonal 42 + (J + 1) * 7 + K + 1
+    t.code = t.kind == 0 ? (int16_t)(t.J * 7 + (t.K + 1)) : (int16_t)(42 + (t.J + 1) * 7 + (t.K + 1));
     t.toff = (int16_t)off;
     off += 8 << t.nf;
     cp.tg[k] = t;
@@ -600,7 +601,7 @@ struct Builder {
   bool fuse = true;
   bool regmode = false;         // q == 2 values: register chains (ChainParams mode 1)
   bool fold = true;             // fold diagonal gates into replace tables (values only)
-  int kRB = 5;                  // register legs of a register chain (4 or 5)
+  int kRB = 6;                  // register legs of a register chain (4 to 6; 3 when counting)
   int tmax = 11, wlow = 5;
   Macro open;
   bool has_open = false;
@@ -692,7 +693,7 @@ struct Builder {
     std::vector<int> S = reg_legs(m);
     cp.mode = 1;
     cp.q = 2;
-    cp.t = kRB;          // 5 (values) or 3 (values + residue planes)
+    cp.t = kRB;          // 6 (values), 3 (values + residue planes)
     cp.tile = 1 << kRB;
     for (int e = 0; e < cp.tile; ++e) {
       int64_t off = 0;
@@ -1001,7 +1002,10 @@ struct Builder {
     // register chains: q = 2 values, or q = 2 counts with 3 primes + witness
     regmode = q == 2 && (P == 0 || P == 4) && std::getenv("TN_TILE_CHAINS") == nullptr;
     fold = std::getenv("TN_NO_FOLD") == nullptr;
-    if (const char *rb = std::getenv("TN_REG_BITS")) kRB = std::atoi(rb) == 4 ? 4 : 5;
+    // values: 6 register legs (2^6 states per thread) with folded tables,
+    // 5 for the unfolded gate lists; counts: 3 legs (values + 4 residue planes)
+    kRB = fold ? 6 : 5;
+    if (const char *rb = std::getenv("TN_REG_BITS")) kRB = std::max(4, std::min(fold ? 6 : 5, std::atoi(rb)));
     if (P > 0) kRB = 3;
     if (q == 3) { tmax = 7; wlow = 4; }
     emit_leaves();

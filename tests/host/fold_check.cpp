@@ -44,15 +44,16 @@ static int check_chain(const ChainParams &p, std::mt19937_64 &rng, int *ntg_out)
   for (int trial = 0; trial < 64; ++trial) {
     int64_t tau = (int64_t)(rng() % (uint64_t)p.outer);
     int64_t base = rc_base(p, tau);
-    double v[32], w[32];
-    for (int e = 0; e < 32; ++e) v[e] = w[e] = X(1000000007ll + base + p.hi_off[e]);
+    const int E = p.tile;   // 2^t register states
+    double v[64], w[64];
+    for (int e = 0; e < E; ++e) v[e] = w[e] = X(1000000007ll + base + p.hi_off[e]);
     for (int gi = 0; gi < p.ngates; ++gi) {
       const ChainGate &g = p.g[gi];
       auto dig = [&](int k, int e) { return g.lsb[k] >= 0 ? (e >> g.lsb[k]) & 1 : (int)((base >> g.lsbh[k]) & 1); };
       if (g.kind != 0) {
-        for (int e = 0; e < 32; ++e) { int x0 = dig(0, e), x1 = g.nb > 1 ? dig(1, e) : 0; v[e] += X(g.offB + x0 * g.sBb[0] + x1 * (g.nb > 1 ? g.sBb[1] : 0)); }
+        for (int e = 0; e < E; ++e) { int x0 = dig(0, e), x1 = g.nb > 1 ? dig(1, e) : 0; v[e] += X(g.offB + x0 * g.sBb[0] + x1 * (g.nb > 1 ? g.sBb[1] : 0)); }
       } else {
-        for (int e = 0; e < 32; ++e) {
+        for (int e = 0; e < E; ++e) {
           if (e & (1 << g.ls)) continue;
           int e1 = e | (1 << g.ls);
           int ww = g.nb > 0 ? dig(0, e) : 0;
@@ -69,9 +70,9 @@ static int check_chain(const ChainParams &p, std::mt19937_64 &rng, int *ntg_out)
       for (int i = 0; i < t.nf; ++i) f |= (int)((base >> t.fsh[i]) & 1) << i;
       const double *tab = &T[t.toff + f * 8];
       if (t.kind != 0) {
-        for (int e = 0; e < 32; ++e) { int x0 = t.J >= 0 ? (e >> t.J) & 1 : 0, x1 = t.K >= 0 ? (e >> t.K) & 1 : 0; w[e] += tab[x0 | x1 << 1]; }
+        for (int e = 0; e < E; ++e) { int x0 = t.J >= 0 ? (e >> t.J) & 1 : 0, x1 = t.K >= 0 ? (e >> t.K) & 1 : 0; w[e] += tab[x0 | x1 << 1]; }
       } else {
-        for (int e = 0; e < 32; ++e) {
+        for (int e = 0; e < E; ++e) {
           if (e & (1 << t.J)) continue;
           int e1 = e | (1 << t.J); int kk = t.K >= 0 ? (e >> t.K) & 1 : 0;
           double a = w[e], b = w[e1];
@@ -80,7 +81,7 @@ static int check_chain(const ChainParams &p, std::mt19937_64 &rng, int *ntg_out)
         }
       }
     }
-    for (int e = 0; e < 32; ++e) if (v[e] != w[e]) bad++;
+    for (int e = 0; e < E; ++e) if (v[e] != w[e]) bad++;
   }
   *ntg_out = p.ntg;
   return bad;

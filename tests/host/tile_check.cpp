@@ -1,7 +1,7 @@
 // tile_check.cpp -- host check of the coalesced tile copies of compiled
 // register chains (no GPU).  For every chain of several programs that has a
-// tile map, simulates the copies of warp tiles (lane copies tile words
-// lane + 32 i) and checks that every shared-memory slot is written once,
+// tile map (5 or 6 register legs), simulates the copies of warp tiles (lane
+// copies tile words lane + 32 i) and checks that every shared-memory slot is written once,
 // that the slot each thread reads for its element (tau, e) holds the word at
 // base(tau) + hi_off[e], and that no warp instruction (copy or read) has two
 // lanes on one bank.  Exit status 0 when all hold.
@@ -43,30 +43,31 @@ int main() {
       TileMap tm;
       if (!tile_map(p, &tm)) continue;
       chains++;
+      const int RB = p.t, E = 1 << RB;
       const int64_t ntiles = p.outer / 32;
       for (int trial = 0; trial < 8; ++trial) {
         const int64_t t0 = (int64_t)(rng() % (uint64_t)ntiles) * 32;
-        std::vector<int64_t> slot(1024, -1);
+        std::vector<int64_t> slot(32 * E, -1);
         int Dt[32];
         for (int lane = 0; lane < 32; ++lane) {
           Dt[lane] = 0;
           for (int j = 0; j < 5; ++j) if ((lane >> j) & 1) Dt[lane] ^= tm.cbit[j];
         }
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < E; ++i) {
           int64_t Ci = 0; int Di = 0;
-          for (int k = 0; k < 5; ++k) if ((i >> k) & 1) { Ci += int64_t(1) << tm.tpos[5 + k]; Di ^= tm.cbit[5 + k]; }
+          for (int k = 0; k < RB; ++k) if ((i >> k) & 1) { Ci += int64_t(1) << tm.tpos[5 + k]; Di ^= tm.cbit[5 + k]; }
           bool used[32] = {false};
           for (int lane = 0; lane < 32; ++lane) {
             const int d = Dt[lane] ^ Di;
-            if (d < 0 || d >= 1024 || slot[d] != -1) { bad++; continue; }
+            if (d < 0 || d >= 32 * E || slot[d] != -1) { bad++; continue; }
             slot[d] = rc_base(p, t0) + lane + Ci;
             if (used[d & 31]) conflicts++;
             used[d & 31] = true;
           }
         }
-        for (int e = 0; e < 32; ++e) {
+        for (int e = 0; e < E; ++e) {
           int g = 0;
-          for (int b = 0; b < 5; ++b) if ((e >> b) & 1) g ^= tm.gbit[b];
+          for (int b = 0; b < RB; ++b) if ((e >> b) & 1) g ^= tm.gbit[b];
           bool used[32] = {false};
           for (int lane = 0; lane < 32; ++lane) {
             const int d = (e << 5) | (lane ^ g);

@@ -226,6 +226,7 @@ def run_gemm(args):
     sm_max = pk.get("sm_max_mhz", 2070.0)
     # non-tensor FP32 peak, an FMA counted as 2 ops: 152 SMs x 128 lanes x 2 x clock
     peak_ops = 152 * 128 * 2 * sm_max * 1e6
+    issue_peak = 152 * 128 * sm_max * 1e6
     out = {}
     clocks = Clocks(0)
     clocks.start()
@@ -251,12 +252,20 @@ def run_gemm(args):
             ms = e0.elapsed_time(e1) / reps
             macs = bt * M * N * K
             ops = 2 * macs / (ms * 1e-3)
+            # ALU instructions one multiply-add needs: an add and half a three-input
+            # max (FP32) or an add and a two-input max (INT32, no three-input form)
+            ipm = 1.5 if dt == torch.float32 else 2.0
             out[f"{str(dt).split('.')[-1]}_{bt}x{M}x{N}x{K}"] = {
                 "ms": ms, "tropical_Top_s": ops / 1e12, "T_MAC_s": macs / (ms * 1e-3) / 1e12,
-                "frac_of_fp32_nontensor_peak": ops / peak_ops}
+                "frac_of_fp32_nontensor_peak": ops / peak_ops,
+                "alu_issue_frac": ipm * macs / (ms * 1e-3) / issue_peak}
     clk = clocks.stop()
     print(json.dumps({"gemm": out, "peak_ops_per_s": peak_ops,
                       "peak": "152 SMs x 128 FP32 lanes x 2 (FMA = 2 ops) x max SM clock",
+                      "issue_peak_lane_instr_per_s": issue_peak,
+                      "issue_peak": "152 SMs x 128 lanes x max SM clock (one ALU instruction "
+                                    "per lane per clock); alu_issue_frac counts the ALU "
+                                    "instructions the multiply-adds need",
                       "clocks": clk}), flush=True)
 
 

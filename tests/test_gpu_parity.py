@@ -360,7 +360,12 @@ def test_fused_chains_match_unfused_exactly(kind, monkeypatch):
     sg2 = P.SpinGlass(inst, order="greedy", seed=3)
     res_u = (sg2.energy(), tuple(sg2.config()[0]), sg2.count(3)[0] if counts else None)
     if kind.endswith("pm"):
-        assert res_f == res_u
+        # degenerate: the same E and count; each sigma* is a ground state, but the
+        # first-argument tie rule applied per chain gate or per multi-leg step may
+        # pick different ones
+        assert res_f[0] == res_u[0] and res_f[2] == res_u[2]
+        for st in (res_f[1], res_u[1]):
+            assert O.energy(inst, P.SpinGlass.state_indices(np.array(st), 2)) == res_f[0]
     else:
         # folded chain tables add the couplings in another order (Eq. 1 is
         # a sum); float32 energies agree to rounding, the state exactly

@@ -270,7 +270,7 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     if (t.nf == 0) f << "0";
     for (int i = 0; i < t.nf; ++i) {
       if (i) f << " | ";
-      f << "((int)((bi >> " << (int)t.fsh[i] << ") & 1) << " << i << ")";
+      f << "((int)((tau >> " << (int)t.fsh[i] << ") & 1) << " << i << ")";
     }
     o << "      const int f = " << f.str() << ";\n"
       << "      const V lo = *reinterpret_cast<const V *>(sT + " << t.toff << " + f * 8);\n";

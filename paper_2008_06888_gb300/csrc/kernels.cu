@@ -1506,13 +1506,25 @@ __device__ __forceinline__ void tc_apply(int code, T (&v)[1 << RB], const V &lo,
 #undef TC_R
 }
 
-// digits of the fixed legs -> table slice offset (8 values per slice)
-template <typename I>
-__device__ __forceinline__ int tc_slice(const int4 &d, I base) {
+// digits of the fixed legs (bits of the outer index tau) -> table slice offset
+// (8 values per slice)
+__device__ __forceinline__ int tc_slice(const int4 &d, int64_t tau) {
   const int s0 = d.z & 0xff, s1 = (d.z >> 8) & 0xff, s2 = (d.z >> 16) & 0xff;
-  const int f = (int)((base >> s0) & 1) | ((int)((base >> s1) & 1) << 1) |
-                ((int)((base >> s2) & 1) << 2);
+  const int f = (int)((tau >> s0) & 1) | ((int)((tau >> s1) & 1) << 1) |
+                ((int)((tau >> s2) & 1) << 2);
   return d.y + f * 8;
+}
+
+// element offset of outer index tau in a layout whose segment shifts are ssh
+template <typename I>
+__device__ __forceinline__ I rc_base_l(const ChainParams &p, int64_t tau, const int32_t *ssh) {
+  I base = 0;
+  I t = (I)tau;
+  for (int sg = p.nseg - 1; sg >= 0; --sg) {
+    base += (t & (I)(p.seg_size[sg] - 1)) << ssh[sg];
+    t >>= p.seg_sh[sg];
+  }
+  return base;
 }
 
 // The register-chain pipeline of k_rchain with table gates: the descriptor of
@@ -1530,15 +1542,18 @@ __global__ void __launch_bounds__(NT, MINB) k_tchain(const ChainParams p,
   __shared__ int4 sD[TN_CHAIN_MAX_G + 3];
   extern __shared__ __align__(16) char rstage[];
   T *stage = reinterpret_cast<T *>(rstage);
-  I sS[RB];
+  I sS[RB], sO[RB];   // register-leg strides in the input and in the output
 #pragma unroll
-  for (int j = 0; j < RB; ++j) sS[j] = (I)p.hi_off[1 << j];
+  for (int j = 0; j < RB; ++j) {
+    sS[j] = (I)p.hi_in[1 << j];
+    sO[j] = (I)p.hi_out[1 << j];
+  }
   const int nt = blockDim.x, tid = threadIdx.x;
   const int64_t step = (int64_t)gridDim.x * nt;
   int64_t tau = blockIdx.x * (int64_t)nt + tid;
   auto issue = [&](int64_t t, T *dst) {
     if (t < p.outer) {
-      const T *src = A + rc_base<I>(p, t);
+      const T *src = A + rc_base_l<I>(p, t, p.ssh_in);
       I o[1 << RB];
       o[0] = 0;
 #pragma unroll
@@ -1561,9 +1576,8 @@ __global__ void __launch_bounds__(NT, MINB) k_tchain(const ChainParams p,
     int4 d = make_int4(-1, 0, 0, 0);
     if (k < p.ntg) {
       const TGate &t = p.tg[k];
-      const int zb = (int)sizeof(I) * 8 - 1;   // a digit that is always 0
       int sh[TN_TG_MAXF];
-      for (int i = 0; i < TN_TG_MAXF; ++i) sh[i] = i < t.nf ? t.fsh[i] : zb;
+      for (int i = 0; i < TN_TG_MAXF; ++i) sh[i] = i < t.nf ? t.fsh[i] : 62;   // 0 bit
       d = make_int4(t.code, t.toff, sh[0] | (sh[1] << 8) | (sh[2] << 16), 0);
     }
     sD[k] = d;
@@ -1577,23 +1591,23 @@ __global__ void __launch_bounds__(NT, MINB) k_tchain(const ChainParams p,
       asm volatile("cp.async.wait_group 2;\n" ::: "memory");
     else
       cp_async_wait_prev();
-    const I bi = rc_base<I>(p, tau);
+    const I bi = rc_base_l<I>(p, tau, p.ssh_out);
     T v[1 << RB];
 #pragma unroll
     for (int e = 0; e < (1 << RB); ++e) v[e] = cur[e * nt + tid];
     // two gates per trip: gate gi runs on (loA, hiA) while gate gi+1's slice
     // loads into (loB, hiB), and the other way round
     int4 dA = sD[0], dB = sD[1];
-    int a = tc_slice<I>(dA, bi);
+    int a = tc_slice(dA, tau);
     V loA = *reinterpret_cast<const V *>(sT + a), hiA = *reinterpret_cast<const V *>(sT + a + 4);
     for (int gi = 0; gi < ntg; gi += 2) {
-      a = tc_slice<I>(dB, bi);
+      a = tc_slice(dB, tau);
       const V loB = *reinterpret_cast<const V *>(sT + a);
       const V hiB = *reinterpret_cast<const V *>(sT + a + 4);
       const int4 dA2 = sD[gi + 2];
       tc_apply<RB>(dA.x, v, loA, hiA);
       if (gi + 1 >= ntg) break;
-      a = tc_slice<I>(dA2, bi);
+      a = tc_slice(dA2, tau);
       loA = *reinterpret_cast<const V *>(sT + a);
       hiA = *reinterpret_cast<const V *>(sT + a + 4);
       const int4 dB2 = sD[gi + 3];
@@ -1607,7 +1621,7 @@ __global__ void __launch_bounds__(NT, MINB) k_tchain(const ChainParams p,
 #pragma unroll
     for (int e = 1; e < (1 << RB); ++e) {
       const int hb = 31 - __clz(e);
-      o[e] = o[e ^ (1 << hb)] + sS[hb];
+      o[e] = o[e ^ (1 << hb)] + sO[hb];
     }
 #pragma unroll
     for (int e = 0; e < (1 << RB); ++e) dst[o[e]] = v[e];
@@ -1788,20 +1802,24 @@ __device__ void trace_tchain(const ChainTrace &ct, const T *X, int8_t *state, in
   __syncthreads();
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) {
-    int64_t part = 0;
+    int64_t part = 0, tpart = 0;   // input offset and outer index tau of the outer spins
     for (int i = lane; i < ct.nout; i += 32) {
       int d = state[ct.out_spin[i]];
       if (d < 0 || d > 1) { *err = 1; d = 0; }
       part += (int64_t)d * ct.out_stride[i];
+      tpart += (int64_t)d << ct.out_rank[i];
     }
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    const int64_t base = part;
+    for (int o = 16; o > 0; o >>= 1) {
+      part += __shfl_xor_sync(0xffffffffu, part, o);
+      tpart += __shfl_xor_sync(0xffffffffu, tpart, o);
+    }
+    const int64_t base = part, tau = tpart;
     auto slice = [&](const TGate &t) {
       int f = 0;
-      for (int i = 0; i < t.nf; ++i) f |= (int)((base >> t.fsh[i]) & 1) << i;
+      for (int i = 0; i < t.nf; ++i) f |= (int)((tau >> t.fsh[i]) & 1) << i;
       return sT + t.toff + f * 8;
     };
-    for (int e = lane; e < E; e += 32) buf[e] = X[ct.offIn + base + p.hi_off[e]];
+    for (int e = lane; e < E; e += 32) buf[e] = X[ct.offIn + base + p.hi_in[e]];
     __syncwarp();
     for (int gi = 0; gi < p.ntg; ++gi) {
       const TGate &t = p.tg[gi];

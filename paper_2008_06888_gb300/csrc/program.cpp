@@ -68,7 +68,7 @@ static bool tg_add_diag(const ChainParams &cp, int d, TGate &t, int jbit) {
   for (int l = 0; l < g.nb; ++l) {
     int8_t bit;
     if (g.lsb[l] < 0) {
-      if (!tg_fixed_bit(u, g.lsbh[l], &bit)) return false;
+      if (!tg_fixed_bit(u, g.lrank[l], &bit)) return false;
     } else if (g.lsb[l] == u.J) {
       if (jbit < 0) return false;
       bit = (int8_t)jbit;
@@ -106,7 +106,7 @@ static void fold_reg_chain(ChainParams &cp) {
         t.K = (int8_t)g.lsb[0];
         t.cbit[0][2] = 2;
       } else {
-        tg_fixed_bit(t, g.lsbh[0], &t.cbit[0][2]);
+        tg_fixed_bit(t, g.lrank[0], &t.cbit[0][2]);
       }
     }
     t.ncomp = 1;
@@ -152,7 +152,7 @@ static void fold_reg_chain(ChainParams &cp) {
     t.cbit[0][0] = t.cbit[0][1] = t.cbit[0][2] = t.cbit[0][3] = -1;
     for (int l = 0; l < g.nb; ++l) {
       int8_t bit = -1;
-      if (g.lsb[l] < 0) tg_fixed_bit(t, g.lsbh[l], &bit);   // at most 2 of 3 slots
+      if (g.lsb[l] < 0) tg_fixed_bit(t, g.lrank[l], &bit);   // at most 2 of 3 slots
       else bit = g.lsb[l] == t.J ? 0 : 1;
       t.cbit[0][2 + l] = bit;
     }
@@ -167,7 +167,7 @@ static void fold_reg_chain(ChainParams &cp) {
   cp.ntg = (int)tg.size();
   for (size_t k = 0; k < ord.size(); ++k) {
     TGate t = tg[ord[k]];
-    for (int i = t.nf; i < TN_TG_MAXF; ++i) t.fsh[i] = 62;   // a digit that is always 0
+    for (int i = t.nf; i < TN_TG_MAXF; ++i) t.fsh[i] = 62;   // a tau bit that is always 0
     // dispatch code: replace J * 7 + K + 1 (< 42), diagonal 42 + (J + 1) * 7 + K + 1
     t.code = t.kind == 0 ? (int16_t)(t.J * 7 + (t.K + 1)) : (int16_t)(42 + (t.J + 1) * 7 + (t.K + 1));
     t.toff = (int16_t)off;
@@ -724,7 +724,13 @@ struct Builder {
       cp.seg_sh[i] = sh[i];
       cp.seg_ssh[i] = 0;
       while ((int64_t(1) << cp.seg_ssh[i]) < st[i]) cp.seg_ssh[i]++;
+      cp.ssh_in[i] = cp.ssh_out[i] = cp.seg_ssh[i];
     }
+    for (int e = 0; e < cp.tile; ++e) cp.hi_in[e] = cp.hi_out[e] = cp.hi_off[e];
+    // bit of each outer position in tau: outer positions, fastest first
+    std::vector<int> trank(R, -1);
+    for (int p = R - 1, r = 0; p >= 0; --p)
+      if (pos_of(S, p) < 0) trank[p] = r++;
     cp.ngates = (int)m.gates.size();
     blocs->clear();
     for (int i = 0; i < cp.ngates; ++i) {
@@ -736,6 +742,7 @@ struct Builder {
       for (int j = 0; j < c.nb; ++j) {
         c.lsb[j] = pos_of(S, g.bpos[j]);
         c.lsbh[j] = R - 1 - g.bpos[j];
+        c.lrank[j] = trank[g.bpos[j]];
         c.sBb[j] = g.sBb[j];
       }
       c.kspin = g.kspin;
@@ -937,6 +944,9 @@ struct Builder {
           if (pos_of(T, p) >= 0) continue;
           ct.out_spin[ct.nout] = ord[p];
           ct.out_stride[ct.nout] = ipow(q, R - 1 - p);
+          int rank = 0;   // bit of this outer leg in tau: outer legs faster than it
+          for (int p2 = p + 1; p2 < R; ++p2) rank += pos_of(T, p2) < 0;
+          ct.out_rank[ct.nout] = rank;
           ct.nout++;
         }
         for (int j = 0; j < (int)T.size(); ++j) ct.local_spin[j] = ord[T[j]];

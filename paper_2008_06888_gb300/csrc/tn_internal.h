@@ -115,6 +115,7 @@ struct ChainGate {
   int32_t kspin;     // contracted spin (replace), for the traceback
   int32_t lsh;       // log2(ls) when q == 2
   int32_t lsbh[2];   // log2(lsb) when q == 2
+  int32_t lrank[2];  // register chains: bit of a fixed leg in the outer index tau
   int32_t nBel;      // elements of B
   int32_t unitB;     // 1: every count of B is 1 (a leaf), ties only add counts
   int64_t offB;      // element offset of B's values in the arena
@@ -132,7 +133,8 @@ struct ChainGate {
 //   index bit 0: contracted digit x (replace) / register leg J (diagonal)
 //   index bit 1: new digit x'       (replace) / register leg K (diagonal)
 //   index bit 2: register leg K     (replace; 0 when K < 0)
-//   index bits 3..: digits of the fixed legs, (base >> fsh[i]) & 1
+//   index bits 3..: digits of the fixed legs, (tau >> fsh[i]) & 1 (tau: the
+//                   thread's outer index, its bits the outer legs, fastest first)
 // The table is the sum of its components: component c is original gate
 // cg[c]'s operand B, read at the offset sum over its legs l (contracted,
 // new, tile leg 0, tile leg 1) of digit(index bit cbit[c][l]) * stride(l).
@@ -143,7 +145,7 @@ struct TGate {
   int8_t kind;                  // 0 replace, 1 diagonal
   int8_t J, K;                  // register legs (-1: none)
   int8_t nf, ncomp;
-  int8_t fsh[TN_TG_MAXF];       // shifts of the fixed legs' digits in base
+  int8_t fsh[TN_TG_MAXF];       // fixed legs: their bits in the outer index tau
   int8_t cg[TN_TG_MAXC];        // original gate of each component
   int8_t cbit[TN_TG_MAXC][4];   // table bit of each of its legs (-1: absent)
   int16_t code;                 // kernel dispatch code of (kind, J, K)
@@ -175,6 +177,11 @@ struct ChainParams {
   int32_t ntg;             // folded table gates (mode 1, P == 0); 0: use g[]
   int32_t ttotal;          // values of all their tables
   TGate tg[TN_CHAIN_MAX_G];
+  // folded register chains: offsets of register state e in the input and in the
+  // output tensor, and each outer segment's shift in both (hi_off / seg_ssh
+  // describe the state between the gates)
+  int64_t hi_in[TN_CHAIN_MAX_HI], hi_out[TN_CHAIN_MAX_HI];
+  int32_t ssh_in[TN_MAX_SEG], ssh_out[TN_MAX_SEG];
 };
 
 // Traceback record of a chain: the tile of the chain input selected by the
@@ -186,6 +193,7 @@ struct ChainTrace {
   int32_t out_spin[TN_MAX_TRACE_LEGS];
   int64_t out_stride[TN_MAX_TRACE_LEGS];
   int32_t local_spin[TN_CHAIN_MAX_T];  // spin on each local leg after the chain (slowest first)
+  int32_t out_rank[TN_MAX_TRACE_LEGS]; // folded register chains: bit of each outer leg in tau
   ChainParams p;
 };
 

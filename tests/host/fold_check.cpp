@@ -67,7 +67,7 @@ static int check_chain(const ChainParams &p, std::mt19937_64 &rng, int *ntg_out)
     for (int k = 0; k < p.ntg; ++k) {
       const TGate &t = p.tg[k];
       int f = 0;
-      for (int i = 0; i < t.nf; ++i) f |= (int)((base >> t.fsh[i]) & 1) << i;
+      for (int i = 0; i < t.nf; ++i) f |= (int)((tau >> t.fsh[i]) & 1) << i;
       const double *tab = &T[t.toff + f * 8];
       if (t.kind != 0) {
         for (int e = 0; e < E; ++e) { int x0 = t.J >= 0 ? (e >> t.J) & 1 : 0, x1 = t.K >= 0 ? (e >> t.K) & 1 : 0; w[e] += tab[x0 | x1 << 1]; }

@@ -132,41 +132,63 @@ bool worth(const ChainParams &p) {
 
 }  // namespace
 
-bool tile_map(const ChainParams &p, TileMap *tm) {
+bool tile_map(const ChainParams &p, const int64_t *hi, TileMap *tm) {
   const int RB = p.t;
   if (p.mode != 1 || RB < 5 || RB > 6 || p.outer % 32) return false;
+  *tm = TileMap{};
   int regpos[6];
   for (int b = 0; b < RB; ++b) {
+    if (hi[1 << b] == 0) continue;   // not a leg of this layout
     int q = 0;
-    while ((int64_t(1) << q) < p.hi_off[1 << b]) ++q;
-    regpos[b] = q;
+    while ((int64_t(1) << q) < hi[1 << b]) ++q;
+    tm->rbit[tm->nreg] = b;
+    regpos[tm->nreg++] = q;
   }
   auto reg_of = [&](int pos) {
-    for (int b = 0; b < RB; ++b)
-      if (regpos[b] == pos) return b;
+    for (int k = 0; k < tm->nreg; ++k)
+      if (regpos[k] == pos) return k;
     return -1;
   };
-  *tm = TileMap{};
   int m = 0;
   for (int q = 0; q < 5; ++q) m += reg_of(q) < 0;
   int k = 0;
   for (int q = 0; q < 5; ++q)
     if (reg_of(q) >= 0) tm->gbit[reg_of(q)] = 1 << (m + k++);
   int rank = 0;
-  for (int q = 0; (int)tm->tpos.size() < 5 + RB && q < 62; ++q) {
-    const int b = reg_of(q);
-    if (b >= 0) {
+  for (int q = 0; (int)tm->tpos.size() < 5 + tm->nreg && q < 62; ++q) {
+    const int c = reg_of(q);
+    if (c >= 0) {
       tm->tpos.push_back(q);
-      tm->cbit.push_back((1 << (5 + b)) ^ tm->gbit[b]);
+      tm->cbit.push_back((1 << (5 + c)) ^ tm->gbit[c]);
     } else if (rank++ < 5) {
       tm->tpos.push_back(q);
       tm->cbit.push_back(1 << (rank - 1));
     }
   }
-  if ((int)tm->tpos.size() != 5 + RB) return false;
+  if ((int)tm->tpos.size() != 5 + tm->nreg) return false;
   for (int j = 0; j < 5; ++j)
     if (tm->tpos[j] != j) return false;   // positions 0..4 are always tile bits
   return true;
+}
+
+int tile_slot(const TileMap &tm, int lane, int e) {
+  int c = 0, g = 0;
+  for (int k = 0; k < tm.nreg; ++k)
+    if ((e >> tm.rbit[k]) & 1) {
+      c |= 1 << k;
+      g ^= tm.gbit[k];
+    }
+  return (c << 5) | (lane ^ g);
+}
+
+void tile_word(const TileMap &tm, int i, int *D, int64_t *off) {
+  *D = 0;
+  *off = 0;
+  for (int k = 0; k < tm.nreg; ++k)
+    if ((i >> k) & 1) {
+      *D ^= tm.cbit[5 + k];
+      *off += int64_t(1) << tm.tpos[5 + k];
+    }
 }
 
 std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &name) {
@@ -174,6 +196,12 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
   const char *T = f32 ? "float" : "int";
   const char *MX = f32 ? "fmaxf" : "max";
   const int RB = p.t, NT = threads_for(RB);
+  const int E = 1 << RB, S = E * NT, W = 32 * E;   // states, slot and warp tile (values)
+  TileMap tin, tout;
+  if (!tile_map(p, p.hi_in, &tin) || !tile_map(p, p.hi_out, &tout)) return "";
+  const bool con = p.ntg > 0 && p.tg[p.ntg - 1].kind == 2;   // final contraction
+  const int nmain = con ? p.ntg - 1 : p.ntg;
+  const int cmask = con ? 1 << p.tg[p.ntg - 1].J : 0;
   const bool i32 = p.outer * p.tile < (int64_t(1) << 31);
   std::ostringstream o;
   o << "#include \"chain_dev.cuh\"\n"
@@ -188,139 +216,120 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     << "  __shared__ __align__(16) T sT[" << std::max(8, (int)p.ttotal) << "];\n"
     << "  extern __shared__ __align__(16) char rstage[];\n"
     << "  T *stage = reinterpret_cast<T *>(rstage);\n"
-    << "  const int tid = threadIdx.x;\n"
+    << "  const int tid = threadIdx.x, lane = tid & 31;\n"
     << "  const long long step = (long long)gridDim.x * " << NT << ";\n"
     << "  long long tau = blockIdx.x * " << NT << "LL + tid;\n";
-  // outer index -> element offset (segments slowest first)
-  o << "  auto base = [](long long t) -> I {\n    I b = 0, u = (I)t;\n";
-  for (int sg = p.nseg - 1; sg >= 0; --sg)
-    o << "    b += (u & (I)" << (p.seg_size[sg] - 1) << ") << " << p.seg_ssh[sg] << ";\n"
-      << "    u >>= " << p.seg_sh[sg] << ";\n";
-  o << "    return b;\n  };\n";
-  const int E = 1 << RB, S = E * NT, W = 32 * E;   // states, slot and warp tile (values)
-  // Tile of a warp: its 32 outer indices x the 2^RB register states.  Its
-  // 5 + RB index bits (word w, memory order) always include memory positions
-  // 0..4, so word w = lane + 32 i lies at tile base + lane + Ci: lane copies
-  // words lane + 32 i and every copy instruction of the warp reads 128
-  // contiguous bytes.  In the warp's shared-memory tile, element (lane rank
-  // bits tau, register index e) sits at (e << 5) | (tau ^ g(e)); g swizzles
-  // the register bits among memory positions 0..4 so that the copies and the
-  // reads by owner are free of bank conflicts.  Word w's slot D(w) is linear
-  // (XOR) in w's bits.  Only the warp itself touches its tile (__syncwarp).
-  TileMap tm;
-  const bool coalesce = std::getenv("TN_JIT_SCATTER") == nullptr && tile_map(p, &tm);
-  const int *gbit = tm.gbit;
-  const std::vector<int> &cbit = tm.cbit;
-  const std::vector<int> &tpos = tm.tpos;
-  if (coalesce) {
-    o << "  const int lane = tid & 31;\n"
-      << "  T *const wstage = stage + (tid >> 5) * " << W << ";\n"
-      << "  const int Dt = 0";
-    for (int j = 0; j < 5; ++j) o << " ^ (-((lane >> " << j << ") & 1) & " << cbit[j] << ")";
-    o << ";\n";
-    o << "  auto issue = [&](long long t, int s) {\n"
-      << "    if (t < " << p.outer << "LL) {\n"
-      << "      const T *src = A + base(t - lane) + lane;\n"
-      << "      T *dst = wstage + s * " << S << ";\n";
-    for (int i = 0; i < E; ++i) {
-      int64_t Ci = 0;
-      int Di = 0;
-      for (int k2 = 0; k2 < RB; ++k2)
-        if ((i >> k2) & 1) {
-          Ci += int64_t(1) << tpos[5 + k2];
-          Di ^= cbit[5 + k2];
-        }
-      o << "      cp_async4(dst + (Dt ^ " << Di << "), src + " << Ci << ");\n";
-    }
-    o << "    }\n    cp_async_commit();\n  };\n";
-  } else {
-    o << "  auto issue = [&](long long t, int s) {\n"
-      << "    if (t < " << p.outer << "LL) {\n"
-      << "      const T *src = A + base(t);\n"
-      << "      T *dst = stage + s * " << S << " + tid;\n";
-    for (int e = 0; e < E; ++e)
-      o << "      cp_async4(dst + " << e * NT << ", src + " << p.hi_off[e] << ");\n";
-    o << "    }\n    cp_async_commit();\n  };\n";
+  // outer index -> element offset in the input and in the output (segments
+  // slowest first)
+  for (int side = 0; side < 2; ++side) {
+    const int32_t *ssh = side == 0 ? p.ssh_in : p.ssh_out;
+    o << "  auto base_" << (side == 0 ? "in" : "out") << " = [](long long t) -> I {\n"
+      << "    I b = 0, u = (I)t;\n";
+    for (int sg = p.nseg - 1; sg >= 0; --sg)
+      o << "    b += (u & (I)" << (p.seg_size[sg] - 1) << ") << " << ssh[sg] << ";\n"
+        << "    u >>= " << p.seg_sh[sg] << ";\n";
+    o << "    return b;\n  };\n";
   }
-  o << "  issue(tau, 0);\n"
+  // Tile of a warp: its 32 outer indices x the register states of a layout.
+  // Its index bits (word w, memory order) always include memory positions
+  // 0..4, so word w = lane + 32 i lies at tile base + lane + off_i: lane
+  // copies words lane + 32 i and every copy of the warp moves 128 contiguous
+  // bytes.  In the warp's shared-memory tile, register state e of the thread
+  // of lane sits at a slot swizzled so that the copies and the owner's reads
+  // and writes are free of bank conflicts (TileMap).  Only the warp itself
+  // touches its tile (__syncwarp).
+  auto lane_D = [&](const TileMap &tm) {
+    std::ostringstream d;
+    d << "0";
+    for (int j = 0; j < 5; ++j) d << " ^ (-((lane >> " << j << ") & 1) & " << tm.cbit[j] << ")";
+    return d.str();
+  };
+  o << "  T *const wstage = stage + (tid >> 5) * " << W << ";\n"
+    << "  const int Din = " << lane_D(tin) << ";\n"
+    << "  const int Dout = " << lane_D(tout) << ";\n"
+    << "  auto issue = [&](long long t, int s) {\n"
+    << "    if (t < " << p.outer << "LL) {\n"
+    << "      const T *src = A + base_in(t - lane) + lane;\n"
+    << "      T *dst = wstage + s * " << S << ";\n";
+  for (int i = 0; i < (1 << tin.nreg); ++i) {
+    int D;
+    int64_t off;
+    tile_word(tin, i, &D, &off);
+    o << "      cp_async4(dst + (Din ^ " << D << "), src + " << off << ");\n";
+  }
+  o << "    }\n    cp_async_commit();\n  };\n"
+    << "  issue(tau, 0);\n"
     << "  build_tables<T>(p, X, sT);\n"
     << "  __syncthreads();\n"
     << "  for (int it = 0; tau < " << p.outer << "LL; tau += step, ++it) {\n"
     << "    const int cur = it & 1;\n"
     << "    issue(tau + step, cur ^ 1);\n"
-    << "    cp_async_wait_prev();\n";
-  if (coalesce) o << "    __syncwarp();\n";   // words of the tile come from other lanes
-  o << "    const I bi = base(tau);\n"
-    << "    const T *sv = " << (coalesce ? "wstage" : "stage") << " + cur * " << S << ";\n";
+    << "    cp_async_wait_prev();\n"
+    << "    __syncwarp();\n"   // words of the tile come from other lanes
+    << "    T *const sw = wstage + cur * " << S << ";\n";
   for (int e = 0; e < E; ++e) {
-    if (coalesce) {
-      int g = 0;
-      for (int b = 0; b < RB; ++b)
-        if ((e >> b) & 1) g ^= gbit[b];
-      o << "    T v" << e << " = sv[" << (e << 5) << " + (lane ^ " << g << ")];\n";
-    } else {
-      o << "    T v" << e << " = sv[" << e * NT << " + tid];\n";
-    }
+    const int sl = tile_slot(tin, 0, e);   // (c << 5) | g(c): the lane XORs in below
+    o << "    T v" << e << " = sw[" << (sl & ~31) << " + (lane ^ " << (sl & 31) << ")];\n";
   }
-  if (coalesce) o << "    __syncwarp();\n";   // the slot is refilled by the next issue
-  for (int k = 0; k < p.ntg; ++k) {
-    const TGate &t = p.tg[k];
-    o << "    {  // table gate " << k << (t.kind == 0 ? ": replace" : ": diagonal") << "\n";
+  o << "    __syncwarp();\n";   // the slot is reused for the outputs below
+  auto gate_table = [&](const TGate &t, std::ostringstream &g) {
     std::ostringstream f;
     if (t.nf == 0) f << "0";
     for (int i = 0; i < t.nf; ++i) {
       if (i) f << " | ";
       f << "((int)((tau >> " << (int)t.fsh[i] << ") & 1) << " << i << ")";
     }
-    o << "      const int f = " << f.str() << ";\n"
+    g << "      const int f = " << f.str() << ";\n"
       << "      const V lo = *reinterpret_cast<const V *>(sT + " << t.toff << " + f * 8);\n";
-    if (t.kind == 0) {
-      if (t.K >= 0) o << "      const V hi = *reinterpret_cast<const V *>(sT + " << t.toff << " + f * 8 + 4);\n";
+    if (t.kind != 1 && t.K >= 0)
+      g << "      const V hi = *reinterpret_cast<const V *>(sT + " << t.toff << " + f * 8 + 4);\n";
+  };
+  for (int k = 0; k < p.ntg; ++k) {
+    const TGate &t = p.tg[k];
+    std::ostringstream g;
+    g << "    {  // table gate " << k
+      << (t.kind == 0 ? ": replace" : t.kind == 2 ? ": final contraction" : ": diagonal") << "\n";
+    gate_table(t, g);
+    if (t.kind == 0 || t.kind == 2) {
       for (int e = 0; e < E; ++e) {
         if (e & (1 << t.J)) continue;
         const int e1 = e | (1 << t.J);
         const char *tb = (t.K >= 0 && ((e >> t.K) & 1)) ? "hi" : "lo";
-        o << "      { const T a = v" << e << ", b = v" << e1 << "; v" << e << " = " << MX << "(a + "
-          << tb << ".x, b + " << tb << ".y); v" << e1 << " = " << MX << "(a + " << tb
-          << ".z, b + " << tb << ".w); }\n";
+        if (t.kind == 0)
+          g << "      { const T a = v" << e << ", b = v" << e1 << "; v" << e << " = " << MX << "(a + "
+            << tb << ".x, b + " << tb << ".y); v" << e1 << " = " << MX << "(a + " << tb
+            << ".z, b + " << tb << ".w); }\n";
+        else
+          g << "      v" << e << " = " << MX << "(v" << e << " + " << tb << ".x, v" << e1 << " + "
+            << tb << ".y);\n";
       }
     } else {
       for (int e = 0; e < E; ++e) {
         const int x0 = t.J >= 0 ? (e >> t.J) & 1 : 0, x1 = t.K >= 0 ? (e >> t.K) & 1 : 0;
         const char *c = x1 ? (x0 ? "w" : "z") : (x0 ? "y" : "x");
-        o << "      v" << e << " = v" << e << " + lo." << c << ";\n";
+        g << "      v" << e << " = v" << e << " + lo." << c << ";\n";
       }
     }
-    o << "    }\n";
+    g << "    }\n";
+    o << g.str();
   }
-  if (coalesce && std::getenv("TN_JIT_SCATTER_STORES") == nullptr) {
-    // outputs go through the warp's tile (its slot was read above) and leave
-    // as whole 128-byte lines: lane stores tile words lane + 32 i
-    o << "    T *sw = wstage + cur * " << S << ";\n";
-    for (int e = 0; e < E; ++e) {
-      int g = 0;
-      for (int b = 0; b < RB; ++b)
-        if ((e >> b) & 1) g ^= gbit[b];
-      o << "    sw[" << (e << 5) << " + (lane ^ " << g << ")] = v" << e << ";\n";
-    }
-    o << "    __syncwarp();\n"
-      << "    T *dst = C + base(tau - lane) + lane;\n";
-    for (int i = 0; i < E; ++i) {
-      int64_t Ci = 0;
-      int Di = 0;
-      for (int k2 = 0; k2 < RB; ++k2)
-        if ((i >> k2) & 1) {
-          Ci += int64_t(1) << tpos[5 + k2];
-          Di ^= cbit[5 + k2];
-        }
-      o << "    dst[" << Ci << "] = sw[Dt ^ " << Di << "];\n";
-    }
-    o << "    __syncwarp();\n";   // the tile is refilled by a later issue
-  } else {
-    o << "    T *dst = C + bi;\n";
-    for (int e = 0; e < E; ++e) o << "    dst[" << p.hi_off[e] << "] = v" << e << ";\n";
+  (void)nmain;
+  // outputs through the warp's tile, then whole 128-byte lines
+  for (int e = 0; e < E; ++e) {
+    if (e & cmask) continue;
+    const int sl = tile_slot(tout, 0, e);
+    o << "    sw[" << (sl & ~31) << " + (lane ^ " << (sl & 31) << ")] = v" << e << ";\n";
   }
-  o << "  }\n  asm volatile(\"cp.async.wait_all;\\n\" ::: \"memory\");\n}\n";
+  o << "    __syncwarp();\n"
+    << "    T *dst = C + base_out(tau - lane) + lane;\n";
+  for (int i = 0; i < (1 << tout.nreg); ++i) {
+    int D;
+    int64_t off;
+    tile_word(tout, i, &D, &off);
+    o << "    dst[" << off << "] = sw[Dout ^ " << D << "];\n";
+  }
+  o << "    __syncwarp();\n"   // the tile is refilled by a later issue
+    << "  }\n  asm volatile(\"cp.async.wait_all;\\n\" ::: \"memory\");\n}\n";
   return o.str();
 }
 
@@ -351,6 +360,7 @@ bool jit_chains(const std::vector<ChainParams> &chains, Dtype dt, std::vector<co
       Job j;
       j.idx = i;
       const std::string probe = jit_chain_source(chains[i], dt, "tn_chain");
+      if (probe.empty()) continue;   // no tile map: the chain stays interpreted
       j.h = fnv1a(tag + probe);
       char nm[40];
       std::snprintf(nm, sizeof(nm), "tn_chain_%016llx", (unsigned long long)j.h);

@@ -23,18 +23,24 @@ namespace tn {
 bool jit_chains(const std::vector<ChainParams> &chains, Dtype dt, std::vector<const void *> *out,
                 std::string *err);
 
-// Coalesced tile copies of a compiled chain with RB register legs (5 or 6).
-// A warp's tile is its 32 outer indices x 2^RB register states; tile word
-// bit j sits at memory position tpos[j] (tpos[j] == j for j < 5).  Word w goes
-// to slot XOR_j{cbit[j] : bit j of w set} of the warp's tile; element (lane
-// rank bits tau, register index e) is at slot
-// (e << 5) | (tau ^ XOR_b{gbit[b] : bit b of e}).
+// Coalesced tile copies of a compiled chain with RB register legs (5 or 6),
+// for one layout (input: hi = hi_in, output: hi = hi_out; a register leg with
+// offset 0 there is not a leg of that layout).  A warp's tile is its 32 outer
+// indices x 2^nreg register states; tile word bit j sits at memory position
+// tpos[j] (tpos[j] == j for j < 5).  Word lane + 32 i lies at the warp's tile
+// base + lane + off_i and in shared-memory slot D_lane ^ D_i (tile_word:
+// D_i, off_i; D_lane = XOR_j<5 {cbit[j] : bit j of lane}); the thread of lane
+// finds register state e at slot tile_slot(lane, e).
 struct TileMap {
-  int gbit[6] = {0, 0, 0, 0, 0, 0};
+  int nreg = 0;                       // register legs of this layout
+  int rbit[6] = {0, 0, 0, 0, 0, 0};   // their bits in the register state index
+  int gbit[6] = {0, 0, 0, 0, 0, 0};   // slot swizzle of each of them
   std::vector<int> cbit;
   std::vector<int> tpos;
 };
-bool tile_map(const ChainParams &p, TileMap *tm);
+bool tile_map(const ChainParams &p, const int64_t *hi, TileMap *tm);
+int tile_slot(const TileMap &tm, int lane, int e);
+void tile_word(const TileMap &tm, int i, int *D, int64_t *off);
 
 // Source of the specialised kernel `name` for one chain (exposed for tests).
 std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &name);

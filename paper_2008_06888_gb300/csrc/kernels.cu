@@ -1506,6 +1506,37 @@ __device__ __forceinline__ void tc_apply(int code, T (&v)[1 << RB], const V &lo,
 #undef TC_R
 }
 
+// final contraction on register bit J (extra leg K): state e with bit J clear
+// keeps max over the bit of value + table (lo / hi by K digit: .x for digit 0,
+// .y for digit 1)
+template <int RB, int J, int K, typename T, typename V>
+__device__ __forceinline__ void tc_con(T (&v)[1 << RB], const V &lo, const V &hi) {
+  if constexpr (J < RB && K < RB) {
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+      if (e & (1 << J)) continue;
+      const bool k = K >= 0 ? ((e >> (K < 0 ? 0 : K)) & 1) != 0 : false;
+      const T t0 = k ? hi.x : lo.x, t1 = k ? hi.y : lo.y;
+      v[e] = max(v[e] + t0, v[e | (1 << J)] + t1);
+    }
+  }
+}
+
+template <int RB, typename T, typename V>
+__device__ __forceinline__ void tc_contract(int code, T (&v)[1 << RB], const V &lo, const V &hi) {
+#define TC_C(J, K) case 100 + (J) * 7 + (K) + 1: tc_con<RB, J, K>(v, lo, hi); break;
+  switch (code) {
+    TC_C(0, -1) TC_C(0, 1) TC_C(0, 2) TC_C(0, 3) TC_C(0, 4) TC_C(0, 5)
+    TC_C(1, -1) TC_C(1, 0) TC_C(1, 2) TC_C(1, 3) TC_C(1, 4) TC_C(1, 5)
+    TC_C(2, -1) TC_C(2, 0) TC_C(2, 1) TC_C(2, 3) TC_C(2, 4) TC_C(2, 5)
+    TC_C(3, -1) TC_C(3, 0) TC_C(3, 1) TC_C(3, 2) TC_C(3, 4) TC_C(3, 5)
+    TC_C(4, -1) TC_C(4, 0) TC_C(4, 1) TC_C(4, 2) TC_C(4, 3) TC_C(4, 5)
+    TC_C(5, -1) TC_C(5, 0) TC_C(5, 1) TC_C(5, 2) TC_C(5, 3) TC_C(5, 4)
+    default: break;
+  }
+#undef TC_C
+}
+
 // digits of the fixed legs (bits of the outer index tau) -> table slice offset
 // (8 values per slice)
 __device__ __forceinline__ int tc_slice(const int4 &d, int64_t tau) {
@@ -1583,7 +1614,10 @@ __global__ void __launch_bounds__(NT, MINB) k_tchain(const ChainParams p,
     sD[k] = d;
   }
   __syncthreads();
-  const int ntg = p.ntg;
+  // a final contraction runs after the loop and halves the stored states
+  const bool con = p.ntg > 0 && p.tg[p.ntg - 1].kind == 2;
+  const int ntg = con ? p.ntg - 1 : p.ntg;
+  const int cmask = con ? 1 << p.tg[p.ntg - 1].J : 0;
   for (int it = 0; tau < p.outer; tau += step, ++it) {
     T *cur = slot(it);
     issue(tau + (STAGES - 1) * step, slot(it + STAGES - 1));
@@ -1615,6 +1649,12 @@ __global__ void __launch_bounds__(NT, MINB) k_tchain(const ChainParams p,
       dA = dA2;
       dB = dB2;
     }
+    if (con) {
+      const int4 dc = sD[ntg];
+      const int ac = tc_slice(dc, tau);
+      tc_contract<RB>(dc.x, v, *reinterpret_cast<const V *>(sT + ac),
+                      *reinterpret_cast<const V *>(sT + ac + 4));
+    }
     T *dst = C + bi;
     I o[1 << RB];
     o[0] = 0;
@@ -1624,7 +1664,8 @@ __global__ void __launch_bounds__(NT, MINB) k_tchain(const ChainParams p,
       o[e] = o[e ^ (1 << hb)] + sO[hb];
     }
 #pragma unroll
-    for (int e = 0; e < (1 << RB); ++e) dst[o[e]] = v[e];
+    for (int e = 0; e < (1 << RB); ++e)
+      if (!(e & cmask)) dst[o[e]] = v[e];
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
@@ -1827,7 +1868,12 @@ __device__ void trace_tchain(const ChainTrace &ct, const T *X, int8_t *state, in
       T *dst = buf + (int64_t)(gi + 1) * E;
       const T *tab = slice(t);
       for (int e = lane; e < E; e += 32) {
-        if (t.kind != 0) {
+        if (t.kind == 2) {   // final contraction: states with bit J clear
+          if (!(e & (1 << t.J))) {
+            const int k = t.K >= 0 ? (e >> t.K) & 1 : 0;
+            dst[e] = max(src[e] + tab[k * 4], src[e | (1 << t.J)] + tab[k * 4 + 1]);
+          }
+        } else if (t.kind != 0) {
           const int x0 = t.J >= 0 ? (e >> t.J) & 1 : 0, x1 = t.K >= 0 ? (e >> t.K) & 1 : 0;
           dst[e] = src[e] + tab[x0 | (x1 << 1)];
         } else if (!(e & (1 << t.J))) {
@@ -1841,14 +1887,27 @@ __device__ void trace_tchain(const ChainTrace &ct, const T *X, int8_t *state, in
       __syncwarp();
     }
     if (lane == 0) {
+      // a final contraction's leg is not fixed yet: its digit is chosen first
+      const int cj = p.ntg > 0 && p.tg[p.ntg - 1].kind == 2 ? p.tg[p.ntg - 1].J : -1;
       int x = 0;
       for (int j = 0; j < p.t; ++j) {
+        if (j == cj) continue;
         int d = state[ct.local_spin[j]];
         if (d < 0 || d > 1) { *err = 1; d = 0; }
         x |= d << j;
       }
       for (int gi = p.ntg - 1; gi >= 0; --gi) {
         const TGate &t = p.tg[gi];
+        if (t.kind == 2) {
+          const T *src = buf + (int64_t)gi * E;
+          const T *tab = slice(t);
+          const int k = t.K >= 0 ? (x >> t.K) & 1 : 0;
+          const T c0 = src[x] + tab[k * 4], c1 = src[x | (1 << t.J)] + tab[k * 4 + 1];
+          const int u = c1 > c0 ? 1 : 0;
+          state[t.kspin] = (int8_t)u;
+          x |= u << t.J;
+          continue;
+        }
         if (t.kind != 0) continue;
         const T *src = buf + (int64_t)gi * E;
         const T *tab = slice(t);

@@ -44,7 +44,9 @@ int pos_of(const std::vector<int> &v, int x) {
 // ("post"), else of the first one that later eliminates one of them ("pre"),
 // provided D's other legs keep their spins in between.  Terms on fixed legs
 // only are per-thread constants and go into any replace gate.  Diagonal
-// gates that fit nowhere remain table gates of their own.
+// gates that fit nowhere remain table gates of their own.  A final
+// contraction (a replace gate without a new digit) takes terms like the
+// replace gate that next eliminates their leg.
 
 static bool tg_fixed_bit(TGate &t, int sh, int8_t *bit) {
   for (int i = 0; i < t.nf; ++i)
@@ -91,15 +93,15 @@ static void fold_reg_chain(ChainParams &cp) {
   std::vector<int> of(n, -1);        // replace gate -> its table gate
   for (int i = 0; i < n; ++i) {
     const ChainGate &g = cp.g[i];
-    if (g.kind != 0) continue;
+    if (g.kind != 0 && g.kind != 2) continue;
     TGate t{};
-    t.kind = 0;
+    t.kind = (int8_t)g.kind;   // 0 replace, 2 contract (no new digit)
     t.J = (int8_t)g.ls;
     t.K = -1;
     t.kspin = g.kspin;
     t.cg[0] = (int8_t)i;
     t.cbit[0][0] = 0;
-    t.cbit[0][1] = 1;
+    t.cbit[0][1] = g.kind == 0 ? 1 : -1;
     t.cbit[0][2] = t.cbit[0][3] = -1;
     if (g.nb > 0) {
       if (g.lsb[0] >= 0) {
@@ -134,7 +136,7 @@ static void fold_reg_chain(ChainParams &cp) {
       if (cs >= 0) done = tg_add_diag(cp, d, tg[of[cs]], 1);
       if (!done) {
         for (int j = d + 1; j < n; ++j) {
-          if (cp.g[j].kind != 0) continue;
+          if (cp.g[j].kind != 0 && cp.g[j].kind != 2) continue;
           if (std::find(regs.begin(), regs.end(), cp.g[j].ls) == regs.end()) continue;
           done = tg_add_diag(cp, d, tg[of[j]], 0);
           break;
@@ -168,8 +170,11 @@ static void fold_reg_chain(ChainParams &cp) {
   for (size_t k = 0; k < ord.size(); ++k) {
     TGate t = tg[ord[k]];
     for (int i = t.nf; i < TN_TG_MAXF; ++i) t.fsh[i] = 62;   // a tau bit that is always 0
-    // dispatch code: replace J * 7 + K + 1 (< 42), diagonal 42 + (J + 1) * 7 + K + 1
-    t.code = t.kind == 0 ? (int16_t)(t.J * 7 + (t.K + 1)) : (int16_t)(42 + (t.J + 1) * 7 + (t.K + 1));
+    // dispatch code: replace J * 7 + K + 1 (< 42), diagonal 42 + (J + 1) * 7 + K + 1,
+    // contract 100 + J * 7 + K + 1 (always the last table gate)
+    t.code = t.kind == 0   ? (int16_t)(t.J * 7 + (t.K + 1))
+             : t.kind == 2 ? (int16_t)(100 + t.J * 7 + (t.K + 1))
+                           : (int16_t)(42 + (t.J + 1) * 7 + (t.K + 1));
     t.toff = (int16_t)off;
     off += 8 << t.nf;
     cp.tg[k] = t;
@@ -580,8 +585,8 @@ struct Builder {
 
   // ---- fused gate chains
   struct CGate {
-    int kind = 0;            // 0 replace, 1 diagonal
-    int pos = -1;            // replaced position (replace)
+    int kind = 0;            // 0 replace, 1 diagonal, 2 contract (ends the chain)
+    int pos = -1;            // replaced / contracted position
     int kspin = -1;
     int btensor = -1;
     std::vector<int> bpos;   // positions of B's legs that are legs of the state
@@ -595,6 +600,11 @@ struct Builder {
     std::vector<CGate> gates;
     std::vector<int> touched;   // positions touched by the gates
     std::vector<int> rpos;      // positions replaced by the gates
+    // rank-changing ends (folded register chains): the chain starts from the
+    // input of a step that adds a leg (the new leg, innermost, is a register
+    // leg and gate 0 adds that step's operand) and/or ends with a contraction
+    bool grow = false, contract = false;
+    std::vector<int> state;     // leg order between the gates
   };
   std::vector<Macro> macros;
   std::vector<int> macro_of;    // tensor -> macro producing it
@@ -634,6 +644,57 @@ struct Builder {
     return true;
   }
 
+  // Rank-changing steps at the ends of a folded register chain (values, q = 2).
+  bool rank_fusion() const { return regmode && fold && P == 0 && kRB >= 5; }
+
+  // a step adding one leg to `big` (no contraction, one batch leg at most): the
+  // chain starts from big, the new leg innermost; gate 0 is the diagonal gate
+  // adding the small operand over (new leg, batch leg)
+  bool try_grow(const PStep &st, int big, int small, CGate *g, std::vector<int> *ord) {
+    if (!rank_fusion()) return false;
+    const std::vector<int> &ob = order[big], &os = order[small];
+    const std::vector<int> &N = (big == st.a) ? st.N : st.M;
+    const std::vector<int> &Mb = (big == st.a) ? st.M : st.N;
+    (void)Mb;
+    if (!st.K.empty() || N.size() != 1 || st.batch.size() > 1) return false;
+    if ((int)os.size() != 1 + (int)st.batch.size()) return false;
+    const int R = (int)ob.size() + 1;
+    if (R < kRB + 8) return false;
+    *ord = ob;
+    ord->push_back(N[0]);
+    *g = CGate();
+    g->kind = 1;
+    g->btensor = small;
+    g->bpos.push_back(R - 1);
+    g->sBb[0] = stride(os, N[0]);
+    if (!st.batch.empty()) {
+      g->bpos.push_back(pos_of(*ord, st.batch[0]));
+      g->sBb[1] = stride(os, st.batch[0]);
+    }
+    return true;
+  }
+
+  // a step contracting one leg of the open chain's state with a small operand
+  // (no new leg, one batch leg at most): the chain's last gate
+  bool try_contract(const PStep &st, int big, int small, CGate *g) {
+    if (!rank_fusion()) return false;
+    const std::vector<int> &ob = order[big], &os = order[small];
+    const std::vector<int> &N = (big == st.a) ? st.N : st.M;
+    if (st.K.size() != 1 || !N.empty() || st.batch.size() > 1) return false;
+    if ((int)os.size() != 1 + (int)st.batch.size()) return false;
+    *g = CGate();
+    g->kind = 2;
+    g->btensor = small;
+    g->pos = pos_of(ob, st.K[0]);
+    g->kspin = st.K[0];
+    g->sBk = stride(os, st.K[0]);
+    if (!st.batch.empty()) {
+      g->bpos.push_back(pos_of(ob, st.batch[0]));
+      g->sBb[0] = stride(os, st.batch[0]);
+    }
+    return true;
+  }
+
   std::vector<int> local_set(int R, const std::vector<int> &touched) const {
     std::vector<int> T;
     for (int p = std::max(0, R - wlow); p < R; ++p) T.push_back(p);
@@ -646,7 +707,7 @@ struct Builder {
     if ((int)m.gates.size() >= TN_CHAIN_MAX_G) return false;
     if (regmode) {
       int n = (int)m.rpos.size();
-      if (g.kind == 0 && pos_of(m.rpos, g.pos) < 0) ++n;
+      if ((g.kind == 0 || g.kind == 2) && pos_of(m.rpos, g.pos) < 0) ++n;
       return n <= kRB;
     }
     std::vector<int> t = m.touched;
@@ -656,14 +717,26 @@ struct Builder {
     return (int)local_set(R, t).size() <= tmax;
   }
 
-  void append(Macro &m, int s, const CGate &g) {
+  void append(Macro &m, int s, const CGate &g, const std::vector<int> *grow_ord = nullptr) {
     const PStep &st = plan.steps[s];
-    std::vector<int> ord = order[m.out];
+    std::vector<int> ord = grow_ord ? *grow_ord : order[m.out];
     if (g.kind == 0) {
       const std::vector<int> &N = (m.out == st.a) ? st.N : st.M;
       ord[g.pos] = N[0];
       m.touched.push_back(g.pos);
       if (pos_of(m.rpos, g.pos) < 0) m.rpos.push_back(g.pos);
+    }
+    if (grow_ord) {
+      // the new leg is a register leg of the chain
+      m.grow = true;
+      if (pos_of(m.rpos, (int)ord.size() - 1) < 0) m.rpos.push_back((int)ord.size() - 1);
+    }
+    m.state = ord;
+    if (g.kind == 2) {
+      m.contract = true;
+      m.touched.push_back(g.pos);
+      if (pos_of(m.rpos, g.pos) < 0) m.rpos.push_back(g.pos);
+      ord.erase(ord.begin() + g.pos);
     }
     for (int p : g.bpos) m.touched.push_back(p);
     std::sort(m.touched.begin(), m.touched.end());
@@ -688,32 +761,54 @@ struct Builder {
 
   ChainParams reg_chain_params(const Macro &m, std::vector<Loc> *blocs) {
     ChainParams cp{};
-    const std::vector<int> &ord = order[m.out];
+    // positions are those of the state between the gates; the input lacks the
+    // grown leg (innermost), the output lacks the contracted one
+    const std::vector<int> &ord = m.state.empty() ? order[m.out] : m.state;
     const int R = (int)ord.size();
     std::vector<int> S = reg_legs(m);
+    const int kpos = m.contract ? m.gates.back().pos : -1;
+    auto s_state = [&](int p) { return int64_t(1) << (R - 1 - p); };
+    auto s_in = [&](int p) -> int64_t {
+      if (!m.grow) return s_state(p);
+      return p == R - 1 ? 0 : int64_t(1) << (R - 2 - p);
+    };
+    auto s_out = [&](int p) -> int64_t {
+      if (!m.contract) return s_state(p);
+      if (p == kpos) return 0;
+      return p < kpos ? int64_t(1) << (R - 2 - p) : s_state(p);
+    };
+    auto lg = [](int64_t x) { int r = 0; while ((int64_t(1) << r) < x) ++r; return r; };
     cp.mode = 1;
     cp.q = 2;
     cp.t = kRB;          // 6 (values), 3 (values + residue planes)
     cp.tile = 1 << kRB;
     for (int e = 0; e < cp.tile; ++e) {
-      int64_t off = 0;
+      int64_t off = 0, oin = 0, oout = 0;
       for (int j = 0; j < kRB; ++j)
-        if (e >> j & 1) off += int64_t(1) << (R - 1 - S[j]);
+        if (e >> j & 1) {
+          off += s_state(S[j]);
+          oin += s_in(S[j]);
+          oout += s_out(S[j]);
+        }
       cp.hi_off[e] = off;
+      cp.hi_in[e] = oin;
+      cp.hi_out[e] = oout;
     }
     std::vector<int64_t> sz, st;
-    std::vector<int> sh;
+    std::vector<int> sh, inner;   // inner: the segment's fastest position
     for (int p = 0; p < R; ++p) {
       if (pos_of(S, p) >= 0) continue;
-      const int64_t sp = int64_t(1) << (R - 1 - p);
+      const int64_t sp = s_state(p);
       if (!sz.empty() && p > 0 && pos_of(S, p - 1) < 0) {
         sz.back() *= 2;
         st.back() = sp;
         sh.back()++;
+        inner.back() = p;
       } else {
         sz.push_back(2);
         st.push_back(sp);
         sh.push_back(1);
+        inner.push_back(p);
       }
     }
     cp.nseg = (int)sz.size();
@@ -722,11 +817,10 @@ struct Builder {
       cp.seg_size[i] = sz[i];
       cp.seg_s[i] = st[i];
       cp.seg_sh[i] = sh[i];
-      cp.seg_ssh[i] = 0;
-      while ((int64_t(1) << cp.seg_ssh[i]) < st[i]) cp.seg_ssh[i]++;
-      cp.ssh_in[i] = cp.ssh_out[i] = cp.seg_ssh[i];
+      cp.seg_ssh[i] = lg(st[i]);
+      cp.ssh_in[i] = lg(s_in(inner[i]));
+      cp.ssh_out[i] = lg(s_out(inner[i]));
     }
-    for (int e = 0; e < cp.tile; ++e) cp.hi_in[e] = cp.hi_out[e] = cp.hi_off[e];
     // bit of each outer position in tau: outer positions, fastest first
     std::vector<int> trank(R, -1);
     for (int p = R - 1, r = 0; p >= 0; --p)
@@ -737,7 +831,7 @@ struct Builder {
       const CGate &g = m.gates[i];
       ChainGate &c = cp.g[i];
       c.kind = g.kind;
-      c.ls = g.kind == 0 ? pos_of(S, g.pos) : 0;
+      c.ls = (g.kind == 0 || g.kind == 2) ? pos_of(S, g.pos) : 0;
       c.nb = (int)g.bpos.size();
       for (int j = 0; j < c.nb; ++j) {
         c.lsb[j] = pos_of(S, g.bpos[j]);
@@ -870,6 +964,11 @@ struct Builder {
             append(open, s, g);
             continue;
           }
+          if (try_contract(st, open.out, small, &g) && fits(open, g)) {
+            append(open, s, g);   // a contraction ends the chain
+            flush_chain();
+            continue;
+          }
           flush_chain();
         }
         int big = tsize(st.a) >= tsize(st.b) ? st.a : st.b;
@@ -884,6 +983,16 @@ struct Builder {
             has_open = true;
             continue;
           }
+        }
+        std::vector<int> gord;
+        if (try_grow(st, big, small, &g, &gord)) {
+          flush_chain();
+          open = Macro();
+          open.chain = true;
+          open.in = open.out = big;
+          append(open, s, g, &gord);
+          has_open = true;
+          continue;
         }
       }
       if (has_open && (st.a == open.out || st.b == open.out)) flush_chain();
@@ -937,13 +1046,15 @@ struct Builder {
         ChainTrace ct{};
         std::vector<Loc> bl;
         ct.p = chain_params(m, &bl);
-        const std::vector<int> &ord = order[m.out];
+        // the state between the gates; outer legs are read from the chain's
+        // input (without the grown leg, the innermost one, if any)
+        const std::vector<int> &ord = m.state.empty() ? order[m.out] : m.state;
         const int R = (int)ord.size();
         std::vector<int> T = regmode ? reg_legs(m) : local_set(R, m.touched);
         for (int p = 0; p < R; ++p) {
           if (pos_of(T, p) >= 0) continue;
           ct.out_spin[ct.nout] = ord[p];
-          ct.out_stride[ct.nout] = ipow(q, R - 1 - p);
+          ct.out_stride[ct.nout] = m.grow ? ipow(q, R - 2 - p) : ipow(q, R - 1 - p);
           int rank = 0;   // bit of this outer leg in tau: outer legs faster than it
           for (int p2 = p + 1; p2 < R; ++p2) rank += pos_of(T, p2) < 0;
           ct.out_rank[ct.nout] = rank;

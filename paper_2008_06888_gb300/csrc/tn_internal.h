@@ -108,7 +108,7 @@ struct TraceStep {
 #define TN_CHAIN_MAX_HI 128
 
 struct ChainGate {
-  int32_t kind;      // 0 replace, 1 diagonal
+  int32_t kind;      // 0 replace, 1 diagonal, 2 contract (folded register chains, last)
   int32_t ls;        // local stride of the replaced leg (replace)
   int32_t nb;        // B legs that are legs of the tile (0..2)
   int32_t lsb[2];    // their local strides
@@ -142,7 +142,7 @@ struct ChainGate {
 #define TN_TG_MAXF 3
 #define TN_TG_TABLE 64       // largest table (8 << TN_TG_MAXF values)
 struct TGate {
-  int8_t kind;                  // 0 replace, 1 diagonal
+  int8_t kind;                  // 0 replace, 1 diagonal, 2 contract (last; no new digit)
   int8_t J, K;                  // register legs (-1: none)
   int8_t nf, ncomp;
   int8_t fsh[TN_TG_MAXF];       // fixed legs: their bits in the outer index tau

@@ -3,8 +3,10 @@
 // Builds the energy and traceback programs of several lattices and chimera
 // graphs, then evaluates every register chain twice on sampled outer
 // indices: through its original gate list (replace gates: max over the
-// eliminated digit of value + operand; diagonal gates: value + operand) and
-// through its folded table gates.  Operands and inputs are small integers
+// eliminated digit of value + operand; diagonal gates: value + operand; a
+// final contraction: max over the contracted digit; a chain that starts
+// from a rank-raising step reads both states of the new leg from one input
+// element) and through its folded table gates.  Operands and inputs are small integers
 // drawn from a hash, so both evaluations are exact and must agree exactly.
 // Exit status 0 when every chain agrees.
 #include <cstdio>
@@ -19,9 +21,9 @@ size_t chain_smem_bytes(const ChainParams &, size_t) { return 0; }
 }
 using namespace tn;
 static double X(int64_t i) { uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull; h ^= h >> 29; h *= 0xBF58476D1CE4E5B9ull; h ^= h >> 32; return (double)(int)(h % 9) - 4.0; }
-static int64_t rc_base(const ChainParams &p, int64_t tau) {
+static int64_t rc_base(const ChainParams &p, int64_t tau, const int32_t *ssh = nullptr) {
   int64_t base = 0, t = tau;
-  for (int sg = p.nseg - 1; sg >= 0; --sg) { base += (t & (p.seg_size[sg] - 1)) << p.seg_ssh[sg]; t >>= p.seg_sh[sg]; }
+  for (int sg = p.nseg - 1; sg >= 0; --sg) { base += (t & (p.seg_size[sg] - 1)) << (ssh ? ssh[sg] : p.seg_ssh[sg]); t >>= p.seg_sh[sg]; }
   return base;
 }
 static int check_chain(const ChainParams &p, std::mt19937_64 &rng, int *ntg_out) {
@@ -43,14 +45,24 @@ static int check_chain(const ChainParams &p, std::mt19937_64 &rng, int *ntg_out)
   }
   for (int trial = 0; trial < 64; ++trial) {
     int64_t tau = (int64_t)(rng() % (uint64_t)p.outer);
-    int64_t base = rc_base(p, tau);
+    int64_t base = rc_base(p, tau), base_in = rc_base(p, tau, p.ssh_in);
     const int E = p.tile;   // 2^t register states
     double v[64], w[64];
-    for (int e = 0; e < E; ++e) v[e] = w[e] = X(1000000007ll + base + p.hi_off[e]);
+    // input layout: a chain starting with a rank-raising step reads both states
+    // of the new leg from one input element
+    for (int e = 0; e < E; ++e) v[e] = w[e] = X(1000000007ll + base_in + p.hi_in[e]);
+    int cj = -1;   // register bit of a final contraction
     for (int gi = 0; gi < p.ngates; ++gi) {
       const ChainGate &g = p.g[gi];
       auto dig = [&](int k, int e) { return g.lsb[k] >= 0 ? (e >> g.lsb[k]) & 1 : (int)((base >> g.lsbh[k]) & 1); };
-      if (g.kind != 0) {
+      if (g.kind == 2) {   // contraction: state e (bit ls clear) keeps the max over the bit
+        cj = g.ls;
+        for (int e = 0; e < E; ++e) {
+          if (e & (1 << g.ls)) continue;
+          int64_t bo = g.nb > 0 ? dig(0, e) * g.sBb[0] : 0;
+          v[e] = std::max(v[e] + X(g.offB + bo), v[e | (1 << g.ls)] + X(g.offB + bo + g.sBk));
+        }
+      } else if (g.kind != 0) {
         for (int e = 0; e < E; ++e) { int x0 = dig(0, e), x1 = g.nb > 1 ? dig(1, e) : 0; v[e] += X(g.offB + x0 * g.sBb[0] + x1 * (g.nb > 1 ? g.sBb[1] : 0)); }
       } else {
         for (int e = 0; e < E; ++e) {
@@ -69,7 +81,13 @@ static int check_chain(const ChainParams &p, std::mt19937_64 &rng, int *ntg_out)
       int f = 0;
       for (int i = 0; i < t.nf; ++i) f |= (int)((tau >> t.fsh[i]) & 1) << i;
       const double *tab = &T[t.toff + f * 8];
-      if (t.kind != 0) {
+      if (t.kind == 2) {
+        for (int e = 0; e < E; ++e) {
+          if (e & (1 << t.J)) continue;
+          int kk = t.K >= 0 ? (e >> t.K) & 1 : 0;
+          w[e] = std::max(w[e] + tab[kk * 4], w[e | (1 << t.J)] + tab[kk * 4 + 1]);
+        }
+      } else if (t.kind != 0) {
         for (int e = 0; e < E; ++e) { int x0 = t.J >= 0 ? (e >> t.J) & 1 : 0, x1 = t.K >= 0 ? (e >> t.K) & 1 : 0; w[e] += tab[x0 | x1 << 1]; }
       } else {
         for (int e = 0; e < E; ++e) {
@@ -81,7 +99,8 @@ static int check_chain(const ChainParams &p, std::mt19937_64 &rng, int *ntg_out)
         }
       }
     }
-    for (int e = 0; e < E; ++e) if (v[e] != w[e]) bad++;
+    for (int e = 0; e < E; ++e)
+      if ((cj < 0 || !(e & (1 << cj))) && v[e] != w[e]) bad++;
   }
   *ntg_out = p.ntg;
   return bad;
@@ -115,7 +134,7 @@ static Net chimera(int L, uint64_t seed) {
 }
 int main() {
   std::mt19937_64 rng(5);
-  int total_bad = 0, nchains = 0, norig = 0, nfold = 0;
+  int total_bad = 0, nchains = 0, norig = 0, nfold = 0, ncontract = 0, ngrow = 0;
   struct Case { const char *name; Net net; int order; };
   std::vector<Case> cases;
   for (int L : {14, 20, 24}) { cases.push_back({"sq", square(L, true, L), 0}); cases.push_back({"sqg", square(L, false, L + 1), 1}); cases.push_back({"sqg-f", square(L, true, L + 2), 1}); }
@@ -138,6 +157,8 @@ int main() {
         if (p.mode != 1) return;
         int ntg = 0;
         int bad = check_chain(p, rng, &ntg);
+        for (int i = 0; i < p.ngates; ++i) ncontract += p.g[i].kind == 2;
+        for (int e = 1; e < p.tile; ++e) ngrow += p.hi_in[e] == 0;
         total_bad += bad; nchains++; norig += p.ngates; nfold += ntg;
         if (bad) printf("MISMATCH %s n=%d chain ngates=%d ntg=%d bad=%d\n", c.name, c.net.n, p.ngates, ntg, bad);
       };
@@ -145,6 +166,7 @@ int main() {
       for (auto &ct : pg.chain_traces) run(ct.p);
     }
   }
+  printf("rank-changing: %d contractions, %d grown legs\n", ncontract, ngrow);
   printf("chains %d orig gates %d table gates %d mismatches %d\n", nchains, norig, nfold, total_bad);
   return total_bad != 0;
 }

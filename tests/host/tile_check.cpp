@@ -1,10 +1,15 @@
 // tile_check.cpp -- host check of the coalesced tile copies of compiled
-// register chains (no GPU).  For every chain of several programs that has a
-// tile map (5 or 6 register legs), simulates the copies of warp tiles (lane
-// copies tile words lane + 32 i) and checks that every shared-memory slot is written once,
-// that the slot each thread reads for its element (tau, e) holds the word at
-// base(tau) + hi_off[e], and that no warp instruction (copy or read) has two
-// lanes on one bank.  Exit status 0 when all hold.
+// register chains (no GPU).  For every chain of several programs and both of
+// its layouts (input: hi_in / ssh_in, output: hi_out / ssh_out), simulates a
+// warp tile: lane copies tile words lane + 32 i, i < 2^nreg, between memory
+// (tile base + lane + off_i) and shared-memory slot D_lane ^ D_i.  Checks that
+// every slot is used once, that the slot the thread of lane uses for register
+// state e (tile_slot) holds the element at base(tau) + hi[e] of that layout,
+// and that no warp instruction (copy, or the owners' accesses for one e) has
+// two lanes on one bank.  Programs include chains that start from a
+// rank-raising step (the new leg is not a leg of the input) and chains that
+// end with a contraction (the contracted leg is not a leg of the output).
+// Exit status 0 when all hold.
 #include <cstdio>
 #include <map>
 #include <random>
@@ -15,9 +20,9 @@ size_t trace_smem_bytes(const ChainParams &p, size_t elem) { return elem * ((siz
 size_t chain_smem_bytes(const ChainParams &, size_t) { return 0; }
 }
 using namespace tn;
-static int64_t rc_base(const ChainParams &p, int64_t tau) {
+static int64_t base_of(const ChainParams &p, int64_t tau, const int32_t *ssh) {
   int64_t base = 0, t = tau;
-  for (int sg = p.nseg - 1; sg >= 0; --sg) { base += (t & (p.seg_size[sg] - 1)) << p.seg_ssh[sg]; t >>= p.seg_sh[sg]; }
+  for (int sg = p.nseg - 1; sg >= 0; --sg) { base += (t & (p.seg_size[sg] - 1)) << ssh[sg]; t >>= p.seg_sh[sg]; }
   return base;
 }
 static Net square(int L) {
@@ -31,54 +36,57 @@ static Net square(int L) {
 }
 int main() {
   std::mt19937_64 rng(9);
-  int chains = 0, bad = 0, conflicts = 0;
-  for (int L : {16, 20, 24}) for (int ord : {0, 1}) {
+  int chains = 0, sides = 0, partial = 0, bad = 0, conflicts = 0;
+  for (int L : {16, 20, 24}) for (int ord : {0, 1, 2, 3}) for (int mode : {0, 1}) {
     Net net = square(L);
     Tree t; std::string err;
     if (ord == 0) { std::vector<int> seq(net.n); for (int i = 0; i < net.n; ++i) seq[i] = i; tree_from_sweep(net, seq, &t, &err); }
-    else { CostModel cm; tree_greedy(net, 5, 4, cm, &t, &err); }
+    else { CostModel cm; tree_greedy(net, 5 + ord, 4, cm, &t, &err); }
     Plan pl; if (!classify(net, t, &pl, &err)) return 2;
-    Program pg; if (!build_program(net, pl, PM_CONFIG, DT_F32, 0, 0, &pg, &err)) return 2;
+    Program pg; if (!build_program(net, pl, (ProgMode)mode, DT_F32, 0, 0, &pg, &err)) return 2;
     for (const ChainParams &p : pg.chains) {
-      TileMap tm;
-      if (!tile_map(p, &tm)) continue;
+      if (p.mode != 1 || p.P != 0) continue;
       chains++;
-      const int RB = p.t, E = 1 << RB;
-      const int64_t ntiles = p.outer / 32;
-      for (int trial = 0; trial < 8; ++trial) {
-        const int64_t t0 = (int64_t)(rng() % (uint64_t)ntiles) * 32;
-        std::vector<int64_t> slot(32 * E, -1);
-        int Dt[32];
-        for (int lane = 0; lane < 32; ++lane) {
-          Dt[lane] = 0;
-          for (int j = 0; j < 5; ++j) if ((lane >> j) & 1) Dt[lane] ^= tm.cbit[j];
-        }
-        for (int i = 0; i < E; ++i) {
-          int64_t Ci = 0; int Di = 0;
-          for (int k = 0; k < RB; ++k) if ((i >> k) & 1) { Ci += int64_t(1) << tm.tpos[5 + k]; Di ^= tm.cbit[5 + k]; }
-          bool used[32] = {false};
-          for (int lane = 0; lane < 32; ++lane) {
-            const int d = Dt[lane] ^ Di;
-            if (d < 0 || d >= 32 * E || slot[d] != -1) { bad++; continue; }
-            slot[d] = rc_base(p, t0) + lane + Ci;
-            if (used[d & 31]) conflicts++;
-            used[d & 31] = true;
+      for (int side = 0; side < 2; ++side) {
+        const int64_t *hi = side == 0 ? p.hi_in : p.hi_out;
+        const int32_t *ssh = side == 0 ? p.ssh_in : p.ssh_out;
+        TileMap tm;
+        if (!tile_map(p, hi, &tm)) { bad++; continue; }
+        sides++;
+        partial += tm.nreg < p.t;
+        const int E = 1 << p.t, N = 1 << tm.nreg;
+        const int64_t ntiles = p.outer / 32;
+        for (int trial = 0; trial < 6; ++trial) {
+          const int64_t t0 = (int64_t)(rng() % (uint64_t)ntiles) * 32;
+          std::vector<int64_t> slot(32 * N, -1);
+          for (int i = 0; i < N; ++i) {
+            int Di; int64_t off;
+            tile_word(tm, i, &Di, &off);
+            bool used[32] = {false};
+            for (int lane = 0; lane < 32; ++lane) {
+              int Dl = 0;
+              for (int j = 0; j < 5; ++j) if ((lane >> j) & 1) Dl ^= tm.cbit[j];
+              const int d = Dl ^ Di;
+              if (d < 0 || d >= 32 * N || slot[d] != -1) { bad++; continue; }
+              slot[d] = base_of(p, t0, ssh) + lane + off;
+              if (used[d & 31]) conflicts++;
+              used[d & 31] = true;
+            }
           }
-        }
-        for (int e = 0; e < E; ++e) {
-          int g = 0;
-          for (int b = 0; b < RB; ++b) if ((e >> b) & 1) g ^= tm.gbit[b];
-          bool used[32] = {false};
-          for (int lane = 0; lane < 32; ++lane) {
-            const int d = (e << 5) | (lane ^ g);
-            if (slot[d] != rc_base(p, t0 + lane) + p.hi_off[e]) bad++;
-            if (used[d & 31]) conflicts++;
-            used[d & 31] = true;
+          for (int e = 0; e < E; ++e) {
+            bool used[32] = {false};
+            for (int lane = 0; lane < 32; ++lane) {
+              const int d = tile_slot(tm, lane, e);
+              if (d < 0 || d >= 32 * N || slot[d] != base_of(p, t0 + lane, ssh) + hi[e]) bad++;
+              if (used[d & 31]) conflicts++;
+              used[d & 31] = true;
+            }
           }
         }
       }
     }
   }
-  printf("chains %d wrong %d bank_conflicts %d\n", chains, bad, conflicts);
+  printf("chains %d layouts %d (without a register leg: %d) wrong %d bank_conflicts %d\n", chains,
+         sides, partial, bad, conflicts);
   return (bad || conflicts || chains == 0) ? 1 : 0;
 }

@@ -151,8 +151,8 @@ def traffic_from_profiles(kind):
         return None
     vals = {}
     for line in open(path):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
+        if ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].rsplit(": ", 1)
             vals[k.strip()] = v.strip()
     if vals.get("chain sources sha256[:16]") != sources_hash():
         return None

@@ -124,7 +124,7 @@ std::map<std::pair<int, uint64_t>, Loaded> g_loaded;   // (device, source hash)
 bool worth(const ChainParams &p) {
   static const long long min_el = [] {
     const char *s = std::getenv("TN_JIT_MIN_ELEMENTS");
-    return s ? std::atoll(s) : (1ll << 20);
+    return s ? std::atoll(s) : (1ll << 15);
   }();
   return p.mode == 1 && p.P == 0 && (p.t == 5 || p.t == 6) && p.ntg > 0 &&
          p.outer * p.tile >= min_el;

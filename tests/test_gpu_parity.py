@@ -513,7 +513,7 @@ def test_chimera6_planted_counts():
 
 @pytest.mark.parametrize("coupling", ["pm1", "gauss"])
 def test_compiled_chain_kernels_match_interpreter(coupling, monkeypatch):
-    """Chains of 2^20+ elements run as kernels compiled for their gate
+    """Chains of 2^15+ elements run as kernels compiled for their gate
     sequence; they do the interpreter's additions and maxima in the same
     order, so E_min and sigma* agree bit for bit."""
     inst = I.square_lattice(22, coupling=coupling,

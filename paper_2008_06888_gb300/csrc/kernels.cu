@@ -2111,7 +2111,7 @@ cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, con
 // Steps are processed in order (the host lists them top-down).  For each, the
 // fixed legs select the slice of A and B, the block finds the first k that
 // maximises A + B, and the contracted spins take the digits of k.
-constexpr int kTraceThreads = 32;   // one warp walks the records
+constexpr int kTraceThreads = 128;  // all threads copy records and build tables; warp 0 walks
 
 // (value, k) pair reduction keeping the larger value, the smaller k on ties.
 template <typename T>
@@ -2181,52 +2181,54 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceStep *__rest
       continue;
     }
     const TraceStep &st = *reinterpret_cast<const TraceStep *>(srec);
-    // one warp: fixed legs select the slices of A and B
-    int64_t pa = 0, pb = 0;
-    for (int i = lane; i < st.nfa; i += 32) {
-      int d = sst[st.fa_spin[i]];
-      if (d < 0 || d >= Q) { serr = 1; d = 0; }
-      pa += (int64_t)d * st.fa_stride[i];
-    }
-    if (st.offB >= 0)
-      for (int i = lane; i < st.nfb; i += 32) {
-        int d = sst[st.fb_spin[i]];
+    if (threadIdx.x < 32) {   // warp 0 alone walks plain records
+      // one warp: fixed legs select the slices of A and B
+      int64_t pa = 0, pb = 0;
+      for (int i = lane; i < st.nfa; i += 32) {
+        int d = sst[st.fa_spin[i]];
         if (d < 0 || d >= Q) { serr = 1; d = 0; }
-        pb += (int64_t)d * st.fb_stride[i];
+        pa += (int64_t)d * st.fa_stride[i];
       }
-    for (int o = 16; o > 0; o >>= 1) {
-      pa += __shfl_xor_sync(0xffffffffu, pa, o);
-      pb += __shfl_xor_sync(0xffffffffu, pb, o);
-    }
-    const int64_t ba = st.offA + pa, bb = st.offB + pb;
-    T best = Lim<T>::neg();
-    int bk = 0x7fffffff;
-    for (int k = lane; k < st.Ks; k += 32) {
-      int64_t oa = ba, ob = bb;
-      int r = k;
-      for (int j = st.nk - 1; j >= 0; --j) {
-        const int d = r % Q;
-        r /= Q;
-        oa += d * st.k_sA[j];
-        ob += d * st.k_sB[j];
+      if (st.offB >= 0)
+        for (int i = lane; i < st.nfb; i += 32) {
+          int d = sst[st.fb_spin[i]];
+          if (d < 0 || d >= Q) { serr = 1; d = 0; }
+          pb += (int64_t)d * st.fb_stride[i];
+        }
+      for (int o = 16; o > 0; o >>= 1) {
+        pa += __shfl_xor_sync(0xffffffffu, pa, o);
+        pb += __shfl_xor_sync(0xffffffffu, pb, o);
       }
-      T v = X[oa];
-      if (st.offB >= 0) v = v + X[ob];
-      argmax_merge(best, bk, v, k);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      T v2 = __shfl_xor_sync(0xffffffffu, best, o);
-      int k2 = __shfl_xor_sync(0xffffffffu, bk, o);
-      argmax_merge(best, bk, v2, k2);
-    }
-    if (lane == 0) {
-      int r = bk;
-      for (int j = st.nk - 1; j >= 0; --j) {
-        sst[st.k_spin[j]] = (int8_t)(r % Q);
-        r /= Q;
+      const int64_t ba = st.offA + pa, bb = st.offB + pb;
+      T best = Lim<T>::neg();
+      int bk = 0x7fffffff;
+      for (int k = lane; k < st.Ks; k += 32) {
+        int64_t oa = ba, ob = bb;
+        int r = k;
+        for (int j = st.nk - 1; j >= 0; --j) {
+          const int d = r % Q;
+          r /= Q;
+          oa += d * st.k_sA[j];
+          ob += d * st.k_sB[j];
+        }
+        T v = X[oa];
+        if (st.offB >= 0) v = v + X[ob];
+        argmax_merge(best, bk, v, k);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        T v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        int k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+        argmax_merge(best, bk, v2, k2);
+      }
+      if (lane == 0) {
+        int r = bk;
+        for (int j = st.nk - 1; j >= 0; --j) {
+          sst[st.k_spin[j]] = (int8_t)(r % Q);
+          r /= Q;
+        }
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
   for (int i = threadIdx.x; i < nspins; i += blockDim.x) state[i] = sst[i];
   if (threadIdx.x == 0 && serr) *err = 1;

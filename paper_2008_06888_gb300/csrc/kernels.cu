@@ -467,86 +467,6 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- tiled max-plus GEMM
-
-// 64 x 64 output tile per block of 256 threads, 4 x 4 per thread, k slabs of
-// 16 staged in shared memory.  Out-of-range operands read the tropical zero.
-template <typename T>
-__global__ void __launch_bounds__(256) k_gemm(const GemmParams p, const T *__restrict__ A,
-                                              const T *__restrict__ B, T *__restrict__ C,
-                                              int64_t ib) {
-  A = inst_ptr(A, ib);
-  B = inst_ptr(B, ib);
-  C = inst_ptr(C, ib);
-  constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
-  __shared__ T As[BK][BM + 4];
-  __shared__ T Bs[BK][BN + 4];
-  const int64_t mt = (p.M + BM - 1) / BM, nt = (p.N + BN - 1) / BN;
-  const int64_t tiles = p.batch * mt * nt;
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t b = t / (mt * nt);
-    const int64_t rem = t % (mt * nt);
-    const int64_t m0 = (rem / nt) * BM, n0 = (rem % nt) * BN;
-    const T *Ab = A + b * p.sAb;
-    const T *Bb = B + b * p.sBb;
-    T acc[TM][TN];
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-      for (int j = 0; j < TN; ++j) acc[i][j] = Lim<T>::neg();
-    for (int64_t k0 = 0; k0 < p.K; k0 += BK) {
-      for (int idx = tid; idx < BM * BK; idx += 256) {
-        int m, k;
-        if (p.sAm == 1) { m = idx % BM; k = idx / BM; } else { k = idx % BK; m = idx / BK; }
-        int64_t gm = m0 + m, gk = k0 + k;
-        As[k][m] = (gm < p.M && gk < p.K) ? Ab[gm * p.sAm + gk * p.sAk] : Lim<T>::neg();
-      }
-      for (int idx = tid; idx < BN * BK; idx += 256) {
-        int n, k;
-        if (p.sBn == 1) { n = idx % BN; k = idx / BN; } else { k = idx % BK; n = idx / BK; }
-        int64_t gn = n0 + n, gk = k0 + k;
-        Bs[k][n] = (gn < p.N && gk < p.K) ? Bb[gk * p.sBk + gn * p.sBn] : Lim<T>::neg();
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < BK; ++kk) {
-        T a[TM], bv[TN];
-#pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
-#pragma unroll
-        for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx * TN + j];
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-          for (int j = 0; j < TN; ++j) acc[i][j] = max(acc[i][j], a[i] + bv[j]);
-      }
-      __syncthreads();
-    }
-    T *Cb = C + b * p.sCb;
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-      for (int j = 0; j < TN; ++j) {
-        int64_t gm = m0 + ty * TM + i, gn = n0 + tx * TN + j;
-        if (gm < p.M && gn < p.N) Cb[gm * p.sCm + gn * p.sCn] = acc[i][j];
-      }
-  }
-}
-
-cudaError_t launch_gemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
-                        const Batch &bt, cudaStream_t st) {
-  int64_t tiles = p.batch * ((p.M + 63) / 64) * ((p.N + 63) / 64);
-  if (tiles == 0) return cudaSuccess;
-  dim3 blocks((unsigned)(tiles < 152 * 16 ? tiles : 152 * 16), bt.B);
-  if (dt == DT_F32)
-    k_gemm<float><<<blocks, 256, 0, st>>>(p, (const float *)A, (const float *)B, (float *)C, bt.ib);
-  else
-    k_gemm<int32_t><<<blocks, 256, 0, st>>>(p, (const int32_t *)A, (const int32_t *)B,
-                                            (int32_t *)C, bt.ib);
-  return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------- register-tiled max-plus GEMM
 //
 // 128 x 128 output tile per block of 256 threads, 8 x 8 outputs per thread,

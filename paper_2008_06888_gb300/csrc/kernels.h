@@ -27,9 +27,6 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
                         const uint64_t *nA, const uint64_t *nB, uint64_t *nC, const PrimeSet &ps,
                         const Batch &bt, cudaStream_t st);
 
-// Tiled strided batched max-plus GEMM, values only.
-cudaError_t launch_gemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
-                        const Batch &bt, cudaStream_t st);
 // Register-tiled max-plus GEMM (128 x 128 tiles, cp.async staging), values only.
 cudaError_t launch_mpgemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
                           const Batch &bt, cudaStream_t st);

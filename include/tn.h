@@ -250,7 +250,13 @@ tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev,
  *   TN_DTYPE_I32 (4-byte elements).  A is [batch][M][K] (transA = 0) or
  *   [batch][K][M] (transA = 1); B is [batch][K][N] (transB = 0) or
  *   [batch][N][K] (transB = 1); C is [batch][M][N]; all row-major, device
- *   memory owned by the caller.  Queued on cuda_stream, not waited for.
+ *   memory owned by the caller.  Queued on cuda_stream, not waited for,
+ *   except on the first call for a shape class (dtype, sizes, layout) made
+ *   outside stream capture: that call times the candidate tile
+ *   configurations on the stream (all give bit-identical C) and keeps the
+ *   fastest for later calls and for the GEMM steps of contractions.  Set
+ *   TN_NO_AUTOTUNE to skip the timing; TN_AUTOTUNE_CACHE names a file that
+ *   keeps the choices across processes.
  *   Errors: TN_EINVAL (bad sizes, NULL), TN_ECUDA (launch); tn_last_error(NULL).
  */
 tn_status tn_maxplus_gemm(int32_t dtype, int64_t batch, int64_t M, int64_t N, int64_t K,

@@ -1085,6 +1085,11 @@ tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev,
   for (int i = 0; i < TN_MAX_PRIMES; ++i) ps.c[i] = kPrimeC[i];
   auto X = [&](const Loc &l) -> void * { return l.buf < 0 ? nullptr : base + abs_off(p, l); };
   const Batch one;
+  // this call only queues work: no GEMM tile timing (it would wait on the stream)
+  struct NoTune {
+    NoTune() { set_gemm_autotune(false); }
+    ~NoTune() { set_gemm_autotune(true); }
+  } no_tune;
   for (const Op &op : p.ops) {
     cudaError_t e = cudaSuccess;
     switch (op.kind) {

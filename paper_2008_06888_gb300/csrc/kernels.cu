@@ -7,6 +7,12 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
 #include <cstdlib>
 #include <stdint.h>
 
@@ -689,28 +695,137 @@ static bool mpgemm16_ok(const GemmParams &p, const void *A, const void *B) {
          (reinterpret_cast<uintptr_t>(A) % 16) == 0 && (reinterpret_cast<uintptr_t>(B) % 16) == 0;
 }
 
-cudaError_t launch_mpgemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
-                          const Batch &bt, cudaStream_t st) {
+// ---- tile autotuner.  Candidates: staging (0: 16-byte cp.async, 1: 4-byte)
+// x resident blocks per SM (2 or 8).  Every candidate computes each output as
+// the max of the same single-rounding sums, so results are bit-identical and
+// only time decides.  A shape class is timed once, on its first launch
+// outside stream capture (its last candidate run leaves the result in C);
+// choices can persist in the file named by TN_AUTOTUNE_CACHE.
+struct GemmTile {
+  int variant, per_sm;
+};
+
+static std::mutex g_tune_mu;
+static std::map<std::string, GemmTile> g_tune;
+static bool g_tune_loaded = false;
+static thread_local bool g_tune_off = false;   // set by callers that must not wait
+
+void set_gemm_autotune(bool on) { g_tune_off = !on; }
+
+static std::string gemm_key(Dtype dt, const GemmParams &p, const Batch &bt, bool v16) {
+  char k[192];
+  std::snprintf(k, sizeof(k), "dt%d b%lld m%lld n%lld k%lld B%d ak%d bn%d v%d", (int)dt,
+                (long long)p.batch, (long long)p.M, (long long)p.N, (long long)p.K, bt.B,
+                (int)(p.sAk == 1), (int)(p.sBn == 1), (int)v16);
+  return k;
+}
+
+static void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char *path = std::getenv("TN_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE *f = std::fopen(path, "r");
+  if (!f) return;
+  char line[256];
+  while (std::fgets(line, sizeof(line), f)) {
+    char *bar = std::strchr(line, '|');
+    if (!bar) continue;
+    *bar = 0;
+    GemmTile t{};
+    if (std::sscanf(bar + 1, "%d %d", &t.variant, &t.per_sm) == 2) g_tune[line] = t;
+  }
+  std::fclose(f);
+}
+
+static void tune_store(const std::string &key, GemmTile t) {
+  const char *path = std::getenv("TN_AUTOTUNE_CACHE");
+  if (!path) return;
+  if (FILE *f = std::fopen(path, "a")) {
+    std::fprintf(f, "%s|%d %d\n", key.c_str(), t.variant, t.per_sm);
+    std::fclose(f);
+  }
+}
+
+static cudaError_t run_mpgemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
+                              const Batch &bt, cudaStream_t st, GemmTile t) {
   const int64_t tiles = p.batch * ((p.M + GBM - 1) / GBM) * ((p.N + GBN - 1) / GBN);
-  if (tiles == 0) return cudaSuccess;
-  const int64_t cap = std::max<int64_t>(1, 152 * 2 * 4 / bt.B);
+  const int64_t cap = std::max<int64_t>(1, 152 * t.per_sm / bt.B);
   dim3 blocks((unsigned)(tiles < cap ? tiles : cap), bt.B);
-  if (mpgemm16_ok(p, A, B) && bt.ib % 16 == 0 && std::getenv("TN_GEMM_SCALAR") == nullptr) {
+  if (t.variant == 0) {
     if (dt == DT_F32)
       k_mpgemm16<float><<<blocks, 256, 0, st>>>(p, (const float *)A, (const float *)B, (float *)C,
                                                 bt.ib);
     else
       k_mpgemm16<int32_t><<<blocks, 256, 0, st>>>(p, (const int32_t *)A, (const int32_t *)B,
                                                   (int32_t *)C, bt.ib);
-    return cudaGetLastError();
+  } else {
+    if (dt == DT_F32)
+      k_mpgemm<float><<<blocks, 256, 0, st>>>(p, (const float *)A, (const float *)B, (float *)C,
+                                              bt.ib);
+    else
+      k_mpgemm<int32_t><<<blocks, 256, 0, st>>>(p, (const int32_t *)A, (const int32_t *)B,
+                                                (int32_t *)C, bt.ib);
   }
-  if (dt == DT_F32)
-    k_mpgemm<float><<<blocks, 256, 0, st>>>(p, (const float *)A, (const float *)B, (float *)C,
-                                            bt.ib);
-  else
-    k_mpgemm<int32_t><<<blocks, 256, 0, st>>>(p, (const int32_t *)A, (const int32_t *)B,
-                                              (int32_t *)C, bt.ib);
   return cudaGetLastError();
+}
+
+cudaError_t launch_mpgemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
+                          const Batch &bt, cudaStream_t st) {
+  const int64_t tiles = p.batch * ((p.M + GBM - 1) / GBM) * ((p.N + GBN - 1) / GBN);
+  if (tiles == 0) return cudaSuccess;
+  const bool v16 = mpgemm16_ok(p, A, B) && bt.ib % 16 == 0 && std::getenv("TN_GEMM_SCALAR") == nullptr;
+  // a forced candidate ("variant per_sm"), e.g. for tests
+  if (const char *f = std::getenv("TN_GEMM_TILE")) {
+    GemmTile t{1, 8};
+    if (std::sscanf(f, "%d %d", &t.variant, &t.per_sm) == 2 && (t.variant == 1 || v16) &&
+        t.per_sm > 0)
+      return run_mpgemm(dt, p, A, B, C, bt, st, t);
+  }
+  const GemmTile fallback{v16 ? 0 : 1, 8};
+  const std::string key = gemm_key(dt, p, bt, v16);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return run_mpgemm(dt, p, A, B, C, bt, st, it->second);
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (g_tune_off || std::getenv("TN_NO_AUTOTUNE") || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone)
+    return run_mpgemm(dt, p, A, B, C, bt, st, fallback);
+  std::vector<GemmTile> cand;
+  for (int v = v16 ? 0 : 1; v <= 1; ++v)
+    for (int per_sm : {2, 8}) cand.push_back({v, per_sm});
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  GemmTile best = fallback;
+  float best_ms = 1e30f;
+  for (const GemmTile &t : cand) {
+    cudaError_t e = run_mpgemm(dt, p, A, B, C, bt, st, t);   // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = run_mpgemm(dt, p, A, B, C, bt, st, t);
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return e != cudaSuccess ? e : cudaGetLastError();
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tune.emplace(key, best).second) tune_store(key, best);
+  }
+  return run_mpgemm(dt, p, A, B, C, bt, st, best);
 }
 
 // Counting planes of a GEMM step: n_i[b,m,n] = sum over the k with

@@ -28,8 +28,12 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
                         const Batch &bt, cudaStream_t st);
 
 // Register-tiled max-plus GEMM (128 x 128 tiles, cp.async staging), values only.
+// The tile configuration of a shape class is chosen by timing the candidates
+// on its first launch outside stream capture (set_gemm_autotune(false) on the
+// calling thread skips that and uses the default).
 cudaError_t launch_mpgemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
                           const Batch &bt, cudaStream_t st);
+void set_gemm_autotune(bool on);
 // Residue planes of a counting GEMM whose values C were produced already.
 cudaError_t launch_gemm_count(Dtype dt, const GemmParams &p, const void *xA, const void *xB,
                               const void *xC, const uint64_t *nA, const uint64_t *nB, uint64_t *nC,

@@ -42,3 +42,43 @@ def test_maxplus_gemm_matches_definition(dtype, shape, trans):
     B.tn_maxplus_gemm(Ad, Bd, Cd, transA=ta, transB=tb)
     torch.cuda.synchronize()
     assert np.array_equal(Cd.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("tile", ["0 2", "0 8", "1 2", "1 8"])
+def test_every_tile_candidate_is_bit_identical(tile, monkeypatch):
+    """The autotuner's candidates (16- or 4-byte staging x 2 or 8 blocks per SM)
+    compute each output as the max of the same single-rounding sums."""
+    import torch
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((2, 256, 96)).astype(np.float32)
+    Bm = rng.standard_normal((2, 96, 384)).astype(np.float32)
+    ref = np.stack([S.maxplus_matmul(A[i], Bm[i]) for i in range(2)]).astype(np.float32)
+    Ad, Bd = torch.tensor(A, device="cuda"), torch.tensor(Bm, device="cuda")
+    Cd = torch.empty((2, 256, 384), dtype=torch.float32, device="cuda")
+    monkeypatch.setenv("TN_GEMM_TILE", tile)
+    B.tn_maxplus_gemm(Ad, Bd, Cd)
+    torch.cuda.synchronize()
+    assert np.array_equal(Cd.cpu().numpy(), ref)
+
+
+def test_autotuner_records_its_choice(tmp_path):
+    """A shape class is timed once; its choice lands in TN_AUTOTUNE_CACHE."""
+    import subprocess
+    import sys
+    cache = tmp_path / "tiles.txt"
+    code = (
+        "import torch, numpy as np\n"
+        "from paper_2008_06888_gb300 import binding as B\n"
+        "A = torch.randn(1, 384, 128, device='cuda'); Bm = torch.randn(1, 128, 256, device='cuda')\n"
+        "C = torch.empty(1, 384, 256, device='cuda')\n"
+        "B.tn_maxplus_gemm(A, Bm, C); torch.cuda.synchronize()\n"
+        "ref = (A[0][:, :, None] + Bm[0][None]).amax(1)\n"
+        "assert torch.equal(C[0], ref)\n")
+    env = dict(__import__("os").environ, TN_AUTOTUNE_CACHE=str(cache))
+    env.pop("TN_NO_AUTOTUNE", None)
+    subprocess.run([sys.executable, "-c", code], check=True, env=env, timeout=300,
+                   cwd=__import__("os").path.dirname(__import__("os").path.dirname(__file__)))
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and "m384 n256 k128" in lines[0]
+    variant, per_sm = map(int, lines[0].split("|")[1].split())
+    assert variant in (0, 1) and per_sm in (2, 8)

@@ -218,7 +218,8 @@ def run_reference(args):
 
 
 def run_gemm(args):
-    """Max-plus GEMM through tn_maxplus_gemm: square 4096^3 and batched shapes."""
+    """Max-plus GEMM through tn_maxplus_gemm: square 4096^3, batched shapes and the dominant
+    step shapes of the 3-regular N = 200 contraction."""
     import torch
     from paper_2008_06888_gb300 import binding as B
     torch.cuda.set_device(0)
@@ -231,7 +232,10 @@ def run_gemm(args):
     clocks = Clocks(0)
     clocks.start()
     for dt in (torch.float32, torch.int32):
-        for (bt, M, N, K) in [(1, 4096, 4096, 4096), (64, 512, 512, 512), (16, 1024, 1024, 256)]:
+        # square and batched shapes, plus the two steps that carry 99% of the
+        # multiply-adds of the 3-regular N = 200 contraction (greedy order)
+        for (bt, M, N, K) in [(1, 4096, 4096, 4096), (64, 512, 512, 512), (16, 1024, 1024, 256),
+                              (8, 131072, 1024, 512), (32, 2048, 256, 16384)]:
             if dt == torch.float32:
                 A = torch.randn(bt, M, K, device="cuda")
                 Bm = torch.randn(bt, K, N, device="cuda")

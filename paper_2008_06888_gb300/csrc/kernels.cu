@@ -2182,37 +2182,48 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceStep *__rest
   for (int i = threadIdx.x; i < nspins; i += blockDim.x) sst[i] = state[i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  // each record is copied into shared memory with one cooperative load
-  __shared__ __align__(16) unsigned long long srec[(sizeof(ChainTrace) + 7) / 8];
+  // records are copied into shared memory by all threads; the copy of record
+  // s + 1 is in flight (registers) while record s is walked
+  constexpr int kWords = (int)((sizeof(ChainTrace) + 7) / 8);
+  constexpr int kPer = (kWords + kTraceThreads - 1) / kTraceThreads;
+  __shared__ __align__(16) unsigned long long srec2[2][kWords];
+  unsigned long long tmp[kPer];
+  auto fetch = [&](int s2) {
+    const int ch = steps[s2].chain;
+    const unsigned long long *src = ch >= 0
+        ? reinterpret_cast<const unsigned long long *>(&chains[ch])
+        : reinterpret_cast<const unsigned long long *>(&steps[s2]);
+    const int words = (int)((ch >= 0 ? sizeof(ChainTrace) : sizeof(TraceStep)) / 8);
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int w = threadIdx.x + i * kTraceThreads;
+      tmp[i] = w < words ? src[w] : 0ull;
+    }
+  };
+  auto put = [&](unsigned long long *dst) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int w = threadIdx.x + i * kTraceThreads;
+      if (w < kWords) dst[w] = tmp[i];
+    }
+  };
+  if (nsteps > 0) {
+    fetch(0);
+    put(srec2[0]);
+  }
+  __syncthreads();
   for (int s = 0; s < nsteps; ++s) {
     const int chain = steps[s].chain;
-    {
-      // all loads of the record are issued before any store (one round trip)
-      const unsigned long long *src = chain >= 0
-          ? reinterpret_cast<const unsigned long long *>(&chains[chain])
-          : reinterpret_cast<const unsigned long long *>(&steps[s]);
-      const int words = (int)((chain >= 0 ? sizeof(ChainTrace) : sizeof(TraceStep)) / 8);
-      constexpr int kPer = (int)((sizeof(ChainTrace) / 8 + kTraceThreads - 1) / kTraceThreads);
-      unsigned long long tmp[kPer];
-#pragma unroll
-      for (int i = 0; i < kPer; ++i) {
-        const int w = threadIdx.x + i * kTraceThreads;
-        tmp[i] = w < words ? src[w] : 0ull;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < kPer; ++i) {
-        const int w = threadIdx.x + i * kTraceThreads;
-        if (w < words) srec[w] = tmp[i];
-      }
-      __syncthreads();
-    }
+    unsigned long long *srec = srec2[s & 1];
+    if (s + 1 < nsteps) fetch(s + 1);
     if (chain >= 0) {
       const ChainTrace &ct = *reinterpret_cast<const ChainTrace *>(srec);
       if (ct.p.mode == 1)
         trace_rchain<T>(ct, X, sst, &serr, work, &sbase[0]);
       else
         trace_chain<T, Q>(ct, X, sst, &serr, work, &sbase[0]);
+      if (s + 1 < nsteps) put(srec2[(s + 1) & 1]);
+      __syncthreads();
       continue;
     }
     const TraceStep &st = *reinterpret_cast<const TraceStep *>(srec);
@@ -2263,6 +2274,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceStep *__rest
         }
       }
     }
+    if (s + 1 < nsteps) put(srec2[(s + 1) & 1]);
     __syncthreads();
   }
   for (int i = threadIdx.x; i < nspins; i += blockDim.x) state[i] = sst[i];
@@ -2283,7 +2295,9 @@ static cudaError_t launch_trace_t(const TraceStep *d_steps, int nsteps, const Ch
                                   int *err, const Batch &bt, cudaStream_t st) {
   smem += trace_state_bytes(nspins);
   static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
+  // static shared memory (two record buffers) comes on top: raise the dynamic
+  // limit whenever a larger request arrives, not only past 48 KB
+  if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(k_trace<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

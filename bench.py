@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "tropical Gop/s & % of FP32/INT32 peak; instances/s for (E, σ*, count)"
 L = 24
 FIELD_SIGMA = 0.1
-ORDER_SEED, ORDER_RESTARTS = 1, 4096
+ORDER_SEED, ORDER_RESTARTS = 1, 16384
 WORKLOAD = (f"square{L}x{L} open Ising glass, J~N(0,1) fp32, h~N(0,0.1^2) fp32, "
             f"greedy order (seed {ORDER_SEED}, {ORDER_RESTARTS} restarts); per instance E_min "
             f"+ sigma* (checkpointed forward + argmax traceback), batched over the step's "

@@ -205,6 +205,11 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
   const bool i32 = p.outer * p.tile < (int64_t(1) << 31);
   std::ostringstream o;
   o << "#include \"chain_dev.cuh\"\n"
+    << "typedef unsigned long long U;   // two FP32 values\n"
+    << "__device__ __forceinline__ U pk2(float a, float b) { U r; asm(\"mov.b64 %0, {%1, %2};\" : \"=l\"(r) : \"f\"(a), \"f\"(b)); return r; }\n"
+    << "__device__ __forceinline__ float lo2(U x) { float a, b; asm(\"mov.b64 {%0, %1}, %2;\" : \"=f\"(a), \"=f\"(b) : \"l\"(x)); return a; }\n"
+    << "__device__ __forceinline__ float hi2(U x) { float a, b; asm(\"mov.b64 {%0, %1}, %2;\" : \"=f\"(a), \"=f\"(b) : \"l\"(x)); return b; }\n"
+    << "__device__ __forceinline__ U add2(U a, U b) { U r; asm(\"add.rn.f32x2 %0, %1, %2;\" : \"=l\"(r) : \"l\"(a), \"l\"(b)); return r; }\n"
     << "extern \"C\" __global__ void __launch_bounds__(" << NT << ", " << blocks_per_sm(RB) << ")\n"
     << name << "(const ChainParams p, const " << T << " *__restrict__ X, const " << T
     << " *__restrict__ A, " << T << " *__restrict__ C, long long ib) {\n"
@@ -267,11 +272,6 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     << "    cp_async_wait_prev();\n"
     << "    __syncwarp();\n"   // words of the tile come from other lanes
     << "    T *const sw = wstage + cur * " << S << ";\n";
-  for (int e = 0; e < E; ++e) {
-    const int sl = tile_slot(tin, 0, e);   // (c << 5) | g(c): the lane XORs in below
-    o << "    T v" << e << " = sw[" << (sl & ~31) << " + (lane ^ " << (sl & 31) << ")];\n";
-  }
-  o << "    __syncwarp();\n";   // the slot is reused for the outputs below
   auto gate_table = [&](const TGate &t, std::ostringstream &g) {
     std::ostringstream f;
     if (t.nf == 0) f << "0";
@@ -284,34 +284,126 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     if (t.kind != 1 && t.K >= 0)
       g << "      const V hi = *reinterpret_cast<const V *>(sT + " << t.toff << " + f * 8 + 4);\n";
   };
-  for (int k = 0; k < p.ntg; ++k) {
-    const TGate &t = p.tg[k];
-    std::ostringstream g;
-    g << "    {  // table gate " << k
-      << (t.kind == 0 ? ": replace" : t.kind == 2 ? ": final contraction" : ": diagonal") << "\n";
-    gate_table(t, g);
-    if (t.kind == 0 || t.kind == 2) {
-      for (int e = 0; e < E; ++e) {
-        if (e & (1 << t.J)) continue;
-        const int e1 = e | (1 << t.J);
-        const char *tb = (t.K >= 0 && ((e >> t.K) & 1)) ? "hi" : "lo";
-        if (t.kind == 0)
-          g << "      { const T a = v" << e << ", b = v" << e1 << "; v" << e << " = " << MX << "(a + "
-            << tb << ".x, b + " << tb << ".y); v" << e1 << " = " << MX << "(a + " << tb
-            << ".z, b + " << tb << ".w); }\n";
-        else
-          g << "      v" << e << " = " << MX << "(v" << e << " + " << tb << ".x, v" << e1 << " + "
-            << tb << ".y);\n";
-      }
-    } else {
-      for (int e = 0; e < E; ++e) {
-        const int x0 = t.J >= 0 ? (e >> t.J) & 1 : 0, x1 = t.K >= 0 ? (e >> t.K) & 1 : 0;
-        const char *c = x1 ? (x0 ? "w" : "z") : (x0 ? "y" : "x");
-        g << "      v" << e << " = v" << e << " + lo." << c << ";\n";
-      }
+  // FP32 chains keep their states in pairs (state e with bit P clear, and e | P)
+  // in 64-bit registers: a replace gate on another bit then does the adds of two
+  // state pairs with two-wide FP32 adds (add.rn.f32x2: each lane rounds like a
+  // scalar add, so results are unchanged) and the maxima on the halves.  P is the
+  // register leg with the fewest replace gates.
+  int P = -1;
+  if (f32 && std::getenv("TN_JIT_NO_F32X2") == nullptr) {
+    int cnt[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < p.ntg; ++k)
+      if (p.tg[k].kind != 1) cnt[p.tg[k].J]++;
+    P = 0;
+    for (int b = 1; b < RB; ++b)
+      if (cnt[b] <= cnt[P]) P = b;
+  }
+  if (P < 0) {
+    for (int e = 0; e < E; ++e) {
+      const int sl = tile_slot(tin, 0, e);   // (c << 5) | g(c): the lane XORs in below
+      o << "    T v" << e << " = sw[" << (sl & ~31) << " + (lane ^ " << (sl & 31) << ")];\n";
     }
-    g << "    }\n";
-    o << g.str();
+    o << "    __syncwarp();\n";   // the slot is reused for the outputs below
+    for (int k = 0; k < p.ntg; ++k) {
+      const TGate &t = p.tg[k];
+      std::ostringstream g;
+      g << "    {  // table gate " << k
+        << (t.kind == 0 ? ": replace" : t.kind == 2 ? ": final contraction" : ": diagonal") << "\n";
+      gate_table(t, g);
+      if (t.kind == 0 || t.kind == 2) {
+        for (int e = 0; e < E; ++e) {
+          if (e & (1 << t.J)) continue;
+          const int e1 = e | (1 << t.J);
+          const char *tb = (t.K >= 0 && ((e >> t.K) & 1)) ? "hi" : "lo";
+          if (t.kind == 0)
+            g << "      { const T a = v" << e << ", b = v" << e1 << "; v" << e << " = " << MX << "(a + "
+              << tb << ".x, b + " << tb << ".y); v" << e1 << " = " << MX << "(a + " << tb
+              << ".z, b + " << tb << ".w); }\n";
+          else
+            g << "      v" << e << " = " << MX << "(v" << e << " + " << tb << ".x, v" << e1 << " + "
+              << tb << ".y);\n";
+        }
+      } else {
+        for (int e = 0; e < E; ++e) {
+          const int x0 = t.J >= 0 ? (e >> t.J) & 1 : 0, x1 = t.K >= 0 ? (e >> t.K) & 1 : 0;
+          const char *c = x1 ? (x0 ? "w" : "z") : (x0 ? "y" : "x");
+          g << "      v" << e << " = v" << e << " + lo." << c << ";\n";
+        }
+      }
+      g << "    }\n";
+      o << g.str();
+    }
+  } else {
+    const int PM = 1 << P;
+    for (int e = 0; e < E; ++e) {
+      if (e & PM) continue;
+      const int s0 = tile_slot(tin, 0, e), s1 = tile_slot(tin, 0, e | PM);
+      o << "    U u" << e << " = pk2(sw[" << (s0 & ~31) << " + (lane ^ " << (s0 & 31) << ")], sw["
+        << (s1 & ~31) << " + (lane ^ " << (s1 & 31) << ")]);\n";
+    }
+    o << "    __syncwarp();\n";   // the slot is reused for the outputs below
+    auto tabsel = [](int k, int kdig) { return kdig ? "hi" : "lo"; };
+    for (int k = 0; k < p.ntg; ++k) {
+      const TGate &t = p.tg[k];
+      std::ostringstream g;
+      g << "    {  // table gate " << k
+        << (t.kind == 0 ? ": replace" : t.kind == 2 ? ": final contraction" : ": diagonal") << "\n";
+      gate_table(t, g);
+      const char *comp[4] = {"x", "y", "z", "w"};
+      if (t.kind != 1 && t.J == P) {
+        // the gate's own pairs are the two halves of one register
+        for (int e = 0; e < E; ++e) {
+          if (e & PM) continue;
+          const char *tb = tabsel(k, t.K >= 0 && ((e >> t.K) & 1));
+          if (t.kind == 0)
+            g << "      { const float a = lo2(u" << e << "), b = hi2(u" << e << "); u" << e
+              << " = pk2(fmaxf(a + " << tb << ".x, b + " << tb << ".y), fmaxf(a + " << tb
+              << ".z, b + " << tb << ".w)); }\n";
+          else
+            g << "      { const float a = lo2(u" << e << "), b = hi2(u" << e << "); u" << e
+              << " = pk2(fmaxf(a + " << tb << ".x, b + " << tb << ".y), 0.f); }\n";
+        }
+      } else if (t.kind != 1) {
+        // packed table constants: the P half may read the other K table
+        const int nsets = (t.K >= 0 && t.K != P) ? 2 : 1;
+        for (int set = 0; set < nsets; ++set)
+          for (int c = 0; c < (t.kind == 0 ? 4 : 2); ++c) {
+            const char *lt = t.K == P ? "lo" : tabsel(k, set);
+            const char *ht = t.K == P ? "hi" : tabsel(k, set);
+            g << "      const U T" << set << c << " = pk2(" << lt << "." << comp[c] << ", " << ht << "."
+              << comp[c] << ");\n";
+          }
+        for (int e = 0; e < E; ++e) {
+          if ((e & PM) || (e & (1 << t.J))) continue;
+          const int e1 = e | (1 << t.J);
+          const int set = (t.K >= 0 && t.K != P) ? ((e >> t.K) & 1) : 0;
+          if (t.kind == 0)
+            g << "      { const U x0 = add2(u" << e << ", T" << set << "0), y0 = add2(u" << e1 << ", T"
+              << set << "1), x1 = add2(u" << e << ", T" << set << "2), y1 = add2(u" << e1 << ", T" << set
+              << "3); u" << e << " = pk2(fmaxf(lo2(x0), lo2(y0)), fmaxf(hi2(x0), hi2(y0))); u" << e1
+              << " = pk2(fmaxf(lo2(x1), lo2(y1)), fmaxf(hi2(x1), hi2(y1))); }\n";
+          else
+            g << "      { const U x0 = add2(u" << e << ", T" << set << "0), y0 = add2(u" << e1 << ", T"
+              << set << "1); u" << e << " = pk2(fmaxf(lo2(x0), lo2(y0)), fmaxf(hi2(x0), hi2(y0))); }\n";
+        }
+      } else {
+        for (int e = 0; e < E; ++e) {
+          if (e & PM) continue;
+          auto cval = [&](int st) {
+            const int x0 = t.J >= 0 ? (st >> t.J) & 1 : 0, x1 = t.K >= 0 ? (st >> t.K) & 1 : 0;
+            return std::string("lo.") + (x1 ? (x0 ? "w" : "z") : (x0 ? "y" : "x"));
+          };
+          g << "      u" << e << " = add2(u" << e << ", pk2(" << cval(e) << ", " << cval(e | PM) << "));\n";
+        }
+      }
+      g << "    }\n";
+      o << g.str();
+    }
+    // unpack for the stores below
+    for (int e = 0; e < E; ++e) {
+      if (e & cmask) continue;
+      o << "    const T v" << e << " = " << ((e & PM) ? "hi2(u" : "lo2(u") << (e & ~PM) << ");\n";
+    }
   }
   (void)nmain;
   // outputs through the warp's tile, then whole 128-byte lines

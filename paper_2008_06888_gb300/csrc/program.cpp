@@ -103,12 +103,14 @@ static void fold_reg_chain(ChainParams &cp) {
     t.cbit[0][0] = 0;
     t.cbit[0][1] = g.kind == 0 ? 1 : -1;
     t.cbit[0][2] = t.cbit[0][3] = -1;
-    if (g.nb > 0) {
-      if (g.lsb[0] >= 0) {
-        t.K = (int8_t)g.lsb[0];
-        t.cbit[0][2] = 2;
+    // its own extra legs: a register leg takes the K slot (the builder admits at
+    // most one), a fixed leg a fixed slot
+    for (int l = 0; l < g.nb; ++l) {
+      if (g.lsb[l] >= 0) {
+        t.K = (int8_t)g.lsb[l];
+        t.cbit[0][2 + l] = 2;
       } else {
-        tg_fixed_bit(t, g.lrank[0], &t.cbit[0][2]);
+        tg_fixed_bit(t, g.lrank[l], &t.cbit[0][2 + l]);
       }
     }
     t.ncomp = 1;
@@ -613,8 +615,9 @@ struct Builder {
   bool fold = true;             // fold diagonal gates into replace tables (values only)
   int kRB = 6;                  // register legs of a register chain (4 to 6; 3 when counting)
   int tmax = 11, wlow = 5;
-  Macro open;
-  bool has_open = false;
+  // chains still accepting gates, by the tensor they currently produce; a chain
+  // is emitted when a step needs its output as a whole tensor
+  std::map<int, Macro> opens;
 
   int64_t tsize(int t) const { return ipow(q, (int)plan.legset[t].size()); }
 
@@ -676,11 +679,13 @@ struct Builder {
 
   // a step contracting one leg of the open chain's state with a small operand
   // (no new leg, one batch leg at most): the chain's last gate
-  bool try_contract(const PStep &st, int big, int small, CGate *g) {
+  // (no new leg, up to two batch legs of which at most one is a register leg of
+  // the chain -- the chain ends here, so its register legs are known)
+  bool try_contract(const Macro &m, const PStep &st, int big, int small, CGate *g) {
     if (!rank_fusion()) return false;
     const std::vector<int> &ob = order[big], &os = order[small];
     const std::vector<int> &N = (big == st.a) ? st.N : st.M;
-    if (st.K.size() != 1 || !N.empty() || st.batch.size() > 1) return false;
+    if (st.K.size() != 1 || !N.empty() || st.batch.size() > 2) return false;
     if ((int)os.size() != 1 + (int)st.batch.size()) return false;
     *g = CGate();
     g->kind = 2;
@@ -688,9 +693,15 @@ struct Builder {
     g->pos = pos_of(ob, st.K[0]);
     g->kspin = st.K[0];
     g->sBk = stride(os, st.K[0]);
-    if (!st.batch.empty()) {
-      g->bpos.push_back(pos_of(ob, st.batch[0]));
-      g->sBb[0] = stride(os, st.batch[0]);
+    for (size_t j = 0; j < st.batch.size(); ++j) {
+      g->bpos.push_back(pos_of(ob, st.batch[j]));
+      g->sBb[j] = stride(os, st.batch[j]);
+    }
+    if (g->bpos.size() == 2) {
+      Macro t = m;
+      if (pos_of(t.rpos, g->pos) < 0) t.rpos.push_back(g->pos);
+      const std::vector<int> S = reg_legs(t);
+      if (pos_of(S, g->bpos[0]) >= 0 && pos_of(S, g->bpos[1]) >= 0) return false;
     }
     return true;
   }
@@ -944,12 +955,14 @@ struct Builder {
     loc[m.out] = out;
   }
 
-  void flush_chain() {
-    if (!has_open) return;
-    emit_chain(open);
-    macros.push_back(open);
-    macro_of[open.out] = (int)macros.size() - 1;
-    has_open = false;
+  void flush_chain(int out) {
+    auto it = opens.find(out);
+    if (it == opens.end()) return;
+    Macro m = it->second;
+    opens.erase(it);
+    emit_chain(m);
+    macros.push_back(m);
+    macro_of[m.out] = (int)macros.size() - 1;
   }
 
   bool forward() {
@@ -958,44 +971,54 @@ struct Builder {
       const PStep &st = plan.steps[s];
       if (fuse && st.b >= 0) {
         CGate g;
-        if (has_open && (st.a == open.out || st.b == open.out)) {
-          int small = st.a == open.out ? st.b : st.a;
-          if (try_gate(st, open.out, small, &g) && fits(open, g)) {
-            append(open, s, g);
+        const int cur = opens.count(st.a) ? st.a : (opens.count(st.b) ? st.b : -1);
+        if (cur >= 0) {
+          const int small = st.a == cur ? st.b : st.a;
+          flush_chain(small);   // an operand must exist as a whole tensor
+          Macro &m = opens[cur];
+          if (try_gate(st, cur, small, &g) && fits(m, g)) {
+            Macro mm = m;
+            opens.erase(cur);
+            append(mm, s, g);
+            opens[mm.out] = mm;
             continue;
           }
-          if (try_contract(st, open.out, small, &g) && fits(open, g)) {
-            append(open, s, g);   // a contraction ends the chain
-            flush_chain();
+          if (try_contract(m, st, cur, small, &g) && fits(m, g)) {
+            Macro mm = m;
+            opens.erase(cur);
+            append(mm, s, g);   // a contraction ends the chain
+            opens[mm.out] = mm;
+            flush_chain(mm.out);
             continue;
           }
-          flush_chain();
+          flush_chain(cur);
         }
+        flush_chain(st.a);
+        flush_chain(st.b);
         int big = tsize(st.a) >= tsize(st.b) ? st.a : st.b;
         int small = big == st.a ? st.b : st.a;
         if (try_gate(st, big, small, &g)) {
-          flush_chain();
-          open = Macro();
-          open.chain = true;
-          open.in = open.out = big;
-          if (fits(open, g)) {
-            append(open, s, g);
-            has_open = true;
+          Macro m;
+          m.chain = true;
+          m.in = m.out = big;
+          if (fits(m, g)) {
+            append(m, s, g);
+            opens[m.out] = m;
             continue;
           }
         }
         std::vector<int> gord;
         if (try_grow(st, big, small, &g, &gord)) {
-          flush_chain();
-          open = Macro();
-          open.chain = true;
-          open.in = open.out = big;
-          append(open, s, g, &gord);
-          has_open = true;
+          Macro m;
+          m.chain = true;
+          m.in = m.out = big;
+          append(m, s, g, &gord);
+          opens[m.out] = m;
           continue;
         }
       }
-      if (has_open && (st.a == open.out || st.b == open.out)) flush_chain();
+      flush_chain(st.a);
+      if (st.b >= 0) flush_chain(st.b);
       if (!emit_step(s)) return false;
       Macro m;
       m.step = s;
@@ -1003,7 +1026,7 @@ struct Builder {
       macros.push_back(m);
       macro_of[st.c] = (int)macros.size() - 1;
     }
-    flush_chain();
+    while (!opens.empty()) flush_chain(opens.begin()->first);
     return true;
   }
 

@@ -59,7 +59,8 @@ static int check_chain(const ChainParams &p, std::mt19937_64 &rng, int *ntg_out)
         cj = g.ls;
         for (int e = 0; e < E; ++e) {
           if (e & (1 << g.ls)) continue;
-          int64_t bo = g.nb > 0 ? dig(0, e) * g.sBb[0] : 0;
+          int64_t bo = 0;
+          for (int l = 0; l < g.nb; ++l) bo += dig(l, e) * g.sBb[l];
           v[e] = std::max(v[e] + X(g.offB + bo), v[e | (1 << g.ls)] + X(g.offB + bo + g.sBk));
         }
       } else if (g.kind != 0) {

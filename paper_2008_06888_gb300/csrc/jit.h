@@ -1,7 +1,7 @@
 // jit.h -- register chains compiled at run time.
 //
 // A register chain (q = 2, values, folded table gates) is a fixed sequence of
-// table gates over the 32 register elements of a thread.  For large chains
+// table gates over the 2^RB register elements of a thread.  For large chains
 // the program builder asks for a kernel specialised to that sequence: the
 // gates, the register-leg offsets and the outer-index decoding become
 // constants, so the chain runs as straight-line code without per-gate

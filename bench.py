@@ -3,13 +3,14 @@
 
 Workload (one step): B instances of the 24x24 open square-lattice Ising spin
 glass, J ~ N(0, 1) and h ~ N(0, 0.1^2) as float32, contracted along one greedy
-order (seeded randomized greedy, 64 restarts, host-side and untimed); for each
+order (seeded randomized greedy, 16384 restarts, host-side and untimed); for each
 instance the step computes E_min (forward contraction keeping checkpoints) and
 the ground state sigma* (argmax traceback).  Couplings are resident in HBM
 before the timed region.  Metric: instances/s over all ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+  python bench.py --workload mixed|cubic|max2sat   # the other workloads (one JSON line each)
 
 Multi-GPU (torchrun): every rank contracts its own instances (weak scaling, no
 data exchange); the slowest rank's time is reported.
@@ -53,7 +54,8 @@ def parse():
     ap.add_argument("--restarts", type=int, default=ORDER_RESTARTS,
                     help="greedy restarts of the (untimed) order search")
     ap.add_argument("--quiet", action="store_true", help="print only value and kernel shares")
-    ap.add_argument("--workload", default="square24", choices=["square24", "mixed"],
+    ap.add_argument("--workload", default="square24",
+                    choices=["square24", "mixed", "cubic", "max2sat"],
                     help="mixed: batch of +-J lattices with L uniform in 8..20, E_min + count")
     ap.add_argument("--mixed-n", type=int, default=2048, help="instances of the mixed batch")
     ap.add_argument("--gemm", action="store_true",
@@ -316,6 +318,163 @@ def run_mixed(args):
         "batched_over_unbatched": (len(insts) / dt) * dt1, "clocks": clk}), flush=True)
 
 
+def roofline_of(prof, clk):
+    """Roofline entry of the kernel kind with the most device time in ``prof``."""
+    pk, how = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    launches = max(d["launches"], 1)
+    avg_ms = d["ms"] / launches
+    if KIND_BOUND[dom] == "alu":
+        achieved = 2 * d["macs"] / launches / (avg_ms / 1e3) / 1e12
+        peak = alu_peak_tops(pk.get("sm_max_mhz", 2070.0))
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": "152 SMs x 128 lanes x max clock (one lane-op per clock)"}
+    achieved = d["bytes"] / launches / (avg_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": dom,
+            "peak_source": how, "bytes_per_launch": d["bytes"] / launches,
+            "avg_launch_ms": avg_ms}
+
+
+def run_ensemble(args):
+    """Ensembles on one plan per graph, batched over coupling sets.
+
+    cubic:   6x6x6 open cubic lattice (216 spins, 540 bonds, one greedy order);
+             value = Gaussian J, E_min + sigma* per instance (tn_config_batch);
+             also +-J E_min + exact count (tn_count_batch) on the same plan.
+    max2sat: Max-2-SAT on random 3-regular graphs, N = 160 variables, 240
+             clauses with random literal signs; 8 graphs (one greedy order each)
+             x B sign patterns per graph; value = min violated clauses + exact
+             number of optimal assignments per instance (tn_count_batch); also
+             +-J Ising spin glasses on the same graphs and orders, same mode.
+    """
+    import torch
+    import instances as I
+    import paper_2008_06888_gb300 as P
+    from paper_2008_06888_gb300 import binding as B
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(2008)
+    groups = []        # (name, context object, J (B, m), h (B, n) or None, mode)
+    if args.workload == "cubic":
+        # arenas per instance at peak 2^30: ~40 GB with checkpoints, ~77 GB counting
+        Bsz = args.batch if args.batch != 48 else 4
+        Bc = max(1, Bsz // 2)
+        base = I.cubic_lattice(6, coupling="gauss", seed=1)
+        sg = P.SpinGlass(base, order="greedy", seed=ORDER_SEED, restarts=4096)
+        Jg = np.stack([I.cubic_lattice(6, coupling="gauss", seed=100 + k)["J"]
+                       for k in range(Bsz)])
+        Jp = np.stack([I.cubic_lattice(6, coupling="pm1", seed=100 + k)["J"]
+                       for k in range(Bc)])
+        groups.append(("gauss_config", sg, Jg, None, "config"))
+        groups.append(("pm_count", sg, Jp, None, "count"))
+        desc = (f"cubic 6x6x6 open Ising glass (216 spins, 540 bonds), greedy order (seed "
+                f"{ORDER_SEED}, 4096 restarts); value: J~N(0,1) fp32, h=0, E_min + sigma* per "
+                f"instance, batch {Bsz}; pm_count: +-J, E_min + exact count (3 primes + witness), "
+                f"batch {Bc}")
+    else:
+        Bsz = args.batch if args.batch != 48 else 16
+        for g in range(8):
+            sat0 = I.max2sat_regular3(160, seed=500 + g)
+            sats = [dict(sat0, clauses=np.where(rng.integers(0, 2, sat0["clauses"].shape) == 1,
+                                                -np.abs(sat0["clauses"]),
+                                                np.abs(sat0["clauses"])).astype(np.int32))
+                    for _ in range(Bsz)]
+            ms_ = P.Max2SAT(sats[0], order="greedy", seed=ORDER_SEED, restarts=1024)
+            cp = [P.Max2SAT.couplings(x) for x in sats]
+            groups.append((f"sat{g}", ms_, np.stack([c[1] for c in cp]),
+                           np.stack([c[2] for c in cp]), "count"))
+            edges = cp[0][0]
+            ising = dict(n=160, q=2, edges=edges, J=np.ones(len(edges), np.float32), h=None)
+            sg = P.SpinGlass(ising, order="greedy", seed=ORDER_SEED, restarts=1024)
+            Jp = np.where(rng.integers(0, 2, (Bsz, len(edges))) == 1, -1.0, 1.0).astype(np.float32)
+            groups.append((f"pm{g}", sg, Jp, None, "count"))
+        desc = ("Max-2-SAT on random 3-regular graphs (pairing model), N = 160 variables, 240 "
+                "clauses, literal signs uniform; 8 graphs x " + str(Bsz) + " sign patterns, one "
+                "greedy order per graph (seed 1, 1024 restarts); per instance the minimum "
+                "number of violated clauses and the exact number of optimal assignments; "
+                "pm_ising: +-J spin glasses on the same graphs, same mode")
+
+    def run(names):
+        for name, obj, J, h, mode in groups:
+            if not any(name.startswith(n) for n in names):
+                continue
+            if mode == "config":
+                B.tn_config_batch(obj.ctx, J, h, obj.n, want_sigma=True)
+            else:
+                obj.count_batch(J, h, 3, limbs_per=4)
+
+    def timed(names, profile=False):
+        objs = [g[1] for g in groups if any(g[0].startswith(n) for n in names)]
+        for o in objs:
+            B.tn_profile_reset(o.ctx)
+            B.tn_set_profiling(o.ctx, profile)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            run(names)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        prof = None
+        if profile:
+            prof = {k: {"launches": 0, "ms": 0.0, "bytes": 0.0, "macs": 0.0}
+                    for k in B.KIND_NAMES}
+            for o in objs:
+                for i, k in enumerate(B.KIND_NAMES):
+                    v = B.tn_profile_get(o.ctx, i)
+                    for f in prof[k]:
+                        prof[k][f] += v[f]
+                B.tn_set_profiling(o.ctx, False)
+        return dt, prof
+
+    main_names = ["gauss"] if args.workload == "cubic" else ["sat"]
+    other_names = ["pm"]
+    n_main = sum(g[2].shape[0] for g in groups if g[0].startswith(main_names[0]))
+    n_other = sum(g[2].shape[0] for g in groups if g[0].startswith("pm"))
+    for _ in range(args.warmup):
+        run(main_names + other_names)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    dt, _ = timed(main_names)
+    dt_o, _ = timed(other_names)
+    clk = clocks.stop()
+    dt_p, prof = timed(main_names, profile=True)
+    total_ms = sum(v["ms"] for v in prof.values())
+    # one by one: each instance of the main ensemble through the unbatched call
+    g0 = next(g for g in groups if g[0].startswith(main_names[0]))
+    name, obj, J, h, mode = g0
+    K1 = min(4, J.shape[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K1):
+        B.tn_set_couplings(obj.ctx, J[k], None if h is None else h[k])
+        if mode == "config":
+            B.tn_config(obj.ctx, obj.n)
+        else:
+            obj.count(3)
+    torch.cuda.synchronize()
+    unb = K1 / (time.perf_counter() - t0)
+    print(json.dumps({
+        "metric": METRIC, "value": n_main / dt, "unit": "instances/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.workload == "cubic" else "int32", "data": "synthetic",
+        "config": {"workload": desc, "instances_per_step": n_main,
+                   "log2_peak_elements": [round(g[1].log2_peak, 2) for g in groups
+                                          if g[0].startswith(main_names[0])][:8]},
+        ("pm_count" if args.workload == "cubic" else "pm_ising"):
+            {"value": n_other / dt_o, "unit": "instances/s", "instances_per_step": n_other},
+        "unbatched_instances_per_s": unb,
+        "roofline": roofline_of(prof, clk),
+        "kernels": {k: {"launches": v["launches"], "ms": v["ms"] / args.steps,
+                        "share": v["ms"] / max(total_ms, 1e-9)} for k, v in prof.items()},
+        "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+        "cpu_baseline": None, "clocks": clk}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -324,6 +483,8 @@ def main():
         return run_gemm(args)
     if args.workload == "mixed":
         return run_mixed(args)
+    if args.workload in ("cubic", "max2sat"):
+        return run_ensemble(args)
     import torch
     import torch.distributed as dist
 

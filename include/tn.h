@@ -73,6 +73,44 @@ tn_status tn_build(tn_ctx **out, int32_t n_spins, int32_t n_edges,
                    int32_t q, uint32_t flags);
 
 /*
+ * Max-2-SAT (App. D): counting optimal assignments of an optimisation problem
+ * on the same graph with the same kernels as the spin glass.  Literals are
+ * signed 1-based variable ids: +(i+1) is x_i, -(i+1) is NOT x_i.  The cost of
+ * an assignment is the number of violated clauses (l_u OR l_v).  Variable x_i
+ * is spin i with x_i = true <-> sigma_i = +1 (state index 0).
+ *
+ * A clause's local tensor (-1 at its one violating pair of values, 0
+ * elsewhere) equals, up to a constant, an Ising bond with coupling
+ * -u_a u_b / 4 and fields -u_a / 4, -u_b / 4 (u = +1 when the literal is
+ * false at sigma = +1, i.e. a negated literal, else -1).  Scaled by 4 these
+ * are integers, so the network runs on the exact INT32 path and
+ *   cost(x) = (E_ising(sigma) + n_clauses) / 4.
+ *
+ * tn_max2sat_couplings -- the Ising instance of a clause list (host only).
+ *   n_vars >= 1, n_clauses >= 0; lits: 2*n_clauses literals, each variable id
+ *   in 1..n_vars and the two variables of a clause distinct.  Clauses on the
+ *   same pair of variables are merged into one edge (couplings summed).
+ *   Writes *n_edges (<= n_clauses), edges (2*n_clauses capacity), J
+ *   (n_clauses capacity) and h (n_vars).  Errors: TN_EINVAL.
+ */
+tn_status tn_max2sat_couplings(int32_t n_vars, int32_t n_clauses, const int32_t *lits,
+                               int32_t *n_edges, int32_t *edges, float *J, float *h);
+
+/*
+ * tn_build_max2sat -- a context for a Max-2-SAT instance (arguments as
+ *   above, flags: TN_DTYPE_AUTO or TN_DTYPE_I32).  It behaves like a tn_build
+ *   context on the couplings of tn_max2sat_couplings, except that every
+ *   energy it returns (tn_energy, tn_config, tn_count, tn_forward, the _batch
+ *   forms and tn_batch_run) is the cost in violated clauses,
+ *   (E_ising + n_clauses) / 4; sigma = +1 means true.  Batched calls take
+ *   couplings from tn_max2sat_couplings of clause lists on the same variable
+ *   pairs.  tn_gradient and tn_energy_noalloc return TN_ESTATE on it.
+ *   Errors: TN_EINVAL as tn_max2sat_couplings.
+ */
+tn_status tn_build_max2sat(tn_ctx **out, int32_t n_vars, int32_t n_clauses,
+                           const int32_t *lits, uint32_t flags);
+
+/*
  * tn_order -- fix the pairwise contraction tree (Sec. III: the cost is
  *   exponential in the treewidth; regular lattices sweep row by row, general
  *   graphs use heuristics such as greedy).  Host only; plans the steps, the

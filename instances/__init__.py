@@ -32,6 +32,7 @@ __all__ = [
     "square_lattice", "chimera", "random_regular3", "potts_square",
     "mixed_square_batch", "planted", "ferromagnet", "instance_digest",
     "square_sweep_order", "chimera_sweep_order", "potts_planted",
+    "cubic_lattice", "cubic_edges", "max2sat_regular3", "max2sat_planted",
 ]
 
 
@@ -84,6 +85,40 @@ def square_sweep_order(L, W=None):
     """Row-by-row spin sequence of an L x W lattice (the circuit sweep of Fig. 1b)."""
     W = L if W is None else W
     return np.arange(L * W, dtype=np.int32)
+
+
+def cubic_edges(L, W=None, H=None):
+    """Open-boundary L x W x H cubic lattice; spin (x, y, z) has id (x*W + y)*H + z.
+
+    Edges are listed spin by spin in id order: the bond along z, then along y,
+    then along x (each only where the neighbour exists).
+    """
+    W = L if W is None else W
+    H = L if H is None else H
+    e = []
+    for x in range(L):
+        for y in range(W):
+            for z in range(H):
+                i = (x * W + y) * H + z
+                if z + 1 < H:
+                    e.append((i, i + 1))
+                if y + 1 < W:
+                    e.append((i, i + H))
+                if x + 1 < L:
+                    e.append((i, i + W * H))
+    return np.asarray(e, dtype=np.int32).reshape(-1, 2)
+
+
+def cubic_lattice(L, W=None, H=None, coupling="pm1", field_sigma=None, seed=0):
+    """L x W x H open cubic-lattice Ising spin glass (the 3D workload of Sec. IV)."""
+    W = L if W is None else W
+    H = L if H is None else H
+    rng = np.random.default_rng(seed)
+    edges = cubic_edges(L, W, H)
+    J = _couplings(rng, len(edges), coupling)
+    h = _fields(rng, L * W * H, field_sigma)
+    return dict(n=L * W * H, q=2, edges=edges, J=J, h=h, seed=seed,
+                name=f"cubic{L}x{W}x{H}-{coupling}" + (f"-h{field_sigma}" if h is not None else ""))
 
 
 def chimera_edges(L):
@@ -166,6 +201,39 @@ def random_regular3(N, coupling="gauss", seed=0):
                 name=f"rrg3-N{N}-{coupling}")
 
 
+def max2sat_regular3(N, seed=0):
+    """Random Max-2-SAT instance on a random 3-regular graph (App. D).
+
+    Every edge (u, v) of a pairing-model 3-regular graph on N variables is one
+    clause l_u OR l_v; each literal is negated independently with
+    probability 1/2.  Returned as a dict:
+
+        n        number of variables
+        clauses  int32 array (m, 2) of literals: +(i+1) for x_i, -(i+1) for NOT x_i
+        name, seed
+    """
+    rng = np.random.default_rng(seed)
+    edges = random_regular3_edges(N, rng)
+    neg = rng.integers(0, 2, size=edges.shape) == 1
+    lits = np.where(neg, -(edges + 1), edges + 1).astype(np.int32)
+    return dict(n=N, clauses=lits, seed=seed, name=f"max2sat-rrg3-N{N}")
+
+
+def max2sat_planted(sat, seed=0):
+    """A satisfiable variant of a Max-2-SAT instance: for a random assignment
+    tau, every clause that tau violates gets its first literal negated, so tau
+    satisfies all clauses.  Returns (instance, tau as int8 array of 0/1 with
+    1 = true)."""
+    rng = np.random.default_rng(seed)
+    tau = rng.integers(0, 2, size=sat["n"]).astype(np.int8)
+    lits = sat["clauses"].copy()
+    var = np.abs(lits) - 1
+    true_lit = np.where(lits > 0, tau[var] == 1, tau[var] == 0)
+    violated = ~true_lit[:, 0] & ~true_lit[:, 1]
+    lits[violated, 0] = -lits[violated, 0]
+    return dict(sat, clauses=lits, name=sat["name"] + "-planted"), tau
+
+
 def potts_square(L, W=None, coupling="gauss", seed=0):
     """q = 3 Potts glass on an open L x W square lattice (App. C)."""
     W = L if W is None else W
@@ -219,6 +287,10 @@ def ferromagnet(inst):
 def instance_digest(inst):
     """sha256 over the instance's arrays; pins a stored expected value to its input."""
     m = hashlib.sha256()
+    if "clauses" in inst:
+        m.update(np.int64(inst["n"]).tobytes())
+        m.update(np.ascontiguousarray(inst["clauses"], dtype=np.int32).tobytes())
+        return m.hexdigest()
     m.update(np.int64(inst["n"]).tobytes())
     m.update(np.int64(inst["q"]).tobytes())
     m.update(np.ascontiguousarray(inst["edges"], dtype=np.int32).tobytes())

@@ -112,6 +112,17 @@ def solve(inst, order=None, count=True, config=True, max_eliminations=None):
     in min-fill order.  ``max_eliminations`` stops after that many spins and
     returns only dict(eliminated=k, width=...) (used to time a bounded sample).
     """
+    return solve_factors(inst, local_tensors(inst, count), order, count, config,
+                         max_eliminations)
+
+
+def solve_factors(inst, factors, order=None, count=True, config=True, max_eliminations=None):
+    """Variable elimination over given factors (values = negative costs).
+
+    ``inst`` supplies n, q and the interaction graph (edges) for the min-fill
+    completion of ``order``; ``factors`` is a list of Factor whose counts are
+    ones (or None without counting).  Same results as ``solve``.
+    """
     n, q = inst["n"], inst["q"]
     if order is None:
         order = min_fill_order(inst)
@@ -121,7 +132,6 @@ def solve(inst, order=None, count=True, config=True, max_eliminations=None):
         raise ValueError("elimination order repeats a spin")
     order += [v for v in min_fill_order(inst) if v not in seen]
 
-    factors = local_tensors(inst, count)
     trace = []
     width = 0
     for step, v in enumerate(order):

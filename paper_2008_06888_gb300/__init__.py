@@ -6,10 +6,10 @@ traceback as a torch.autograd.Function (autograd.py).  There is no CPU
 fallback: without the built library or a CUDA device every compute call fails.
 """
 from .binding import *  # noqa: F401,F403
-from .binding import SpinGlass, TNError, lib  # noqa: F401
+from .binding import Max2SAT, SpinGlass, TNError, lib  # noqa: F401
 
 __all__ = [n for n in dir() if n.startswith("tn_") or n.startswith("TN_")] + [
-    "SpinGlass", "TNError", "lib", "TropicalEnergy"]
+    "SpinGlass", "Max2SAT", "TNError", "lib", "TropicalEnergy"]
 
 
 def __getattr__(name):

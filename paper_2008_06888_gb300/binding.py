@@ -23,6 +23,10 @@ TN_ORDER_SWEEP, TN_ORDER_GREEDY, TN_ORDER_TREE = 0, 1, 2
 _SIGS = {
     "tn_build": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                            C.c_void_p, C.c_int32, C.c_uint32]),
+    "tn_max2sat_couplings": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_int32),
+                                       C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tn_build_max2sat": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_void_p,
+                                   C.c_uint32]),
     "tn_order": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_uint64, C.c_int32,
                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "tn_leaf_count": (C.c_int32, [C.c_void_p]),
@@ -102,6 +106,31 @@ def tn_build(inst, dtype=TN_DTYPE_AUTO):
     out = C.c_void_p()
     st = lib().tn_build(C.byref(out), int(inst["n"]), len(edges), _ptr(edges), _ptr(J), _ptr(h),
                         int(inst["q"]), dtype)
+    _check(st, None)
+    return out
+
+
+def _lits(sat):
+    return np.ascontiguousarray(sat["clauses"], dtype=np.int32).reshape(-1, 2)
+
+
+def tn_max2sat_couplings(sat):
+    """(edges (k, 2), J (k,), h (n,)) of the Ising network of a Max-2-SAT instance."""
+    lits = _lits(sat)
+    m, n = len(lits), int(sat["n"])
+    edges = np.zeros((max(m, 1), 2), np.int32)
+    J = np.zeros(max(m, 1), np.float32)
+    h = np.zeros(n, np.float32)
+    ne = C.c_int32()
+    st = lib().tn_max2sat_couplings(n, m, _ptr(lits), C.byref(ne), _ptr(edges), _ptr(J), _ptr(h))
+    _check(st, None)
+    return edges[:ne.value].copy(), J[:ne.value].copy(), h
+
+
+def tn_build_max2sat(sat, dtype=TN_DTYPE_AUTO):
+    lits = _lits(sat)
+    out = C.c_void_p()
+    st = lib().tn_build_max2sat(C.byref(out), int(sat["n"]), len(lits), _ptr(lits), dtype)
     _check(st, None)
     return out
 
@@ -378,6 +407,30 @@ class SpinGlass:
         """Map tn_config output (+-1 for Ising) to state indices 0..q-1."""
         s = np.asarray(sigma, dtype=np.int64)
         return ((1 - s) // 2).astype(np.int8) if q == 2 else s.astype(np.int8)
+
+
+class Max2SAT(SpinGlass):
+    """A Max-2-SAT instance (n variables, clauses of signed 1-based literals)
+    contracted by the library; every energy is the number of violated clauses
+    and sigma = +1 means true.  The batched calls take the couplings that
+    ``couplings(sat)`` gives for clause lists on the same variable pairs."""
+
+    def __init__(self, sat, order="greedy", seq=None, seed=0, restarts=16):
+        self.n = int(sat["n"])
+        self.q = 2
+        self.m = len(tn_max2sat_couplings(sat)[0])
+        self.ctx = tn_build_max2sat(sat)
+        method = {"greedy": TN_ORDER_GREEDY, "sweep": TN_ORDER_SWEEP, "tree": TN_ORDER_TREE}[order]
+        self.log2_peak, self.log2_ops = tn_order(self.ctx, method, seq, seed, restarts)
+
+    @staticmethod
+    def couplings(sat):
+        return tn_max2sat_couplings(sat)
+
+    def assignment(self):
+        """(x as uint8 0/1 with 1 = true, min number of violated clauses)."""
+        sigma, cost = self.config()
+        return (np.asarray(sigma) > 0).astype(np.uint8), cost
 
 
 def ln_count_of(c):

@@ -62,6 +62,9 @@ struct tn_ctx {
   // host-side program of tn_energy_noalloc and the plan fingerprint it was built for
   std::unique_ptr<Program> prog_noalloc;
   uint64_t noalloc_fp = 0;
+  // energies returned = e_scale * E_ising + e_offset (Max-2-SAT contexts: the
+  // number of violated clauses; 1 and 0 otherwise)
+  double e_scale = 1.0, e_offset = 0.0;
 };
 
 static std::string g_build_err;
@@ -412,14 +415,17 @@ tn_status run_program(tn_ctx *ctx, Program &p, int op_begin = 0, int op_end = -1
 }
 
 double root_energy(const tn_ctx *ctx, const void *raw) {
+  double E;
   if (ctx->dt == DT_F32) {
     float v;
     std::memcpy(&v, raw, 4);
-    return -(double)v;
+    E = -(double)v;
+  } else {
+    int32_t v;
+    std::memcpy(&v, raw, 4);
+    E = -(double)v;
   }
-  int32_t v;
-  std::memcpy(&v, raw, 4);
-  return -(double)v;
+  return ctx->e_scale * E + ctx->e_offset;
 }
 
 // ---- exact count from residues (Garner's mixed-radix CRT)
@@ -626,6 +632,65 @@ tn_status tn_build(tn_ctx **out, int32_t n_spins, int32_t n_edges, const int32_t
   return TN_OK;
 }
 
+tn_status tn_max2sat_couplings(int32_t n_vars, int32_t n_clauses, const int32_t *lits,
+                               int32_t *n_edges, int32_t *edges, float *J, float *h) {
+  if (n_vars < 1 || n_clauses < 0 || (n_clauses > 0 && !lits) || !n_edges || !h ||
+      (n_clauses > 0 && (!edges || !J)))
+    return fail(nullptr, TN_EINVAL, "bad Max-2-SAT arguments");
+  // 4 * [clause violated] = 1 + u_a s_a + u_b s_b + u_a u_b s_a s_b with
+  // u = +1 for a negated literal (false at s = +1) and -1 otherwise, so
+  // -4 * cost = -n_clauses + sum J s s + sum h s with J = -u_a u_b, h = -u.
+  std::map<std::pair<int, int>, int> at;
+  std::vector<int> hv(n_vars, 0);
+  int ne = 0;
+  for (int c = 0; c < n_clauses; ++c) {
+    int la = lits[2 * c], lb = lits[2 * c + 1];
+    int a = std::abs(la) - 1, b = std::abs(lb) - 1;
+    if (la == 0 || lb == 0 || a >= n_vars || b >= n_vars || a == b)
+      return fail(nullptr, TN_EINVAL, "clause " + std::to_string(c) + " has a bad literal");
+    int ua = la < 0 ? 1 : -1, ub = lb < 0 ? 1 : -1;
+    hv[a] -= ua;
+    hv[b] -= ub;
+    std::pair<int, int> key(std::min(a, b), std::max(a, b));
+    auto it = at.find(key);
+    if (it == at.end()) {
+      at[key] = ne;
+      edges[2 * ne] = a;
+      edges[2 * ne + 1] = b;
+      J[ne] = (float)(-ua * ub);
+      ++ne;
+    } else {
+      J[it->second] += (float)(-ua * ub);
+    }
+  }
+  for (int i = 0; i < n_vars; ++i) h[i] = (float)hv[i];
+  *n_edges = ne;
+  return TN_OK;
+}
+
+tn_status tn_build_max2sat(tn_ctx **out, int32_t n_vars, int32_t n_clauses, const int32_t *lits,
+                           uint32_t flags) {
+  if (!out) return fail(nullptr, TN_EINVAL, "out is NULL");
+  *out = nullptr;
+  if ((flags & TN_DTYPE_MASK) == TN_DTYPE_F32)
+    return fail(nullptr, TN_EINVAL, "Max-2-SAT contexts are integral (INT32)");
+  if (n_vars < 1 || n_clauses < 0) return fail(nullptr, TN_EINVAL, "bad sizes");
+  std::vector<int32_t> edges(2 * (size_t)std::max(n_clauses, 1));
+  std::vector<float> J(std::max(n_clauses, 1)), h(n_vars);
+  int32_t ne = 0;
+  tn_status s = tn_max2sat_couplings(n_vars, n_clauses, lits, &ne, edges.data(), J.data(),
+                                     h.data());
+  if (s != TN_OK) return s;
+  tn_ctx *c = nullptr;
+  s = tn_build(&c, n_vars, ne, edges.data(), J.data(), h.data(), 2,
+               (flags & ~TN_DTYPE_MASK) | TN_DTYPE_I32);
+  if (s != TN_OK) return s;
+  c->e_scale = 0.25;
+  c->e_offset = 0.25 * (double)n_clauses;
+  *out = c;
+  return TN_OK;
+}
+
 int32_t tn_leaf_count(const tn_ctx *ctx) { return ctx ? (int32_t)ctx->net.leaves.size() : 0; }
 
 tn_status tn_order(tn_ctx *ctx, int32_t method, const int32_t *seq, int32_t seq_len,
@@ -779,6 +844,7 @@ tn_status tn_config(tn_ctx *ctx, int8_t *sigma, double *E) {
 
 tn_status tn_gradient(tn_ctx *ctx, float *dJ, float *dh, int32_t on_device) {
   if (!ctx) return TN_EINVAL;
+  if (ctx->e_scale != 1.0) return fail(ctx, TN_ESTATE, "no coupling gradient for Max-2-SAT");
   if (!ctx->have_state) return fail(ctx, TN_ESTATE, "tn_config has not run");
   const Net &n = ctx->net;
   if (on_device) {
@@ -928,6 +994,11 @@ tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limb
     mix((uint64_t)c->net.q);
     mix((uint64_t)c->dt);
     mix((uint64_t)c->net.h.empty());
+    uint64_t ab[2];
+    std::memcpy(&ab[0], &c->e_scale, 8);
+    std::memcpy(&ab[1], &c->e_offset, 8);
+    mix(ab[0]);
+    mix(ab[1]);
     for (int e = 0; e < c->net.m; ++e) mix(((uint64_t)c->net.eu[e] << 32) | (uint32_t)c->net.ev[e]);
     for (auto &st : c->plan.steps) mix(((uint64_t)(st.a + 7) << 40) ^ ((uint64_t)(st.b + 7) << 20) ^ (uint64_t)st.c);
     return f;
@@ -1047,6 +1118,7 @@ tn_status tn_plan_info(const tn_ctx *ctx, int32_t *n_steps, int32_t *n_transpose
 tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev, float *E_dev,
                             void *cuda_stream) {
   if (!ctx) return TN_EINVAL;
+  if (ctx->e_scale != 1.0) return fail(ctx, TN_ESTATE, "Max-2-SAT contexts have no noalloc path");
   if (!E_dev) return fail(ctx, TN_EINVAL, "E_dev is NULL");
   if (ctx->net.m > 0 && !J_dev) return fail(ctx, TN_EINVAL, "J_dev is NULL");
   if (!ctx->net.h.empty() && !h_dev)

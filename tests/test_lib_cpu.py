@@ -159,3 +159,39 @@ def test_no_gpu_fails_loudly():
     with pytest.raises(B.TNError) as e:
         sg.energy()
     assert e.value.status == B.TN_ECUDA
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_max2sat_couplings_reproduce_the_clause_cost(seed):
+    """cost(x) = (E_ising(sigma) + n_clauses) / 4 for every assignment, x true <-> sigma = +1
+    (E_ising by Eq. 1 in the oracle, cost from the clauses by the oracle)."""
+    import oracle
+    from oracle import max2sat as M
+    sat = I.max2sat_regular3(12, seed=seed)
+    if seed == 3:        # clauses repeated on one pair are merged into one edge
+        extra = np.array([[1, -2], [-1, -2]], np.int32)
+        sat = dict(sat, clauses=np.concatenate([sat["clauses"], extra]))
+    e, J, h = B.tn_max2sat_couplings(sat)
+    assert np.all(J == np.round(J)) and np.all(h == np.round(h))
+    inst = dict(n=sat["n"], q=2, edges=e, J=J, h=h)
+    idx = np.arange(1 << sat["n"])
+    x = (idx[:, None] >> np.arange(sat["n"])[None, :]) & 1
+    E = oracle.energies_of(inst, (1 - x).astype(np.int8))
+    assert np.array_equal((E + len(sat["clauses"])) / 4, M.cost(sat, x))
+
+
+def test_max2sat_rejects_bad_clauses():
+    for lits in ([[1, 1]], [[0, 2]], [[1, 9]], [[-3, 3]]):
+        with pytest.raises(B.TNError) as e:
+            B.tn_build_max2sat(dict(n=4, clauses=np.array(lits, np.int32)))
+        assert e.value.status == B.TN_EINVAL
+    c = B.tn_build_max2sat(I.max2sat_regular3(10, seed=0))
+    B.tn_order(c, B.TN_ORDER_GREEDY, None, 1, 4)
+    B.tn_destroy(c)
+
+
+def test_cubic_6x6x6_greedy_order_fits():
+    c = B.tn_build(I.cubic_lattice(6, coupling="gauss", seed=1))
+    pk, ops = B.tn_order(c, B.TN_ORDER_GREEDY, None, 1, 256)
+    assert pk <= 31 and ops < 39
+    B.tn_destroy(c)

@@ -75,6 +75,10 @@ def _random_small(kind, seed):
         return I.potts_square(2, 4, seed=seed)
     if kind == "potts_pm":
         return I.potts_square(3, 3, coupling="pm1", seed=seed)
+    if kind == "cubic_pm":
+        return I.cubic_lattice(2, 2, 3, coupling="pm1", seed=seed)
+    if kind == "cubic_gauss_h":
+        return I.cubic_lattice(2, 2, 3, coupling="gauss", field_sigma=0.5, seed=seed)
     if kind == "random_graph_int_h":
         n = 10
         pairs = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < 0.35]
@@ -85,7 +89,7 @@ def _random_small(kind, seed):
 
 
 KINDS = ["square_pm", "square_gauss_h", "rrg3_pm", "chimera1", "potts_gauss", "potts_pm",
-         "random_graph_int_h"]
+         "cubic_pm", "cubic_gauss_h", "random_graph_int_h"]
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -118,6 +122,7 @@ GRAPHS = {
     "square5x9_pm": lambda seed: I.square_lattice(5, 9, coupling="pm1", seed=seed),
     "chimera2": lambda seed: I.chimera(2, coupling="gauss", seed=seed),
     "rrg3_24": lambda seed: I.random_regular3(24, coupling="gauss", seed=seed),
+    "cubic4": lambda seed: I.cubic_lattice(4, coupling="gauss", seed=seed),
 }
 
 
@@ -367,3 +372,14 @@ def test_chimera_sweep_order_is_a_permutation_and_exact():
     a = O.solve(inst, order=I.chimera_sweep_order(2))
     b = O.solve(inst)
     assert (a["E"], a["count"]) == (b["E"], b["count"])
+
+
+def test_cubic_lattice_graph():
+    """Open L x W x H cubic lattice: 3LWH - WH - LH - LW bonds, degree 6 inside."""
+    e = I.cubic_edges(6)
+    assert len(e) == 3 * 216 - 3 * 36 == 540
+    assert len({tuple(sorted(x)) for x in e.tolist()}) == len(e)
+    deg = np.bincount(e.ravel(), minlength=216)
+    assert deg.max() == 6 and deg.min() == 3
+    assert deg[(1 * 6 + 1) * 6 + 1] == 6 and deg[0] == 3
+    assert len(I.cubic_edges(2, 3, 4)) == 3 * 24 - 12 - 8 - 6

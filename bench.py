@@ -349,34 +349,41 @@ def run_ensemble(args):
              x B sign patterns per graph; value = min violated clauses + exact
              number of optimal assignments per instance (tn_count_batch); also
              +-J Ising spin glasses on the same graphs and orders, same mode.
+    Graphs run one after another (their batch arenas are freed in between);
+    the reported time is the sum of the graphs' timed steps.
     """
     import torch
     import instances as I
     import paper_2008_06888_gb300 as P
     from paper_2008_06888_gb300 import binding as B
     torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
     rng = np.random.default_rng(2008)
-    groups = []        # (name, context object, J (B, m), h (B, n) or None, mode)
+
     if args.workload == "cubic":
         # arenas per instance at peak 2^30: ~40 GB with checkpoints, ~77 GB counting
         Bsz = args.batch if args.batch != 48 else 4
         Bc = max(1, Bsz // 2)
-        base = I.cubic_lattice(6, coupling="gauss", seed=1)
-        sg = P.SpinGlass(base, order="greedy", seed=ORDER_SEED, restarts=4096)
-        Jg = np.stack([I.cubic_lattice(6, coupling="gauss", seed=100 + k)["J"]
-                       for k in range(Bsz)])
-        Jp = np.stack([I.cubic_lattice(6, coupling="pm1", seed=100 + k)["J"]
-                       for k in range(Bc)])
-        groups.append(("gauss_config", sg, Jg, None, "config"))
-        groups.append(("pm_count", sg, Jp, None, "count"))
+        n_units = 1
+
+        def make_unit(g):
+            base = I.cubic_lattice(6, coupling="gauss", seed=1)
+            sg = P.SpinGlass(base, order="greedy", seed=ORDER_SEED, restarts=4096)
+            Jg = np.stack([I.cubic_lattice(6, coupling="gauss", seed=100 + k)["J"]
+                           for k in range(Bsz)])
+            Jp = np.stack([I.cubic_lattice(6, coupling="pm1", seed=100 + k)["J"]
+                           for k in range(Bc)])
+            return [sg], (sg, Jg, None, "config"), (sg, Jp, None, "count")
+
         desc = (f"cubic 6x6x6 open Ising glass (216 spins, 540 bonds), greedy order (seed "
                 f"{ORDER_SEED}, 4096 restarts); value: J~N(0,1) fp32, h=0, E_min + sigma* per "
-                f"instance, batch {Bsz}; pm_count: +-J, E_min + exact count (3 primes + witness), "
+                f"instance, batch {Bsz}; other: +-J, E_min + exact count (3 primes + witness), "
                 f"batch {Bc}")
+        other_key = "pm_count"
     else:
         Bsz = args.batch if args.batch != 48 else 16
-        for g in range(8):
+        n_units = 8
+
+        def make_unit(g):
             sat0 = I.max2sat_regular3(160, seed=500 + g)
             sats = [dict(sat0, clauses=np.where(rng.integers(0, 2, sat0["clauses"].shape) == 1,
                                                 -np.abs(sat0["clauses"]),
@@ -384,89 +391,92 @@ def run_ensemble(args):
                     for _ in range(Bsz)]
             ms_ = P.Max2SAT(sats[0], order="greedy", seed=ORDER_SEED, restarts=1024)
             cp = [P.Max2SAT.couplings(x) for x in sats]
-            groups.append((f"sat{g}", ms_, np.stack([c[1] for c in cp]),
-                           np.stack([c[2] for c in cp]), "count"))
             edges = cp[0][0]
             ising = dict(n=160, q=2, edges=edges, J=np.ones(len(edges), np.float32), h=None)
             sg = P.SpinGlass(ising, order="greedy", seed=ORDER_SEED, restarts=1024)
             Jp = np.where(rng.integers(0, 2, (Bsz, len(edges))) == 1, -1.0, 1.0).astype(np.float32)
-            groups.append((f"pm{g}", sg, Jp, None, "count"))
+            return ([ms_, sg], (ms_, np.stack([c[1] for c in cp]), np.stack([c[2] for c in cp]),
+                                "count"), (sg, Jp, None, "count"))
+
         desc = ("Max-2-SAT on random 3-regular graphs (pairing model), N = 160 variables, 240 "
                 "clauses, literal signs uniform; 8 graphs x " + str(Bsz) + " sign patterns, one "
                 "greedy order per graph (seed 1, 1024 restarts); per instance the minimum "
                 "number of violated clauses and the exact number of optimal assignments; "
-                "pm_ising: +-J spin glasses on the same graphs, same mode")
+                "other: +-J spin glasses on the same graphs, same mode")
+        other_key = "pm_ising"
 
-    def run(names):
-        for name, obj, J, h, mode in groups:
-            if not any(name.startswith(n) for n in names):
-                continue
-            if mode == "config":
-                B.tn_config_batch(obj.ctx, J, h, obj.n, want_sigma=True)
-            else:
-                obj.count_batch(J, h, 3, limbs_per=4)
+    def run(w):
+        obj, J, h, mode = w
+        if mode == "config":
+            B.tn_config_batch(obj.ctx, J, h, obj.n, want_sigma=True)
+        else:
+            obj.count_batch(J, h, 3, limbs_per=4)
 
-    def timed(names, profile=False):
-        objs = [g[1] for g in groups if any(g[0].startswith(n) for n in names)]
-        for o in objs:
-            B.tn_profile_reset(o.ctx)
-            B.tn_set_profiling(o.ctx, profile)
+    def timed(w, profile=False):
+        obj = w[0]
+        B.tn_profile_reset(obj.ctx)
+        B.tn_set_profiling(obj.ctx, profile)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            run(names)
+            run(w)
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / args.steps
-        prof = None
-        if profile:
-            prof = {k: {"launches": 0, "ms": 0.0, "bytes": 0.0, "macs": 0.0}
-                    for k in B.KIND_NAMES}
-            for o in objs:
-                for i, k in enumerate(B.KIND_NAMES):
-                    v = B.tn_profile_get(o.ctx, i)
-                    for f in prof[k]:
-                        prof[k][f] += v[f]
-                B.tn_set_profiling(o.ctx, False)
+        dt = time.perf_counter() - t0
+        prof = {k: B.tn_profile_get(obj.ctx, i) for i, k in enumerate(B.KIND_NAMES)}
+        B.tn_set_profiling(obj.ctx, False)
         return dt, prof
 
-    main_names = ["gauss"] if args.workload == "cubic" else ["sat"]
-    other_names = ["pm"]
-    n_main = sum(g[2].shape[0] for g in groups if g[0].startswith(main_names[0]))
-    n_other = sum(g[2].shape[0] for g in groups if g[0].startswith("pm"))
-    for _ in range(args.warmup):
-        run(main_names + other_names)
-    torch.cuda.synchronize()
+    prof = {k: {"launches": 0, "ms": 0.0, "bytes": 0.0, "macs": 0.0} for k in B.KIND_NAMES}
+    t_main = t_other = 0.0
+    n_main = n_other = 0
+    peaks_l2 = []
+    unb = None
     clocks = Clocks(0)
     clocks.start()
-    dt, _ = timed(main_names)
-    dt_o, _ = timed(other_names)
+    for g in range(n_units):
+        objs, wm, wo = make_unit(g)
+        peaks_l2.append(round(wm[0].log2_peak, 2))
+        for _ in range(args.warmup):
+            run(wm)
+            run(wo)
+        dt, _ = timed(wm)
+        t_main += dt
+        n_main += wm[1].shape[0] * args.steps
+        dt, _ = timed(wo)
+        t_other += dt
+        n_other += wo[1].shape[0] * args.steps
+        _, pr = timed(wm, profile=True)
+        for k, v in pr.items():
+            for f in prof[k]:
+                prof[k][f] += v[f]
+        if g == 0:
+            # one by one: instances of the first graph through the unbatched call
+            obj, J, h, mode = wm
+            K1 = min(4, J.shape[0])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(K1):
+                B.tn_set_couplings(obj.ctx, J[k], None if h is None else h[k])
+                if mode == "config":
+                    B.tn_config(obj.ctx, obj.n)
+                else:
+                    obj.count(3)
+            torch.cuda.synchronize()
+            unb = K1 / (time.perf_counter() - t0)
+        for o in objs:
+            o.close()
     clk = clocks.stop()
-    dt_p, prof = timed(main_names, profile=True)
     total_ms = sum(v["ms"] for v in prof.values())
-    # one by one: each instance of the main ensemble through the unbatched call
-    g0 = next(g for g in groups if g[0].startswith(main_names[0]))
-    name, obj, J, h, mode = g0
-    K1 = min(4, J.shape[0])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(K1):
-        B.tn_set_couplings(obj.ctx, J[k], None if h is None else h[k])
-        if mode == "config":
-            B.tn_config(obj.ctx, obj.n)
-        else:
-            obj.count(3)
-    torch.cuda.synchronize()
-    unb = K1 / (time.perf_counter() - t0)
     print(json.dumps({
-        "metric": METRIC, "value": n_main / dt, "unit": "instances/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.workload == "cubic" else "int32", "data": "synthetic",
-        "config": {"workload": desc, "instances_per_step": n_main,
-                   "log2_peak_elements": [round(g[1].log2_peak, 2) for g in groups
-                                          if g[0].startswith(main_names[0])][:8]},
-        ("pm_count" if args.workload == "cubic" else "pm_ising"):
-            {"value": n_other / dt_o, "unit": "instances/s", "instances_per_step": n_other},
+        "metric": METRIC, "value": n_main / t_main, "unit": "instances/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_main * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.workload == "cubic" else "int32",
+        "data": "synthetic",
+        "config": {"workload": desc, "instances_per_step": n_main // args.steps,
+                   "log2_peak_elements": peaks_l2},
+        other_key: {"value": n_other / t_other, "unit": "instances/s",
+                    "instances_per_step": n_other // args.steps},
         "unbatched_instances_per_s": unb,
         "roofline": roofline_of(prof, clk),
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"] / args.steps,

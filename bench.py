@@ -58,6 +58,9 @@ def parse():
                     choices=["square24", "mixed", "cubic", "max2sat"],
                     help="mixed: batch of +-J lattices with L uniform in 8..20, E_min + count")
     ap.add_argument("--mixed-n", type=int, default=2048, help="instances of the mixed batch")
+    ap.add_argument("--one-by-one-only", action="store_true",
+                    help="mixed workload: time only the one-by-one sample (run by bench.py "
+                         "itself with TN_NO_GRAPH=1 for the plain unbatched path)")
     ap.add_argument("--gemm", action="store_true",
                     help="max-plus GEMM microbenchmark (FP32 and INT32) instead of the workload")
     return ap.parse_args()
@@ -287,6 +290,21 @@ def run_mixed(args):
     sgs = [P.SpinGlass(x, order="sweep",
                        seq=I.square_sweep_order(int(round(np.sqrt(x["n"]))))) for x in insts]
     ctxs = [s.ctx for s in sgs]
+    sub = list(range(0, len(insts), max(1, len(insts) // 128)))
+
+    def one_by_one():
+        for k in sub[:4]:
+            sgs[k].count(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in sub:
+            sgs[k].count(3)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / len(sub)
+
+    if args.one_by_one_only:
+        print(json.dumps({"one_by_one_s": one_by_one(), "sample": len(sub)}), flush=True)
+        return
     for _ in range(args.warmup):
         st, E, counts, status = B.tn_batch_run(ctxs, limbs_per=4)
     torch.cuda.synchronize()
@@ -298,16 +316,36 @@ def run_mixed(args):
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / args.steps
     clk = clocks.stop()
-    # one by one (each instance its own context, same kernels, no batching)
-    sub = list(range(0, len(insts), max(1, len(insts) // 128)))
-    for k in sub[:4]:
-        sgs[k].count(3)
+    # kernel shares of one batched pass (events around every launch)
+    for c in ctxs:
+        B.tn_profile_reset(c)
+        B.tn_set_profiling(c, True)
+    B.tn_batch_run(ctxs, limbs_per=4)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in sub:
-        sgs[k].count(3)
-    torch.cuda.synchronize()
-    dt1 = (time.perf_counter() - t0) / len(sub)
+    prof = {k: {"launches": 0, "ms": 0.0, "bytes": 0.0, "macs": 0.0} for k in B.KIND_NAMES}
+    for c in ctxs:
+        for i, k in enumerate(B.KIND_NAMES):
+            v = B.tn_profile_get(c, i)
+            for f in prof[k]:
+                prof[k][f] += v[f]
+        B.tn_set_profiling(c, False)
+    total_ms = sum(v["ms"] for v in prof.values())
+    # one by one (each instance its own context, same kernels, no batching), with the
+    # launches of each call replayed from a CUDA graph ...
+    dt1 = one_by_one()
+    # ... and the plain path (every kernel launched directly): a fresh process,
+    # since graph use is fixed per process
+    plain = None
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", "mixed",
+                            "--mixed-n", str(args.mixed_n), "--one-by-one-only"],
+                           env=dict(os.environ, TN_NO_GRAPH="1"), capture_output=True,
+                           text=True, timeout=600)
+        lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+        if r.returncode == 0 and lines:
+            plain = json.loads(lines[-1])["one_by_one_s"]
+    except Exception:
+        plain = None
     ok = int(np.sum(status == 0))
     print(json.dumps({
         "metric": METRIC, "value": len(insts) / dt, "unit": "instances/s",
@@ -315,7 +353,13 @@ def run_mixed(args):
                     f"(3 primes + witness), grouped batches through tn_batch_run",
         "ms_per_batch": dt * 1e3, "instances_ok": ok,
         "unbatched_instances_per_s": 1.0 / dt1, "unbatched_sample": len(sub),
-        "batched_over_unbatched": (len(insts) / dt) * dt1, "clocks": clk}), flush=True)
+        "batched_over_unbatched": (len(insts) / dt) * dt1,
+        "unbatched_plain_instances_per_s": None if plain is None else 1.0 / plain,
+        "batched_over_unbatched_plain": None if plain is None else (len(insts) / dt) * plain,
+        "roofline": roofline_of(prof, clk),
+        "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
+                        "share": v["ms"] / max(total_ms, 1e-9)} for k, v in prof.items()},
+        "clocks": clk}), flush=True)
 
 
 def roofline_of(prof, clk):

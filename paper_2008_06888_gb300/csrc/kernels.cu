@@ -377,8 +377,9 @@ static bool gate2_form(const GateParams &p, const void *A, const void *B, const 
   if (p.P > 0 || p.outer < 4 || (p.outer & 3)) return false;
   if (!((p.Ks == 1 || p.Ks == 2) && (p.Ns == 1 || p.Ns == 2))) return false;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(C)) % 16 ||
-      (ib * (int64_t)elem) % 16)
+      ib % 16)
     return false;
+  (void)elem;
   (void)B;
   *g = Gate2{};
   g->pk = 0;
@@ -407,6 +408,181 @@ static bool gate2_form(const GateParams &p, const void *A, const void *B, const 
     js *= p.seg_size[s];
   }
   return js == p.outer;
+}
+
+// Counting form of k_gate2: the same index map, with the P residue planes of
+// every element moved alongside its value (two 16-byte accesses per plane for
+// four outer indices).  Per output the terms are taken in k order: the first
+// term and every larger one replace (value, counts), an equal one adds its
+// counts mod p -- the rule of k_gate, so the results are identical.
+template <typename T, int KS, int NS, int P>
+__global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 g,
+                                                const T *__restrict__ A, const T *__restrict__ B,
+                                                T *__restrict__ C,
+                                                const uint64_t *__restrict__ nA,
+                                                const uint64_t *__restrict__ nB,
+                                                uint64_t *__restrict__ nC, const PrimeSet ps,
+                                                int64_t ib) {
+  typedef typename Vec4<T>::t V;
+  A = inst_ptr(A, ib);
+  C = inst_ptr(C, ib);
+  nA = inst_ptr(nA, ib);
+  nC = inst_ptr(nC, ib);
+  if (p.hasB) {
+    B = inst_ptr(B, ib);
+    nB = inst_ptr(nB, ib);
+  }
+  __shared__ T sBt[16];            // index: bd0 | bd1 << 1 | k << 2 | n << 3
+  __shared__ uint64_t sBn[P][16];
+  const bool mulB = p.hasB && !p.unitB;
+  if (threadIdx.x < 16) {
+    const int i = threadIdx.x, b0 = i & 1, b1 = (i >> 1) & 1, k = (i >> 2) & 1, n = (i >> 3) & 1;
+    const bool ok = p.hasB && k < KS && n < NS && (b0 == 0 || g.nbd > 0) && (b1 == 0 || g.nbd > 1);
+    const int64_t off = ok ? p.kB[k] + p.nB[n] + b0 * g.sb[0] + b1 * g.sb[1] : 0;
+    sBt[i] = ok ? B[off] : T(0);
+#pragma unroll
+    for (int r = 0; r < P; ++r) sBn[r][i] = (ok && mulB) ? nB[r * p.planeB + off] : 1ull;
+  }
+  __syncthreads();
+  const int pb0 = g.nbd > 0 ? g.pb[0] : 62, pb1 = g.nbd > 1 ? g.pb[1] : 62;
+  const int pk = g.pk;
+  const int64_t nq = p.outer >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nq; t += stride) {
+    const int64_t j0 = t << 2;
+    T a[KS][4];
+    uint64_t na[P][KS][4];
+    if (KS == 1 || pk >= 2) {
+      int64_t base = j0;
+      if (KS == 2) {
+        const int64_t lo = j0 & ((int64_t(1) << pk) - 1);
+        base = ((j0 >> pk) << (pk + 1)) | lo;
+      }
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int64_t e = base + ((int64_t)k << pk);
+        const V v = *reinterpret_cast<const V *>(A + e);
+        a[k][0] = v.x; a[k][1] = v.y; a[k][2] = v.z; a[k][3] = v.w;
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+          const ulonglong2 c0 = *reinterpret_cast<const ulonglong2 *>(nA + r * p.planeA + e);
+          const ulonglong2 c1 = *reinterpret_cast<const ulonglong2 *>(nA + r * p.planeA + e + 2);
+          na[r][k][0] = c0.x; na[r][k][1] = c0.y; na[r][k][2] = c1.x; na[r][k][3] = c1.y;
+        }
+      }
+    } else {
+      // the contracted leg is one of the two lowest bits: 8 contiguous elements
+      const V v0 = *reinterpret_cast<const V *>(A + 2 * j0);
+      const V v1 = *reinterpret_cast<const V *>(A + 2 * j0 + 4);
+      const T blk[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4)
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+          a[k][q4] = pk == 0 ? blk[2 * q4 + k] : blk[((q4 >> 1) << 2) | (k << 1) | (q4 & 1)];
+#pragma unroll
+      for (int r = 0; r < P; ++r) {
+        uint64_t cb[8];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(nA + r * p.planeA + 2 * j0 + 2 * h);
+          cb[2 * h] = c.x;
+          cb[2 * h + 1] = c.y;
+        }
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4)
+#pragma unroll
+          for (int k = 0; k < KS; ++k)
+            na[r][k][q4] = pk == 0 ? cb[2 * q4 + k] : cb[((q4 >> 1) << 2) | (k << 1) | (q4 & 1)];
+      }
+    }
+    T out[NS][4];
+    uint64_t cout[P][NS][4];
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      const int64_t j = j0 + q4;
+      const int bd = (int)((j >> pb0) & 1) | ((int)((j >> pb1) & 1) << 1);
+#pragma unroll
+      for (int n = 0; n < NS; ++n) {
+        T best = a[0][q4] + sBt[bd | (n << 3)];
+        uint64_t cnt[P];
+#pragma unroll
+        for (int r = 0; r < P; ++r)
+          cnt[r] = mulB ? mulmod61(na[r][0][q4], sBn[r][bd | (n << 3)], ps.c[r]) : na[r][0][q4];
+#pragma unroll
+        for (int k = 1; k < KS; ++k) {
+          const int bi = bd | (k << 2) | (n << 3);
+          const T v = a[k][q4] + sBt[bi];
+          if (v >= best) {
+            const bool gt = v > best;
+#pragma unroll
+            for (int r = 0; r < P; ++r) {
+              const uint64_t tr =
+                  mulB ? mulmod61(na[r][k][q4], sBn[r][bi], ps.c[r]) : na[r][k][q4];
+              cnt[r] = gt ? tr : addmod61(cnt[r], tr, ps.c[r]);
+            }
+            best = gt ? v : best;
+          }
+        }
+        out[n][q4] = best;
+#pragma unroll
+        for (int r = 0; r < P; ++r) cout[r][n][q4] = cnt[r];
+      }
+    }
+    // C and its planes: new leg innermost, so the 4 * NS outputs are contiguous
+#pragma unroll
+    for (int h = 0; h < NS; ++h) {
+      const int q0 = 4 * h;   // flat output index f = NS * q4 + n covers [q0, q0 + 4)
+      T o4[4];
+      uint64_t c4[P][4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int f = q0 + e, q4 = f / NS, n = f % NS;
+        o4[e] = out[n][q4];
+#pragma unroll
+        for (int r = 0; r < P; ++r) c4[r][e] = cout[r][n][q4];
+      }
+      V v;
+      v.x = o4[0]; v.y = o4[1]; v.z = o4[2]; v.w = o4[3];
+      *reinterpret_cast<V *>(C + NS * j0 + q0) = v;
+#pragma unroll
+      for (int r = 0; r < P; ++r) {
+        uint64_t *dst = nC + r * p.planeC + NS * j0 + q0;
+        *reinterpret_cast<ulonglong2 *>(dst) = make_ulonglong2(c4[r][0], c4[r][1]);
+        *reinterpret_cast<ulonglong2 *>(dst + 2) = make_ulonglong2(c4[r][2], c4[r][3]);
+      }
+    }
+  }
+}
+
+template <typename T>
+static bool launch_gate2c(const GateParams &p, const T *A, const T *B, T *C, const uint64_t *nA,
+                          const uint64_t *nB, uint64_t *nC, const PrimeSet &ps, const Batch &bt,
+                          cudaStream_t st) {
+  if (p.P != 4 || std::getenv("TN_NO_GATE2")) return false;
+  GateParams q = p;
+  q.P = 0;   // gate2_form checks the value layout; the planes share it
+  Gate2 g;
+  if (!gate2_form(q, A, B, C, bt.ib, sizeof(T), &g)) return false;
+  if ((reinterpret_cast<uintptr_t>(nA) | reinterpret_cast<uintptr_t>(nC)) % 16 ||
+      (p.planeA | p.planeC) & 1)
+    return false;
+  const int64_t nq = p.outer >> 2;
+  int64_t blocks = (nq + 255) / 256;
+  const int64_t cap = std::max<int64_t>(1, 152 * 8 / bt.B);
+  if (blocks > cap) blocks = cap;
+  dim3 grid((unsigned)blocks, bt.B);
+#define TN_G2C(KS_, NS_)                                                                   \
+  if (p.Ks == KS_ && p.Ns == NS_) {                                                       \
+    k_gate2c<T, KS_, NS_, 4><<<grid, 256, 0, st>>>(p, g, A, B, C, nA, nB, nC, ps, bt.ib); \
+    return true;                                                                          \
+  }
+  TN_G2C(1, 1)
+  TN_G2C(1, 2)
+  TN_G2C(2, 1)
+  TN_G2C(2, 2)
+#undef TN_G2C
+  return false;
 }
 
 template <typename T>
@@ -453,6 +629,13 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
                           : launch_gate_t<int32_t>(p, (const int32_t *)xA, (const int32_t *)xB,
                                                    (int32_t *)xC, b2, threads, bt.ib, st);
     if (done) return cudaGetLastError();
+  } else {
+    const bool streamed =
+        dt == DT_F32 ? launch_gate2c<float>(p, (const float *)xA, (const float *)xB, (float *)xC,
+                                            nA, nB, nC, ps, bt, st)
+                     : launch_gate2c<int32_t>(p, (const int32_t *)xA, (const int32_t *)xB,
+                                              (int32_t *)xC, nA, nB, nC, ps, bt, st);
+    if (streamed) return cudaGetLastError();
   }
   if (dt == DT_F32) {
     if (cnt)

@@ -149,3 +149,23 @@ def test_max2sat_refuses_gradient():
     with pytest.raises(B.TNError) as e:
         ms.gradient()
     assert e.value.status == B.TN_ESTATE
+
+
+@pytest.mark.parametrize("kind", ["sat", "square_pm"])
+def test_streaming_count_gates_match_generic(kind, monkeypatch):
+    """Counting gate steps in the streaming q = 2 form (k_gate2c) give the same
+    energies and counts as the generic gate kernel (TN_NO_GATE2)."""
+    def run():
+        if kind == "sat":
+            sat = I.max2sat_regular3(120, seed=6)
+            o = P.Max2SAT(sat, order="greedy", seed=2, restarts=64)
+        else:
+            o = P.SpinGlass(I.square_lattice(14, coupling="pm1", seed=3), order="greedy",
+                            seed=2, restarts=64)
+        c, ln, E = o.count(3)
+        o.close()
+        return E, c
+    a = run()
+    monkeypatch.setenv("TN_NO_GATE2", "1")
+    b = run()
+    assert a == b

@@ -196,6 +196,26 @@ tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_li
                    double *ln_count, double *E);
 
 /*
+ * tn_sample -- n_samples ground states drawn uniformly at random (Sec. III:
+ *   fix the spins one at a time in `order`, each with its conditional
+ *   probability of being in a ground state given the spins fixed before it).
+ *   The conditional probabilities are exact ratios of degeneracy counts: a
+ *   unit field on each fixed spin selects, among the ground states, those
+ *   that agree with it, and tn_count_batch counts them (3 primes + witness),
+ *   two candidates per sample and step, 16 samples per batch; n_spins steps.
+ *   order: n_spins distinct spin ids, or NULL for 0..n_spins-1.  seed: sample
+ *   s draws from a counter-based generator keyed by (seed, s, step), so the
+ *   result does not depend on n_samples.  sigma: n_samples * n_spins values
+ *   +-1, sample-major (host).  Requires tn_order, q == 2, an INT32 context
+ *   (integral J and h: exact ties), couplings last set from the host.
+ *   Errors: TN_EINVAL (arguments, q, dtype), TN_ESTATE (no order; counts that
+ *   no ground state extends), TN_EOVERFLOW (a count beyond the primes),
+ *   TN_ENOMEM / TN_ECUDA as tn_count_batch.
+ */
+tn_status tn_sample(tn_ctx *ctx, int32_t n_samples, uint64_t seed, const int32_t *order,
+                    int8_t *sigma);
+
+/*
  * Batches on one context: B coupling sets on the context's graph and order
  * (many disorder instances of one lattice).  Every kernel of the plan is
  * launched once for all B instances (instance = one grid dimension, each with

@@ -27,6 +27,7 @@ _SIGS = {
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "tn_build_max2sat": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_void_p,
                                    C.c_uint32]),
+    "tn_sample": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p]),
     "tn_order": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_uint64, C.c_int32,
                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "tn_leaf_count": (C.c_int32, [C.c_void_p]),
@@ -133,6 +134,14 @@ def tn_build_max2sat(sat, dtype=TN_DTYPE_AUTO):
     st = lib().tn_build_max2sat(C.byref(out), int(sat["n"]), len(lits), _ptr(lits), dtype)
     _check(st, None)
     return out
+
+
+def tn_sample(ctx, n_spins, n_samples, seed=0, order=None):
+    """(n_samples, n_spins) int8 array of ground states (+-1), drawn uniformly."""
+    sigma = np.zeros((max(n_samples, 1), n_spins), np.int8)
+    o = None if order is None else np.ascontiguousarray(order, dtype=np.int32).ravel()
+    _check(lib().tn_sample(ctx, n_samples, seed, _ptr(o), _ptr(sigma)), ctx)
+    return sigma[:n_samples]
 
 
 def tn_order(ctx, method=TN_ORDER_GREEDY, seq=None, seed=0, restarts=16):
@@ -369,6 +378,10 @@ class SpinGlass:
 
     def count(self, n_primes=3):
         return tn_count(self.ctx, n_primes)
+
+    def sample(self, n_samples, seed=0, order=None):
+        """Ground states drawn uniformly (+-1 per spin), by conditional counts."""
+        return tn_sample(self.ctx, self.n, n_samples, seed, order)
 
     def energy_batch(self, J, h=None):
         return tn_energy_batch(self.ctx, J, h)

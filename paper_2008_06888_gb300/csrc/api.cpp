@@ -18,6 +18,7 @@
 #include "planner.h"
 #include "program.h"
 #include "jit.h"
+#include "sampler.h"
 
 using namespace tn;
 
@@ -65,6 +66,7 @@ struct tn_ctx {
   // energies returned = e_scale * E_ising + e_offset (Max-2-SAT contexts: the
   // number of violated clauses; 1 and 0 otherwise)
   double e_scale = 1.0, e_offset = 0.0;
+  bool host_couplings = true;   // net.J / net.h hold the couplings in use
 };
 
 static std::string g_build_err;
@@ -760,9 +762,11 @@ tn_status tn_set_couplings(tn_ctx *ctx, const float *J, const float *h, int32_t 
     n.J = nj;
     n.h = nh;
     ctx->couplings_dirty = true;
+    ctx->host_couplings = true;
     return TN_OK;
   }
   tn_status s = ensure_device(ctx);
+  ctx->host_couplings = false;
   if (s != TN_OK) return s;
   if (J && n.m)
     CK(cudaMemcpyAsync(ctx->d_J, J, n.m * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1218,6 +1222,75 @@ tn_status tn_maxplus_gemm(int32_t dtype, int64_t batch, int64_t M, int64_t N, in
                                 (cudaStream_t)cuda_stream);
   if (e != cudaSuccess)
     return fail(nullptr, TN_ECUDA, std::string("tn_maxplus_gemm: ") + cudaGetErrorString(e));
+  return TN_OK;
+}
+
+tn_status tn_sample(tn_ctx *ctx, int32_t n_samples, uint64_t seed, const int32_t *order,
+                    int8_t *sigma) {
+  if (!ctx) return TN_EINVAL;
+  if (n_samples < 0 || (n_samples > 0 && !sigma)) return fail(ctx, TN_EINVAL, "bad sample buffer");
+  if (!ctx->ordered) return fail(ctx, TN_ESTATE, "tn_order has not run");
+  const Net &n = ctx->net;
+  if (n.q != 2) return fail(ctx, TN_EINVAL, "sampling is Ising only (q == 2)");
+  if (ctx->dt != DT_I32)
+    return fail(ctx, TN_EINVAL, "sampling needs integral couplings (an INT32 context)");
+  if (!ctx->host_couplings)
+    return fail(ctx, TN_ESTATE, "couplings were last set on the device; set them from the host");
+  std::vector<int> ord(n.n);
+  if (order) {
+    std::vector<char> seen(n.n, 0);
+    for (int i = 0; i < n.n; ++i) {
+      const int v = order[i];
+      if (v < 0 || v >= n.n || seen[v]) return fail(ctx, TN_EINVAL, "order is not a permutation");
+      seen[v] = 1;
+      ord[i] = v;
+    }
+  } else {
+    for (int i = 0; i < n.n; ++i) ord[i] = i;
+  }
+  // pinned instances: |values| stay below the INT32 sentinel margin
+  double mag = n.n + 1.0;
+  for (float x : n.J) mag += std::fabs(x);
+  for (float x : n.h) mag += std::fabs(x);
+  if (mag >= (double)(1 << 29)) return fail(ctx, TN_EINVAL, "couplings too large to pin exactly");
+  // the same graph and plan, with fields on every spin (zeros if it has none)
+  std::vector<int32_t> e(2 * (size_t)std::max(n.m, 1));
+  for (int k = 0; k < n.m; ++k) {
+    e[2 * k] = n.eu[k];
+    e[2 * k + 1] = n.ev[k];
+  }
+  std::vector<float> h0 = n.h.empty() ? std::vector<float>(n.n, 0.f) : n.h;
+  tn_ctx *pc = nullptr;
+  tn_status s = tn_build(&pc, n.n, n.m, e.data(), n.J.data(), h0.data(), 2, TN_DTYPE_I32);
+  if (s != TN_OK) return fail(ctx, s, "sampler: " + g_build_err);
+  std::unique_ptr<tn_ctx, void (*)(tn_ctx *)> guard(pc, tn_destroy);
+  pc->plan = ctx->plan;
+  pc->ordered = true;
+  pc->stream = ctx->stream;
+  std::vector<float> Jrep;
+  CountFn fn = [&](const std::vector<float> &h, int K, std::vector<double> *E,
+                   std::vector<Big> *cnt) -> int {
+    Jrep.assign((size_t)std::max(1, K * n.m), 0.f);
+    for (int k = 0; k < K; ++k) std::copy(n.J.begin(), n.J.end(), Jrep.begin() + (size_t)k * n.m);
+    std::vector<uint64_t> limbs((size_t)K * 3);
+    std::vector<int32_t> st(K, 0);
+    E->assign(K, 0.0);
+    tn_status r = tn_count_batch(pc, K, Jrep.data(), h.data(), 0, 3, limbs.data(), 3, E->data(),
+                                 st.data());
+    if (r != TN_OK) {
+      fail(ctx, r, "sampler: " + pc->err);
+      return (int)r;
+    }
+    cnt->assign(K, Big());
+    for (int k = 0; k < K; ++k) (*cnt)[k].assign(limbs.begin() + 3 * k, limbs.begin() + 3 * k + 3);
+    return 0;
+  };
+  std::vector<int8_t> out;
+  std::string err;
+  const int rc = sample_ground_states(n.n, n_samples, ord, h0, seed, 16, fn, &out, &err);
+  if (rc == -1) return fail(ctx, TN_ESTATE, err);
+  if (rc) return (tn_status)rc;
+  std::copy(out.begin(), out.end(), sigma);
   return TN_OK;
 }
 

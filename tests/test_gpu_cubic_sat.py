@@ -169,3 +169,50 @@ def test_streaming_count_gates_match_generic(kind, monkeypatch):
     monkeypatch.setenv("TN_NO_GATE2", "1")
     b = run()
     assert a == b
+
+
+# ------------------------------------------------------------ ground-state sampling
+
+def _degenerate_square(min_gs=6, max_gs=40):
+    for seed in range(1, 200):
+        inst = I.square_lattice(4, coupling="pm1", seed=seed)
+        b = O.brute_force(inst)
+        if min_gs <= b["count"] <= max_gs:
+            return inst, b
+    raise RuntimeError("no degenerate instance found")
+
+
+def test_sample_draws_every_ground_state_uniformly():
+    """Sec. III: spins fixed one at a time with their conditional probabilities
+    (exact count ratios) give uniform samples of the ground states."""
+    inst, b = _degenerate_square()
+    sg = P.SpinGlass(inst, order="greedy", seed=1, restarts=16)
+    S = 40 * b["count"]
+    sig = sg.sample(S, seed=7)
+    gs = {tuple(x) for x in b["states"].tolist()}
+    freq = {}
+    for row in sig:
+        st = tuple(((1 - row.astype(np.int64)) // 2).tolist())
+        assert st in gs
+        freq[st] = freq.get(st, 0) + 1
+    assert len(freq) == len(gs)
+    expct = S / len(gs)
+    chi2 = sum((freq[g] - expct) ** 2 / expct for g in gs)
+    dof = len(gs) - 1
+    assert chi2 <= dof + 6 * np.sqrt(2 * dof) + 1, (chi2, dof)
+    # the same seed gives the same samples, another order still ground states
+    assert np.array_equal(sg.sample(S, seed=7)[:10], sig[:10])
+    other = sg.sample(20, seed=8, order=np.arange(inst["n"])[::-1])
+    for row in other:
+        assert O.energy(inst, ((1 - row.astype(np.int64)) // 2).astype(np.int8)) == b["E"]
+
+
+def test_sample_max2sat_optimal_assignments():
+    sat = I.max2sat_regular3(18, seed=2)
+    o = M.brute_force(sat)
+    ms = P.Max2SAT(sat, order="greedy", seed=1, restarts=16)
+    sig = ms.sample(30, seed=3)
+    xs = {tuple((row > 0).astype(int).tolist()) for row in sig}
+    for x in xs:
+        assert M.cost(sat, np.array(x))[0] == o["E"]
+    assert len(xs) > 1 if o["count"] > 1 else len(xs) == 1

@@ -4,7 +4,8 @@ planner and program builder (no GPU):
 - tests/host/fold_check.cpp: the folded table gates of every register chain
   evaluate exactly like the original gate lists;
 - tests/host/tile_check.cpp: the coalesced tile copies of compiled chains put
-  every element where its owning thread reads it, without bank conflicts."""
+  every element where its owning thread reads it, without bank conflicts;
+- tests/host/sample_check.cpp: the ground-state sampler with brute-force counts."""
 import os
 import shutil
 import subprocess
@@ -57,3 +58,18 @@ def test_tile_copies_of_compiled_chains(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=240, env=env)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.split()[-3:] == ["0", "bank_conflicts", "0"] or "wrong 0 bank_conflicts 0" in r.stdout
+
+
+@pytest.mark.timeout(300)
+def test_ground_state_sampler_with_brute_force_counts(tmp_path):
+    """tests/host/sample_check.cpp: the conditional-count sampler (Sec. III) draws
+    only ground states, uniformly, independent of its batch size."""
+    if shutil.which("g++") is None:
+        pytest.skip("g++ missing")
+    exe = str(tmp_path / "sample_check")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I", CSRC,
+                    os.path.join(ROOT, "tests", "host", "sample_check.cpp"),
+                    os.path.join(CSRC, "sampler.cpp"), "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=240)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip().splitlines()[-1].endswith("bad 0")

@@ -195,3 +195,27 @@ def test_cubic_6x6x6_greedy_order_fits():
     pk, ops = B.tn_order(c, B.TN_ORDER_GREEDY, None, 1, 256)
     assert pk <= 31 and ops < 39
     B.tn_destroy(c)
+
+
+def test_sample_argument_checks_before_any_device_work():
+    g = B.tn_build(I.square_lattice(3, coupling="gauss", seed=1))
+    with pytest.raises(B.TNError) as e:
+        B.tn_sample(g, 9, 2)
+    assert e.value.status == B.TN_ESTATE          # no order yet
+    B.tn_order(g, B.TN_ORDER_GREEDY, None, 1, 4)
+    with pytest.raises(B.TNError) as e:
+        B.tn_sample(g, 9, 2)
+    assert e.value.status == B.TN_EINVAL          # float couplings: no exact ties
+    B.tn_destroy(g)
+    c = B.tn_build(I.square_lattice(3, coupling="pm1", seed=1))
+    B.tn_order(c, B.TN_ORDER_GREEDY, None, 1, 4)
+    with pytest.raises(B.TNError) as e:
+        B.tn_sample(c, 9, 2, order=[0, 1, 2, 3, 4, 5, 6, 7, 7])
+    assert e.value.status == B.TN_EINVAL          # not a permutation
+    B.tn_destroy(c)
+    p = B.tn_build(I.potts_square(2, coupling="pm1", seed=1))
+    B.tn_order(p, B.TN_ORDER_GREEDY, None, 1, 4)
+    with pytest.raises(B.TNError) as e:
+        B.tn_sample(p, 4, 2)
+    assert e.value.status == B.TN_EINVAL          # Ising only
+    B.tn_destroy(p)

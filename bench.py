@@ -10,7 +10,7 @@ before the timed region.  Metric: instances/s over all ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
-  python bench.py --workload mixed|cubic|max2sat   # the other workloads (one JSON line each)
+  python bench.py --workload mixed|cubic|max2sat|sample   # the other workloads (one JSON line each)
 
 Multi-GPU (torchrun): every rank contracts its own instances (weak scaling, no
 data exchange); the slowest rank's time is reported.
@@ -55,7 +55,7 @@ def parse():
                     help="greedy restarts of the (untimed) order search")
     ap.add_argument("--quiet", action="store_true", help="print only value and kernel shares")
     ap.add_argument("--workload", default="square24",
-                    choices=["square24", "mixed", "cubic", "max2sat"],
+                    choices=["square24", "mixed", "cubic", "max2sat", "sample"],
                     help="mixed: batch of +-J lattices with L uniform in 8..20, E_min + count")
     ap.add_argument("--mixed-n", type=int, default=2048, help="instances of the mixed batch")
     ap.add_argument("--one-by-one-only", action="store_true",
@@ -529,6 +529,38 @@ def run_ensemble(args):
         "cpu_baseline": None, "clocks": clk}), flush=True)
 
 
+def run_sample(args):
+    """Uniform ground-state samples (tn_sample) of a degenerate 16x16 +-J lattice:
+    256 steps, each one batched count of 2 x 16 pinned instances."""
+    import torch
+    import instances as I
+    import paper_2008_06888_gb300 as P
+    torch.cuda.set_device(0)
+    inst = I.square_lattice(16, coupling="pm1", seed=3)
+    sg = P.SpinGlass(inst, order="greedy", seed=ORDER_SEED, restarts=1024)
+    count, ln, E = sg.count(3)
+    sg.sample(2, seed=0)            # builds the pinned program and its graphs
+    S = 16
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(max(1, args.steps)):
+        sig = sg.sample(S, seed=100 + k)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    distinct = len({row.tobytes() for row in sig})
+    print(json.dumps({
+        "metric": "uniform ground-state samples/s", "value": S / dt, "unit": "samples/s",
+        "n_gpus": 1, "steps": args.steps, "higher_is_better": True, "data": "synthetic",
+        "dtype": "int32",
+        "config": {"workload": "square16x16 open +-J Ising glass (seed 3), greedy order; "
+                               "16 samples per call, each spin fixed by its conditional "
+                               "probability from exact counts (3 primes + witness)",
+                   "log2_peak_elements": sg.log2_peak},
+        "ground_states": str(count), "E_min": E, "distinct_in_last_call": distinct,
+        "count_calls_per_call": inst["n"] + 1, "instances_per_count_call": 2 * S,
+        "ms_per_call": dt * 1e3}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -539,6 +571,8 @@ def main():
         return run_mixed(args)
     if args.workload in ("cubic", "max2sat"):
         return run_ensemble(args)
+    if args.workload == "sample":
+        return run_sample(args)
     import torch
     import torch.distributed as dist
 

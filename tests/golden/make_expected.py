@@ -16,6 +16,7 @@ sys.path.insert(0, ROOT)
 
 import instances as I  # noqa: E402
 import oracle as O  # noqa: E402
+from oracle import max2sat as M  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "expected_full.json")
 
@@ -30,6 +31,11 @@ def cases():
     # 12x12 3-state Potts glass, Gaussian couplings
     yield "potts12_gauss", I.potts_square(12, coupling="gauss", seed=2008), \
         dict(order=I.square_sweep_order(12), count=True, config=True)
+    # 5x5x5 open cubic +-J lattice with its exact degeneracy
+    yield "cubic5_pm", I.cubic_lattice(5, coupling="pm1", seed=2008), \
+        dict(count=True, config=True)
+    # Max-2-SAT on a random 3-regular graph, 140 variables (clause-tensor oracle)
+    yield "max2sat140", I.max2sat_regular3(140, seed=2008), dict(count=True, config=True)
 
 
 def main():
@@ -42,7 +48,7 @@ def main():
         if only and name not in only:
             continue
         t = time.time()
-        r = O.solve(inst, **kw)
+        r = M.solve(inst, **kw) if "clauses" in inst else O.solve(inst, **kw)
         out[name] = dict(
             name=inst["name"], seed=inst["seed"], digest=I.instance_digest(inst),
             E=r["E"], count=None if r["count"] is None else str(r["count"]),

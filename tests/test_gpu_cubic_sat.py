@@ -216,3 +216,38 @@ def test_sample_max2sat_optimal_assignments():
     for x in xs:
         assert M.cost(sat, np.array(x))[0] == o["E"]
     assert len(xs) > 1 if o["count"] > 1 else len(xs) == 1
+
+
+# ------------------------------------------------------------ stored oracle values (larger sizes)
+
+def _expected(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "expected_full.json")
+    with open(path) as f:
+        d = json.load(f)
+    if name not in d:
+        pytest.skip(f"{name} not in expected_full.json")
+    return d[name]
+
+
+def test_full_cubic5_pm_counts():
+    exp = _expected("cubic5_pm")
+    inst = I.cubic_lattice(5, coupling="pm1", seed=2008)
+    assert I.instance_digest(inst) == exp["digest"]
+    sg = P.SpinGlass(inst, order="greedy", seed=1, restarts=64)
+    c, _, E = sg.count(3)
+    assert E == exp["E"] and c == int(exp["count"])
+    st, E2 = state_of(sg)
+    assert E2 == E and O.energy(inst, st) == E
+
+
+def test_full_max2sat140_counts():
+    exp = _expected("max2sat140")
+    sat = I.max2sat_regular3(140, seed=2008)
+    assert I.instance_digest(sat) == exp["digest"]
+    ms = P.Max2SAT(sat, order="greedy", seed=1, restarts=64)
+    c, _, E = ms.count(3)
+    assert E == exp["E"] and c == int(exp["count"])
+    x, E2 = ms.assignment()
+    assert E2 == E and M.cost(sat, x)[0] == E

@@ -20,6 +20,10 @@ from oracle import max2sat as M  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "expected_full.json")
 
+# indices into mixed_square_batch(2048, 8, 20, seed=2026): L = 10, 11, ..., 20, then three more L = 18
+MIXED_2026 = [1, 19, 4, 33, 5, 26, 3, 12, 10, 0, 21, 11, 31, 46]
+MIXED_BATCH_2026 = None
+
 
 def cases():
     # 24x24 open square lattice, J ~ N(0,1), h ~ N(0, 0.1^2), float32 values
@@ -36,9 +40,21 @@ def cases():
         dict(count=True, config=True)
     # Max-2-SAT on a random 3-regular graph, 140 variables (clause-tensor oracle)
     yield "max2sat140", I.max2sat_regular3(140, seed=2008), dict(count=True, config=True)
+    # a second 5x5x5 +-J cubic lattice (batched cubic counts)
+    yield "cubic5_pm_2009", I.cubic_lattice(5, coupling="pm1", seed=2009), \
+        dict(count=True, config=False)
+    # members of the 2048-instance mixed +-J batch (L uniform in 8..20, base seed 2026):
+    # one instance of every L in 10..20, and three more with L = 18 (one batched plan)
+    for k in MIXED_2026:
+        inst = MIXED_BATCH_2026[k]
+        L = int(round(inst["n"] ** 0.5))
+        yield f"mixed2026_{k}", inst, dict(order=I.square_sweep_order(L), count=True,
+                                           config=False)
 
 
 def main():
+    global MIXED_BATCH_2026
+    MIXED_BATCH_2026 = I.mixed_square_batch(2048, Lmin=8, Lmax=20, seed=2026)
     out = {}
     if os.path.exists(OUT):
         with open(OUT) as f:

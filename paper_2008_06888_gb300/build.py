@@ -33,8 +33,6 @@ def nvcc():
 def _compile(src, verbose_ptxas=False):
     obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + ARCH + CFLAGS + ["-I" + OUT_DIR]
-    if src.endswith(".cpp"):
-        cmd += ["-x", "cu"] if False else []
     if verbose_ptxas and src.endswith(".cu"):
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

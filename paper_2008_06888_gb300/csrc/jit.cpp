@@ -516,12 +516,22 @@ bool jit_chains(const std::vector<ChainParams> &chains, Dtype dt, std::vector<co
   return true;
 }
 
+// SMs of the current device (this file also builds into host-only checks,
+// without kernels.cu)
+static int jit_sms() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+    return 152;
+  return v;
+}
+
 cudaError_t launch_jit_chain(const void *kernel, const ChainParams &p, const char *arena,
                              const void *Ax, void *Cx, const Batch &bt, cudaStream_t st) {
   if (p.outer == 0) return cudaSuccess;
   const int NT = threads_for(p.t);
   int64_t blocks = (p.outer + NT - 1) / NT;
-  const int64_t cap = std::max<int64_t>(1, 152 * blocks_per_sm(p.t) / bt.B);
+  const int64_t cap = std::max<int64_t>(1, jit_sms() * blocks_per_sm(p.t) / bt.B);
   if (blocks > cap) blocks = cap;
   ChainParams pc = p;
   const void *X = arena;

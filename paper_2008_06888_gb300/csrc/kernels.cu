@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -58,7 +59,22 @@ __device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b, uint64_t c)
   return s >= p ? s - p : s;
 }
 
-static inline int grid_for(int64_t n, int threads, int max_blocks = 152 * 32) {
+// Streaming multiprocessors of the current device (GB300: 152), queried once
+// per device; grid sizes are multiples of it.
+int num_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+    return 152;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+static inline int grid_for(int64_t n, int threads, int max_blocks = 0) {
+  if (max_blocks <= 0) max_blocks = num_sms() * 32;
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
   if (b > max_blocks) b = max_blocks;
@@ -569,7 +585,7 @@ static bool launch_gate2c(const GateParams &p, const T *A, const T *B, T *C, con
     return false;
   const int64_t nq = p.outer >> 2;
   int64_t blocks = (nq + 255) / 256;
-  const int64_t cap = std::max<int64_t>(1, 152 * 8 / bt.B);
+  const int64_t cap = std::max<int64_t>(1, num_sms() * 8 / bt.B);
   if (blocks > cap) blocks = cap;
   dim3 grid((unsigned)blocks, bt.B);
 #define TN_G2C(KS_, NS_)                                                                   \
@@ -592,7 +608,7 @@ static bool launch_gate2(const GateParams &p, const T *A, const T *B, T *C, cons
   if (std::getenv("TN_NO_GATE2") || !gate2_form(p, A, B, C, bt.ib, sizeof(T), &g)) return false;
   const int64_t nq = p.outer >> 2;
   int64_t blocks = (nq + 511) / 512;
-  const int64_t cap = std::max<int64_t>(1, 152 * 8 / bt.B);
+  const int64_t cap = std::max<int64_t>(1, num_sms() * 8 / bt.B);
   if (blocks > cap) blocks = cap;
   dim3 grid((unsigned)blocks, bt.B);
 #define TN_G2(KS_, NS_)                                                            \
@@ -893,7 +909,11 @@ static std::map<std::string, GemmTile> g_tune;
 static bool g_tune_loaded = false;
 static thread_local bool g_tune_off = false;   // set by callers that must not wait
 
-void set_gemm_autotune(bool on) { g_tune_off = !on; }
+bool set_gemm_autotune(bool on) {
+  const bool was = !g_tune_off;
+  g_tune_off = !on;
+  return was;
+}
 
 static std::string gemm_key(Dtype dt, const GemmParams &p, const Batch &bt, bool v16) {
   char k[192];
@@ -933,7 +953,7 @@ static void tune_store(const std::string &key, GemmTile t) {
 static cudaError_t run_mpgemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
                               const Batch &bt, cudaStream_t st, GemmTile t) {
   const int64_t tiles = p.batch * ((p.M + GBM - 1) / GBM) * ((p.N + GBN - 1) / GBN);
-  const int64_t cap = std::max<int64_t>(1, 152 * t.per_sm / bt.B);
+  const int64_t cap = std::max<int64_t>(1, num_sms() * t.per_sm / bt.B);
   dim3 blocks((unsigned)(tiles < cap ? tiles : cap), bt.B);
   if (t.variant == 0) {
     if (dt == DT_F32)
@@ -1357,7 +1377,8 @@ static cudaError_t launch_chain_t(const ChainParams &p, const char *arena, const
     if (e != cudaSuccess) return e;
     configured = sm;
   }
-  int64_t blocks = p.outer < 152 * 8 ? p.outer : 152 * 8;
+  const int64_t gmax = num_sms() * 8;
+  int64_t blocks = p.outer < gmax ? p.outer : gmax;
   k_chain<T, Q, COUNT><<<dim3((unsigned)blocks, bt.B), 256, sm, st>>>(
       p, reinterpret_cast<const T *>(arena), reinterpret_cast<const uint64_t *>(arena),
       static_cast<const T *>(Ax), An, static_cast<T *>(Cx), Cn, ps, bt.ib);
@@ -2031,7 +2052,7 @@ cudaError_t launch_rchain_count(Dtype dt, const ChainParams &p, const char *aren
                                 const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
   if (p.t != 3 || p.P != 4) return cudaErrorInvalidValue;
   int64_t blocks = (p.outer + 255) / 256;
-  const int64_t cap = std::max<int64_t>(1, 152 * 2 * 4 / bt.B);
+  const int64_t cap = std::max<int64_t>(1, num_sms() * 2 * 4 / bt.B);
   if (blocks > cap) blocks = cap;
   if (dt == DT_F32)
     k_rchain_count<float, 3, 4><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(
@@ -2287,7 +2308,7 @@ static cudaError_t launch_tchain6(const ChainParams &p, const char *arena, const
     configured = true;
   }
   int64_t blocks = (p.outer + NT - 1) / NT;
-  const int64_t cap = std::max<int64_t>(1, 152 * 3 / bt.B);
+  const int64_t cap = std::max<int64_t>(1, num_sms() * 3 / bt.B);
   if (blocks > cap) blocks = cap;
   k_tchain<T, 6, I, 2, 3, NT><<<dim3((unsigned)blocks, bt.B), NT, smem, st>>>(
       p, reinterpret_cast<const T *>(arena), static_cast<const T *>(Ax), static_cast<T *>(Cx),
@@ -2313,7 +2334,7 @@ cudaError_t launch_rchain(Dtype dt, const ChainParams &p, const char *arena, con
                                                         : 2;
   const int per_sm = p.t == 5 ? (minb == 3 ? 3 : 2) : 4;
   int64_t blocks = (p.outer + 255) / 256;
-  const int64_t cap = std::max<int64_t>(1, 152 * per_sm / bt.B);
+  const int64_t cap = std::max<int64_t>(1, num_sms() * per_sm / bt.B);
   if (blocks > cap) blocks = cap;
   const size_t smem = (size_t)2 * (1 << p.t) * 256 * 4;
   if (dt == DT_F32) {

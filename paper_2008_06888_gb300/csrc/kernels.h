@@ -16,6 +16,9 @@ struct Batch {
   int64_t ib = 0, jstride = 0, hstride = 0;
 };
 
+// Streaming multiprocessors of the current device (queried once per device).
+int num_sms();
+
 // Leaves (Sec. II bond / vertex tensors).  x: base of the value arena (bytes),
 // counts: when P > 0 every leaf element gets count 1 in each residue plane.
 cudaError_t launch_leaves(Dtype dt, int q, const LeafDesc *d_leaves, int nleaves, const float *J,
@@ -33,7 +36,8 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
 // calling thread skips that and uses the default).
 cudaError_t launch_mpgemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
                           const Batch &bt, cudaStream_t st);
-void set_gemm_autotune(bool on);
+// returns the previous setting of the calling thread
+bool set_gemm_autotune(bool on);
 // Residue planes of a counting GEMM whose values C were produced already.
 cudaError_t launch_gemm_count(Dtype dt, const GemmParams &p, const void *xA, const void *xB,
                               const void *xC, const uint64_t *nA, const uint64_t *nB, uint64_t *nC,
@@ -73,5 +77,9 @@ cudaError_t launch_state_out(int q, int n, const int8_t *state, int8_t *out, int
 size_t noalloc_scratch_bytes();
 cudaError_t noalloc_scratch(char **ptr);
 cudaError_t launch_energy_out(Dtype dt, const void *root, float *E, cudaStream_t st);
+// Leaves of tn_energy_noalloc from host descriptors passed as kernel
+// parameters (no device copy of the descriptors; values only).
+cudaError_t launch_leaves_param(Dtype dt, int q, const LeafDesc *leaves, int nleaves,
+                                const float *J, const float *h, char *scratch, cudaStream_t st);
 
 }  // namespace tn

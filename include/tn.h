@@ -273,6 +273,17 @@ tn_status tn_plan_info(const tn_ctx *ctx, int32_t *n_steps, int32_t *n_transpose
                        int64_t *arena_energy, int64_t *arena_config, int64_t *arena_count);
 
 /*
+ * tn_plan_launches -- kernel launches of one execution of the lowered program
+ *   (host only; Sec. III: which steps run as transposes + GEMMs and which as
+ *   gate contractions or fused chains).  mode: 0 tn_energy, 1 tn_config
+ *   (checkpoints kept, traceback included), 2 tn_count with 3 primes +
+ *   witness.  counts: 7 int64 entries, indexed by the kinds of
+ *   tn_profile_get (a counting GEMM or transpose is two launches: values and
+ *   residue planes).  Errors: TN_EINVAL (arguments), TN_ESTATE (no order).
+ */
+tn_status tn_plan_launches(const tn_ctx *ctx, int32_t mode, int64_t *counts);
+
+/*
  * tn_energy_noalloc -- E_min like tn_energy, for callers that cannot allocate
  *   device memory: code recording work inside a CUDA stream capture (where
  *   cudaMalloc is not allowed), frameworks whose caching allocator owns the
@@ -287,12 +298,13 @@ tn_status tn_plan_info(const tn_ctx *ctx, int32_t *n_steps, int32_t *n_transpose
  *   for it.  INT32 contexts read J_dev / h_dev as integers (rounded).
  *   Scratch: a static 32 MiB device array inside libtn.so, held by every GPU
  *   that loads the library until the process exits.  A plan whose
- *   intermediates plus leaf descriptors need more returns TN_ENOMEM with the
- *   size it needs (lattices up to about 20 x 20 fit).  The first call on a
- *   device looks up the array's device address (cudaGetSymbolAddress); make
- *   that first call before any stream capture.  No cudaMalloc, cudaFree or
- *   allocating library routine is called; the leaf descriptors are copied
- *   into the scratch with one cudaMemcpyAsync from host memory.
+ *   intermediates need more returns TN_ENOMEM with the size it needs
+ *   (lattices up to about 20 x 20 fit).  The first call on a device looks up
+ *   the array's device address (cudaGetSymbolAddress); make that first call
+ *   before any stream capture.  No cudaMalloc, cudaFree, memory copy or
+ *   allocating library routine is called: the leaf descriptors travel as
+ *   kernel parameters, so the call only queues kernel launches on the
+ *   stream.
  *   All calls share the one array and it keeps the last call's contents;
  *   every intermediate is written before it is read, so nothing needs
  *   clearing, but calls that overlap on the GPU (other streams, other host

@@ -50,6 +50,7 @@ _SIGS = {
                                C.c_void_p]),
     "tn_plan_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "tn_plan_launches": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "tn_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "tn_profile_get": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -293,6 +294,15 @@ def tn_plan_info(ctx):
 
 
 KIND_NAMES = ["leaves", "transpose", "gate", "gemm", "trace", "other", "chain"]
+
+
+def tn_plan_launches(ctx, mode="count"):
+    """Kernel launches per kind (KIND_NAMES) of one execution of the lowered
+    program: mode "energy", "config" or "count" (3 primes + witness)."""
+    m = {"energy": 0, "config": 1, "count": 2}[mode]
+    out = np.zeros(7, np.int64)
+    _check(lib().tn_plan_launches(ctx, m, _ptr(out)), ctx)
+    return dict(zip(KIND_NAMES, (int(x) for x in out)))
 
 
 def tn_set_profiling(ctx, enable=True):

@@ -1007,19 +1007,44 @@ tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limb
     for (auto &st : c->plan.steps) mix(((uint64_t)(st.a + 7) << 40) ^ ((uint64_t)(st.b + 7) << 20) ^ (uint64_t)st.c);
     return f;
   };
-  std::map<uint64_t, std::vector<int>> groups;
+  // the hash only buckets; a context joins a group only if its graph, dtype,
+  // energy map and steps equal those of the group's first context exactly
+  auto same = [](const tn_ctx *a, const tn_ctx *b) {
+    const Net &x = a->net, &y = b->net;
+    if (x.n != y.n || x.q != y.q || x.m != y.m || a->dt != b->dt ||
+        x.h.empty() != y.h.empty() || a->e_scale != b->e_scale || a->e_offset != b->e_offset ||
+        x.eu != y.eu || x.ev != y.ev || a->plan.n_leaves != b->plan.n_leaves ||
+        a->plan.steps.size() != b->plan.steps.size())
+      return false;
+    for (size_t i = 0; i < a->plan.steps.size(); ++i) {
+      const PStep &s = a->plan.steps[i], &t = b->plan.steps[i];
+      if (s.a != t.a || s.b != t.b || s.c != t.c) return false;
+    }
+    return true;
+  };
+  std::map<uint64_t, std::vector<std::vector<int>>> buckets;
   for (int k = 0; k < B; ++k) {
     if (!ctxs[k] || !ctxs[k]->ordered) {
       if (status) status[k] = TN_ESTATE;
       continue;
     }
-    groups[key(ctxs[k])].push_back(k);
+    std::vector<std::vector<int>> &bk = buckets[key(ctxs[k])];
+    bool placed = false;
+    for (auto &g : bk)
+      if (same(ctxs[g[0]], ctxs[k])) {
+        g.push_back(k);
+        placed = true;
+        break;
+      }
+    if (!placed) bk.push_back({k});
   }
+  std::vector<std::vector<int>> groups;
+  for (auto &kv : buckets)
+    for (auto &g : kv.second) groups.push_back(std::move(g));
   tn_status first = TN_OK;
   for (int k = 0; k < B; ++k)
     if (!ctxs[k] || !ctxs[k]->ordered) first = TN_ESTATE;
-  for (auto &kv : groups) {
-    const std::vector<int> &ids = kv.second;
+  for (auto &ids : groups) {
     tn_ctx *owner = ctxs[ids[0]];
     const Net &n = owner->net;
     const int G = (int)ids.size();
@@ -1115,10 +1140,26 @@ tn_status tn_plan_info(const tn_ctx *ctx, int32_t *n_steps, int32_t *n_transpose
   return TN_OK;
 }
 
+tn_status tn_plan_launches(const tn_ctx *ctx, int32_t mode, int64_t *counts) {
+  if (!ctx || !counts || mode < 0 || mode > 2) return TN_EINVAL;
+  if (!ctx->ordered) return TN_ESTATE;
+  Program pg;
+  std::string err;
+  const ProgMode pm = mode == 0 ? PM_ENERGY : mode == 1 ? PM_CONFIG : PM_COUNT;
+  if (!build_program(ctx->net, ctx->plan, pm, ctx->dt, pm == PM_COUNT ? 4 : 0, 0, &pg, &err))
+    return TN_EINVAL;
+  for (int k = 0; k < 7; ++k) counts[k] = 0;
+  for (const Op &op : pg.ops) {
+    const int nl = ((op.kind == OP_GEMM || op.kind == OP_PERM) && pg.P > 0) ? 2 : 1;
+    counts[op_kind_slot(op.kind)] += nl;
+  }
+  return TN_OK;
+}
+
 // For callers that cannot allocate device memory (see tn.h): the energy
 // program runs in the static scratch of noalloc.cu.  Nothing here calls
-// cudaMalloc/cudaFree; the only device traffic besides the kernels is one
-// host-to-device copy of the leaf descriptors into the scratch.
+// cudaMalloc/cudaFree or copies memory: the leaf descriptors travel as
+// kernel parameters, so the call only queues kernel launches.
 tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev, float *E_dev,
                             void *cuda_stream) {
   if (!ctx) return TN_EINVAL;
@@ -1143,8 +1184,7 @@ tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev,
     ctx->noalloc_fp = fp;
   }
   Program &p = *ctx->prog_noalloc;
-  const int64_t leaves_off = (p.arena_bytes + 255) / 256 * 256;
-  const int64_t need = leaves_off + (int64_t)(p.leaves.size() * sizeof(LeafDesc));
+  const int64_t need = p.arena_bytes;
   const int64_t cap = (int64_t)noalloc_scratch_bytes();
   if (need > cap)
     return fail(ctx, TN_ENOMEM, "tn_energy_noalloc: this plan needs " + std::to_string(need) +
@@ -1153,24 +1193,22 @@ tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev,
   char *base = nullptr;
   CK(noalloc_scratch(&base));
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  LeafDesc *d_leaves = reinterpret_cast<LeafDesc *>(base + leaves_off);
-  if (!p.leaves.empty())
-    CK(cudaMemcpyAsync(d_leaves, p.leaves.data(), p.leaves.size() * sizeof(LeafDesc),
-                       cudaMemcpyHostToDevice, st));
   PrimeSet ps;
   for (int i = 0; i < TN_MAX_PRIMES; ++i) ps.c[i] = kPrimeC[i];
   auto X = [&](const Loc &l) -> void * { return l.buf < 0 ? nullptr : base + abs_off(p, l); };
   const Batch one;
   // this call only queues work: no GEMM tile timing (it would wait on the stream)
   struct NoTune {
-    NoTune() { set_gemm_autotune(false); }
-    ~NoTune() { set_gemm_autotune(true); }
+    bool was;
+    NoTune() : was(set_gemm_autotune(false)) {}
+    ~NoTune() { set_gemm_autotune(was); }
   } no_tune;
   for (const Op &op : p.ops) {
     cudaError_t e = cudaSuccess;
     switch (op.kind) {
       case OP_LEAVES:
-        e = launch_leaves(p.dt, p.q, d_leaves, (int)p.leaves.size(), J_dev, h_dev, base, 0, one, st);
+        e = launch_leaves_param(p.dt, p.q, p.leaves.data(), (int)p.leaves.size(), J_dev, h_dev,
+                                base, st);
         break;
       case OP_PERM:
         e = launch_permute(p.perms[op.idx], X(op.in0), X(op.out), nullptr, nullptr, one, st);

@@ -527,3 +527,111 @@ def test_compiled_chain_kernels_match_interpreter(coupling, monkeypatch):
     Eb2 = b.energy()
     assert Ea == Eb and Ea2 == Eb2 and np.array_equal(sa, sb)
     check_energy(inst, O.energy(inst, P.SpinGlass.state_indices(sa, 2)), Ea)
+
+
+# ------------------------------------------------------------ batched path at full size
+
+MIXED_2026 = [1, 19, 4, 33, 5, 26, 3, 12, 10, 0, 21, 11, 31, 46]
+
+
+def _mixed_stored():
+    """Members of the bench's 2048-instance mixed batch (L uniform in 8..20, base
+    seed 2026) with oracle values stored by tests/golden/make_expected.py."""
+    batch = I.mixed_square_batch(2048, Lmin=8, Lmax=20, seed=2026)
+    out = []
+    for k in MIXED_2026:
+        exp = _expected(f"mixed2026_{k}")
+        assert I.instance_digest(batch[k]) == exp["digest"]
+        out.append((batch[k], exp))
+    return out
+
+
+def _sweep(inst):
+    L = int(round(np.sqrt(inst["n"])))
+    return P.SpinGlass(inst, order="sweep", seq=I.square_sweep_order(L))
+
+
+def test_full_mixed_batch_run_matches_stored_oracle():
+    """tn_batch_run over L = 10..20 (four instances share the L = 18 plan), each
+    with the bench's row-by-row order: E_min and count bit-exact; the counting
+    register chains (2^15+ elements per instance, L >= 15) and the batched
+    launches over one plan's group both run."""
+    cases = _mixed_stored()
+    assert sum(1 for x, _ in cases if x["n"] >= 16 * 16) >= 3
+    sgs = [_sweep(x) for x, _ in cases]
+    try:
+        for s in sgs:
+            B.tn_set_profiling(s.ctx, True)
+        st, E, counts, status = B.tn_batch_run([s.ctx for s in sgs], limbs_per=4)
+        assert st == 0 and np.all(status == 0)
+        for k, (x, exp) in enumerate(cases):
+            assert E[k] == exp["E"] and counts[k] == int(exp["count"]), (x["name"], E[k], counts[k])
+        chains = sum(B.tn_profile_get(s.ctx, 6)["launches"] for s in sgs)
+        assert chains > 0
+    finally:
+        for s in sgs:
+            s.close()
+
+
+def test_full_count_batch_L18_four_instances():
+    """tn_count_batch with B = 4 on one 18 x 18 plan (one launch per step for all
+    four instances), against the stored oracle values."""
+    cases = [(x, e) for x, e in _mixed_stored() if x["n"] == 18 * 18]
+    assert len(cases) == 4
+    sg = _sweep(cases[0][0])
+    try:
+        E, counts, status = sg.count_batch(np.stack([x["J"] for x, _ in cases]), limbs_per=4)
+        assert np.all(status == 0)
+        for k, (x, exp) in enumerate(cases):
+            assert E[k] == exp["E"] and counts[k] == int(exp["count"])
+        # and the energies alone through the batched energy program
+        Eb = sg.energy_batch(np.stack([x["J"] for x, _ in cases]))
+        assert [float(v) for v in Eb] == [exp["E"] for _, exp in cases]
+    finally:
+        sg.close()
+
+
+def test_full_cubic5_count_batch_matches_stored_oracle():
+    """Two 5x5x5 +-J cubic lattices counted in one batch on one greedy plan."""
+    exps = [_expected("cubic5_pm"), _expected("cubic5_pm_2009")]
+    insts = [I.cubic_lattice(5, coupling="pm1", seed=s) for s in (2008, 2009)]
+    for x, e in zip(insts, exps):
+        assert I.instance_digest(x) == e["digest"]
+    sg = P.SpinGlass(insts[0], order="greedy", seed=1, restarts=64)
+    try:
+        E, counts, status = sg.count_batch(np.stack([x["J"] for x in insts]), limbs_per=4)
+        assert np.all(status == 0)
+        for k, e in enumerate(exps):
+            assert E[k] == e["E"] and counts[k] == int(e["count"])
+    finally:
+        sg.close()
+
+
+def test_kernel_mix_transposes_gemms_and_counting_gemms_run():
+    """A plan with transposes and max-plus GEMM steps (chimera 4x4 cells, greedy
+    order): the profile shows the transpose, GEMM and counting-GEMM launches the
+    lowered program lists, and E_min, the count and sigma* agree with the
+    oracle."""
+    inst = I.chimera(4, coupling="pm1", seed=2)
+    o = O.solve(inst, order=I.chimera_sweep_order(4))
+    sg = P.SpinGlass(inst, order="greedy", seed=2, restarts=16)
+    try:
+        plan = B.tn_plan_launches(sg.ctx, "count")
+        assert plan["transpose"] > 0 and plan["gemm"] > 0
+        B.tn_set_profiling(sg.ctx, True)
+        B.tn_profile_reset(sg.ctx)
+        c, _, E = sg.count(3)
+        assert (E, c) == (o["E"], o["count"])
+        got = {k: B.tn_profile_get(sg.ctx, i)["launches"] for i, k in enumerate(B.KIND_NAMES)}
+        # counting steps launch the value GEMM and the residue-plane GEMM
+        assert got["transpose"] == plan["transpose"] > 0
+        assert got["gemm"] == plan["gemm"] and got["gemm"] >= 2 and got["gemm"] % 2 == 0
+        B.tn_profile_reset(sg.ctx)
+        assert sg.energy() == o["E"]
+        e_plan = B.tn_plan_launches(sg.ctx, "energy")
+        got = {k: B.tn_profile_get(sg.ctx, i)["launches"] for i, k in enumerate(B.KIND_NAMES)}
+        assert got["gemm"] == e_plan["gemm"] > 0 and got["transpose"] == e_plan["transpose"] > 0
+        st, E2 = gpu_state(sg)
+        assert E2 == o["E"] and O.energy(inst, st) == o["E"]
+    finally:
+        sg.close()

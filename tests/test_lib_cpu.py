@@ -219,3 +219,21 @@ def test_sample_argument_checks_before_any_device_work():
         B.tn_sample(p, 4, 2)
     assert e.value.status == B.TN_EINVAL          # Ising only
     B.tn_destroy(p)
+
+
+def test_plan_launches_of_the_kernel_mix_case():
+    """The chimera 4x4 greedy plan the GPU kernel-mix test runs has transposes,
+    GEMMs and (in count mode) twice as many GEMM launches (values + residues)."""
+    import instances as I
+    inst = I.chimera(4, coupling="pm1", seed=2)
+    c = B.tn_build(inst)
+    try:
+        B.tn_order(c, B.TN_ORDER_GREEDY, None, 2, 16)
+        e = B.tn_plan_launches(c, "energy")
+        n = B.tn_plan_launches(c, "count")
+        assert e["transpose"] > 0 and e["gemm"] > 0
+        assert n["gemm"] == 2 * e["gemm"] and n["transpose"] == 2 * e["transpose"]
+        assert e["leaves"] == 1 and e["trace"] == 0
+        assert B.tn_plan_launches(c, "config")["trace"] > 0
+    finally:
+        B.tn_destroy(c)

@@ -71,3 +71,49 @@ def test_noalloc_rejects_plans_beyond_the_static_scratch():
         assert "static scratch" in str(e.value)
     finally:
         B.tn_destroy(c)
+
+
+def test_noalloc_captured_in_a_cuda_graph_allocates_nothing():
+    """The use the entry point exists for: recorded inside a stream capture.
+
+    The call is made once eagerly (its first call on the device looks up the
+    scratch address, which must happen outside capture), then captured into a
+    CUDA graph in torch's strictest capture mode, where any allocation or
+    synchronous copy would end the capture with an error.  Two replays must
+    give tn_energy's E_min, and neither the replays nor the eager calls may
+    change the memory the device reports as in use or torch's allocations."""
+    torch = pytest.importorskip("torch")
+    inst = I.square_lattice(14, coupling="gauss", field_sigma=0.1, seed=41)
+    c = _ctx(inst, method=B.TN_ORDER_GREEDY, seed=1, restarts=8)
+    try:
+        ref = B.tn_energy(c)
+        J = torch.tensor(inst["J"], device="cuda")
+        h = torch.tensor(inst["h"], device="cuda")
+        E = torch.full((1,), float("nan"), dtype=torch.float32, device="cuda")
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            B.tn_energy_noalloc(c, J.data_ptr(), h.data_ptr(), E.data_ptr(), s.cuda_stream)
+        s.synchronize()
+        assert abs(float(E.item()) - ref) <= REL * max(1.0, abs(ref))
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
+        for _ in range(2):
+            with torch.cuda.stream(s):
+                B.tn_energy_noalloc(c, J.data_ptr(), h.data_ptr(), E.data_ptr(), s.cuda_stream)
+        s.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s, capture_error_mode="global"):
+            B.tn_energy_noalloc(c, J.data_ptr(), h.data_ptr(), E.data_ptr(), s.cuda_stream)
+        assert torch.cuda.memory_allocated() == alloc0
+        for rep in range(2):
+            E.fill_(float("nan"))
+            g.replay()
+            torch.cuda.synchronize()
+            got = float(E.item())
+            assert abs(got - ref) <= REL * max(1.0, abs(ref)), (rep, got, ref)
+        assert torch.cuda.memory_allocated() == alloc0
+        del g
+    finally:
+        B.tn_destroy(c)

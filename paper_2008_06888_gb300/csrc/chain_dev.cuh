@@ -20,10 +20,19 @@ __device__ __forceinline__ P *inst_ptr(P *p, int64_t ib) {
                                    static_cast<const void *>(p))) + blockIdx.y * ib);
 }
 
-// Asynchronous 4-byte global -> shared copies (cp.async) and their groups.
+// Asynchronous 4-, 8- and 16-byte global -> shared copies (cp.async) and their groups.
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+// 16 bytes, cached in L2 only (a streamed tile is not re-read)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");

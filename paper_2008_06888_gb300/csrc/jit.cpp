@@ -22,6 +22,7 @@
 #include <fstream>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <sstream>
 #include <thread>
 
@@ -32,8 +33,22 @@ namespace tn {
 namespace {
 
 // threads per block and resident blocks per SM of a chain with RB register legs
-int threads_for(int RB) { return RB >= 6 ? 128 : 256; }
-int blocks_per_sm(int RB) { return RB >= 6 ? 3 : 2; }
+// six-leg chains: TN_JIT_SHAPE6="threads:blocks" overrides the launch shape
+std::pair<int, int> shape6() {
+  static const std::pair<int, int> sh = [] {
+    std::pair<int, int> d{128, 3};
+    if (const char *e = std::getenv("TN_JIT_SHAPE6")) {
+      int a = 0, b = 0;
+      if (std::sscanf(e, "%d:%d", &a, &b) == 2 && a % 32 == 0 && a >= 32 && a <= 256 && b >= 1 &&
+          b <= 16)
+        d = {a, b};
+    }
+    return d;
+  }();
+  return sh;
+}
+int threads_for(int RB) { return RB >= 6 ? shape6().first : 256; }
+int blocks_per_sm(int RB) { return RB >= 6 ? shape6().second : 2; }
 size_t smem_for(int RB) { return (size_t)2 * (32 << RB) * (threads_for(RB) / 32) * 4; }
 
 uint64_t fnv1a(const std::string &s, uint64_t h = 1469598103934665603ull) {
@@ -191,6 +206,26 @@ void tile_word(const TileMap &tm, int i, int *D, int64_t *off) {
     }
 }
 
+int tile_vec(const TileMap &tm) {
+  int k = 0;
+  while (k < 2 && tm.cbit[k] == (1 << k)) ++k;
+  while ((1 << k) > (1 << tm.nreg)) --k;   // a copy instruction spans w tile lines
+  return 1 << k;
+}
+
+void tile_vec_lane(const TileMap &tm, int w, int lane, int *D, int64_t *off) {
+  const int per = 32 / w, sub = lane / per, first = (lane % per) * w;
+  *D = 0;
+  *off = first;
+  for (int j = 0; j < 5; ++j)
+    if ((first >> j) & 1) *D ^= tm.cbit[j];
+  for (int k = 0; (1 << k) < w; ++k)
+    if ((sub >> k) & 1) {
+      *D ^= tm.cbit[5 + k];
+      *off += int64_t(1) << tm.tpos[5 + k];
+    }
+}
+
 std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &name) {
   const bool f32 = dt == DT_F32;
   const char *T = f32 ? "float" : "int";
@@ -243,24 +278,35 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
   // of lane sits at a slot swizzled so that the copies and the owner's reads
   // and writes are free of bank conflicts (TileMap).  Only the warp itself
   // touches its tile (__syncwarp).
-  auto lane_D = [&](const TileMap &tm) {
+  // Vector copies (tile_vec): lane-dependent slot and memory offsets of the
+  // first word a lane moves, as in tile_vec_lane.
+  const bool vec = std::getenv("TN_JIT_NO_VEC") == nullptr;
+  const int win = vec ? tile_vec(tin) : 1, wout = vec ? tile_vec(tout) : 1;
+  auto lane_vec = [&](const TileMap &tm, int w, const char *Dn, const char *On) {
     std::ostringstream d;
-    d << "0";
-    for (int j = 0; j < 5; ++j) d << " ^ (-((lane >> " << j << ") & 1) & " << tm.cbit[j] << ")";
+    const int per = 32 / w;
+    d << "  const int " << Dn << " = 0";
+    for (int j = 0; j < 5; ++j)
+      d << " ^ (-((((lane % " << per << ") * " << w << ") >> " << j << ") & 1) & " << tm.cbit[j] << ")";
+    for (int k = 0; (1 << k) < w; ++k)
+      d << " ^ (-(((lane / " << per << ") >> " << k << ") & 1) & " << tm.cbit[5 + k] << ")";
+    d << ";\n  const int " << On << " = (lane % " << per << ") * " << w;
+    for (int k = 0; (1 << k) < w; ++k)
+      d << " + ((((lane / " << per << ") >> " << k << ") & 1) << " << tm.tpos[5 + k] << ")";
+    d << ";\n";
     return d.str();
   };
   o << "  T *const wstage = stage + (tid >> 5) * " << W << ";\n"
-    << "  const int Din = " << lane_D(tin) << ";\n"
-    << "  const int Dout = " << lane_D(tout) << ";\n"
+    << lane_vec(tin, win, "Din", "Oin") << lane_vec(tout, wout, "Dout", "Oout")
     << "  auto issue = [&](long long t, int s) {\n"
     << "    if (t < " << p.outer << "LL) {\n"
-    << "      const T *src = A + base_in(t - lane) + lane;\n"
+    << "      const T *src = A + base_in(t - lane) + Oin;\n"
     << "      T *dst = wstage + s * " << S << ";\n";
-  for (int i = 0; i < (1 << tin.nreg); ++i) {
+  for (int i = 0; i < (1 << tin.nreg); i += win) {
     int D;
     int64_t off;
     tile_word(tin, i, &D, &off);
-    o << "      cp_async4(dst + (Din ^ " << D << "), src + " << off << ");\n";
+    o << "      cp_async" << 4 * win << "(dst + (Din ^ " << D << "), src + " << off << ");\n";
   }
   o << "    }\n    cp_async_commit();\n  };\n"
     << "  issue(tau, 0);\n"
@@ -413,12 +459,14 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     o << "    sw[" << (sl & ~31) << " + (lane ^ " << (sl & 31) << ")] = v" << e << ";\n";
   }
   o << "    __syncwarp();\n"
-    << "    T *dst = C + base_out(tau - lane) + lane;\n";
-  for (int i = 0; i < (1 << tout.nreg); ++i) {
+    << "    T *dst = C + base_out(tau - lane) + Oout;\n";
+  const char *VT = wout == 4 ? "V" : wout == 2 ? "typename Vec2<T>::t" : "T";
+  for (int i = 0; i < (1 << tout.nreg); i += wout) {
     int D;
     int64_t off;
     tile_word(tout, i, &D, &off);
-    o << "    dst[" << off << "] = sw[Dout ^ " << D << "];\n";
+    o << "    *reinterpret_cast<" << VT << " *>(dst + " << off << ") = *reinterpret_cast<const "
+      << VT << " *>(sw + (Dout ^ " << D << "));\n";
   }
   o << "    __syncwarp();\n"   // the tile is refilled by a later issue
     << "  }\n  asm volatile(\"cp.async.wait_all;\\n\" ::: \"memory\");\n}\n";
@@ -530,9 +578,18 @@ cudaError_t launch_jit_chain(const void *kernel, const ChainParams &p, const cha
                              const void *Ax, void *Cx, const Batch &bt, cudaStream_t st) {
   if (p.outer == 0) return cudaSuccess;
   const int NT = threads_for(p.t);
-  int64_t blocks = (p.outer + NT - 1) / NT;
-  const int64_t cap = std::max<int64_t>(1, jit_sms() * blocks_per_sm(p.t) / bt.B);
-  if (blocks > cap) blocks = cap;
+  const int64_t need = (p.outer + NT - 1) / NT;
+  // blocks per instance: the B instances' blocks should fill the resident
+  // slots (SMs x blocks per SM) in whole waves, so that every SM carries the
+  // same number of equal blocks; else one partial wave
+  const int64_t slots = (int64_t)jit_sms() * blocks_per_sm(p.t);
+  const int64_t cap = std::max<int64_t>(1, slots / bt.B);
+  const int64_t whole = slots / std::gcd(slots, (int64_t)bt.B);
+  int64_t blocks = std::min(need, cap);
+  if (whole <= need && whole <= 4 * cap) blocks = whole;
+  // the compiled tile copies move up to 16 bytes per lane
+  if ((reinterpret_cast<uintptr_t>(Ax) | reinterpret_cast<uintptr_t>(Cx) | (uintptr_t)bt.ib) & 15)
+    return cudaErrorMisalignedAddress;
   ChainParams pc = p;
   const void *X = arena;
   const void *A = Ax;

@@ -41,6 +41,14 @@ struct TileMap {
 bool tile_map(const ChainParams &p, const int64_t *hi, TileMap *tm);
 int tile_slot(const TileMap &tm, int lane, int e);
 void tile_word(const TileMap &tm, int i, int *D, int64_t *off);
+// Vector copies: when memory positions 0..k-1 (k <= 2) are not register legs
+// of the layout, w = 2^k consecutive words of a line sit in w consecutive,
+// w-aligned slots, so a lane copies w words at once: copy instruction i
+// (i < 2^nreg / w) of lane moves words lane_v + j (j < w) of tile line
+// i * w + sub (sub = lane / (32 / w)), i.e. memory tile base + off_v + off_{i*w}
+// + j to slots (D_v ^ D_{i*w}) + j, with (D_v, off_v) = tile_vec_lane(lane).
+int tile_vec(const TileMap &tm);
+void tile_vec_lane(const TileMap &tm, int w, int lane, int *D, int64_t *off);
 
 // Source of the specialised kernel `name` for one chain (exposed for tests).
 std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &name);

@@ -6,7 +6,9 @@
 // every slot is used once, that the slot the thread of lane uses for register
 // state e (tile_slot) holds the element at base(tau) + hi[e] of that layout,
 // and that no warp instruction (copy, or the owners' accesses for one e) has
-// two lanes on one bank.  Programs include chains that start from a
+// two lanes on one bank.  The vector copies (tile_vec: w words per lane when
+// memory positions below log2 w are not register legs) must move the same
+// words to the same slots, w-aligned in memory and in shared memory.  Programs include chains that start from a
 // rank-raising step (the new leg is not a leg of the input) and chains that
 // end with a contraction (the contracted leg is not a leg of the output).
 // Exit status 0 when all hold.
@@ -36,7 +38,7 @@ static Net square(int L) {
 }
 int main() {
   std::mt19937_64 rng(9);
-  int chains = 0, sides = 0, partial = 0, bad = 0, conflicts = 0;
+  int chains = 0, sides = 0, partial = 0, bad = 0, conflicts = 0, vbad = 0, vsides = 0;
   for (int L : {16, 20, 24}) for (int ord : {0, 1, 2, 3}) for (int mode : {0, 1}) {
     Net net = square(L);
     Tree t; std::string err;
@@ -73,6 +75,30 @@ int main() {
               used[d & 31] = true;
             }
           }
+          // vector copies (tile_vec): the same words and slots, w at a time
+          const int w = tile_vec(tm);
+          std::vector<int> vseen(32 * N, 0);
+          for (int i = 0; i < N; i += w) {
+            int Di; int64_t offi;
+            tile_word(tm, i, &Di, &offi);
+            for (int lane = 0; lane < 32; ++lane) {
+              int Dv; int64_t ov;
+              tile_vec_lane(tm, w, lane, &Dv, &ov);
+              const int s0 = Dv ^ Di;
+              if (s0 % w || (ov + offi) % w) vbad++;
+              for (int j = 0; j < w; ++j) {
+                const int line = i + lane / (32 / w), word = (lane % (32 / w)) * w + j;
+                int Dl = 0;
+                for (int b = 0; b < 5; ++b) if ((word >> b) & 1) Dl ^= tm.cbit[b];
+                int Dline; int64_t offline;
+                tile_word(tm, line, &Dline, &offline);
+                if (s0 + j != (Dl ^ Dline) || ov + offi + j != word + offline) vbad++;
+                if (s0 + j >= 0 && s0 + j < 32 * N) vseen[s0 + j]++;
+              }
+            }
+          }
+          for (int v : vseen) if (v != 1) vbad++;
+          if (trial == 0) vsides += w > 1;
           for (int e = 0; e < E; ++e) {
             bool used[32] = {false};
             for (int lane = 0; lane < 32; ++lane) {
@@ -86,7 +112,8 @@ int main() {
       }
     }
   }
+  printf("vector copies: layouts %d wrong %d\n", vsides, vbad);
   printf("chains %d layouts %d (without a register leg: %d) wrong %d bank_conflicts %d\n", chains,
          sides, partial, bad, conflicts);
-  return (bad || conflicts || chains == 0) ? 1 : 0;
+  return (bad || conflicts || vbad || chains == 0 || vsides == 0) ? 1 : 0;
 }

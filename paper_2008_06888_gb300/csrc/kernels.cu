@@ -677,8 +677,8 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
 // 128 x 128 output tile per block of 256 threads, 8 x 8 outputs per thread,
 // k slabs of 16 staged in shared memory by cp.async (two stages).  The
 // tropical multiply-add of two consecutive k is done with two adds and one
-// three-input max (FP32), the fastest form measured on GB300; INT32 uses
-// add + max.  Out-of-range operands read the tropical zero.
+// three-input max (FP32), the fastest form measured on GB300; INT32 uses the
+// fused add-max (DPX) instruction.  Out-of-range operands read the tropical zero.
 
 __device__ __forceinline__ float tmax3(float a, float b, float c) {
   float r;
@@ -687,6 +687,15 @@ __device__ __forceinline__ float tmax3(float a, float b, float c) {
 }
 __device__ __forceinline__ int32_t tmax3(int32_t a, int32_t b, int32_t c) {
   return max(max(a, b), c);
+}
+// acc (+)= a0 (.) b0 (+) a1 (.) b1: FP32 two adds and a three-input max; INT32
+// two fused add-max instructions (DPX: max(a + b, c)), same integer result
+__device__ __forceinline__ float tmac2(float acc, float a0, float b0, float a1, float b1) {
+  return tmax3(acc, a0 + b0, a1 + b1);
+}
+__device__ __forceinline__ int32_t tmac2(int32_t acc, int32_t a0, int32_t b0, int32_t a1,
+                                         int32_t b1) {
+  return __viaddmax_s32(a1, b1, __viaddmax_s32(a0, b0, acc));
 }
 
 constexpr int GBM = 128, GBN = 128, GBK = 16, GPAD = 4;
@@ -771,7 +780,7 @@ __global__ void __launch_bounds__(256, 2) k_mpgemm(const GemmParams p, const T *
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = tmax3(acc[i][j], a0[i] + b0[j], a1[i] + b1[j]);
+          for (int j = 0; j < 8; ++j) acc[i][j] = tmac2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
       }
       __syncthreads();
     }
@@ -792,11 +801,8 @@ __global__ void __launch_bounds__(256, 2) k_mpgemm(const GemmParams p, const T *
 
 // Fast path for A = [batch][M][K] and B = [batch][K][N] (both row-major, K and N
 // multiples of 4, whole 128 x 128 x 16 tiles): each k slab moves as 16-byte
-// cp.async chunks, A staged k-contiguous (As[m][k]) and read as 4-k vectors.
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
+// cp.async chunks (cp_async16), A staged k-contiguous (As[m][k]) and read as
+// 4-k vectors.
 
 constexpr int GAK = GBK + 4;   // padded row of As[m][k]
 
@@ -870,7 +876,7 @@ __global__ void __launch_bounds__(256, 2) k_mpgemm16(const GemmParams p, const T
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = tmax3(acc[i][j], a0[i] + b0[j], a1[i] + b1[j]);
+          for (int j = 0; j < 8; ++j) acc[i][j] = tmac2(acc[i][j], a0[i], b0[j], a1[i], b1[j]);
       }
       __syncthreads();
     }

@@ -3,6 +3,7 @@
 #include "../../include/tn.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -72,6 +73,27 @@ struct tn_ctx {
 static std::string g_build_err;
 
 namespace {
+
+// NVTX range for profilers (no cost without an attached tool): every entry
+// point that computes, every batch group and every eagerly launched op.
+struct Nvtx {
+  explicit Nvtx(const char *name) { nvtxRangePushA(name); }
+  ~Nvtx() { nvtxRangePop(); }
+  Nvtx(const Nvtx &) = delete;
+  Nvtx &operator=(const Nvtx &) = delete;
+};
+
+const char *op_name(OpKind k) {
+  switch (k) {
+    case OP_LEAVES: return "leaves";
+    case OP_PERM: return "transpose";
+    case OP_GATE: return "gate";
+    case OP_GEMM: return "maxplus_gemm";
+    case OP_TRACE: return "traceback";
+    case OP_CHAIN: return "gate_chain";
+  }
+  return "op";
+}
 
 tn_status fail(tn_ctx *c, tn_status s, const std::string &msg) {
   if (c) c->err = msg; else g_build_err = msg;
@@ -285,6 +307,7 @@ tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_
     const Op &op = p.ops[oi];
     cudaError_t e = cudaSuccess;
     const int slot = op_kind_slot(op.kind);
+    Nvtx nv(op_name(op.kind));
     int e0 = -1;
     if (ctx->profiling) {
       e0 = ctx->ev_next;
@@ -781,6 +804,7 @@ tn_status tn_set_stream(tn_ctx *ctx, void *cuda_stream) {
 }
 
 tn_status tn_energy(tn_ctx *ctx, double *E) {
+  Nvtx nv("tn_energy");
   if (!ctx || !E) return fail(ctx, TN_EINVAL, "NULL argument");
   ctx->fwd_done = false;
   tn_status s = ensure_device(ctx);
@@ -797,6 +821,7 @@ tn_status tn_energy(tn_ctx *ctx, double *E) {
 }
 
 tn_status tn_forward(tn_ctx *ctx, double *E) {
+  Nvtx nv("tn_forward");
   if (!ctx) return TN_EINVAL;
   tn_status s = ensure_device(ctx);
   if (s != TN_OK) return s;
@@ -816,6 +841,7 @@ tn_status tn_forward(tn_ctx *ctx, double *E) {
 }
 
 tn_status tn_backward(tn_ctx *ctx, int8_t *sigma) {
+  Nvtx nv("tn_backward");
   if (!ctx) return TN_EINVAL;
   if (!ctx->fwd_done || !ctx->prog[PM_CONFIG])
     return fail(ctx, TN_ESTATE, "tn_backward needs tn_forward as the previous call");
@@ -869,6 +895,7 @@ tn_status tn_gradient(tn_ctx *ctx, float *dJ, float *dh, int32_t on_device) {
 
 tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_limbs,
                    double *ln_count, double *E) {
+  Nvtx nv("tn_count");
   if (!ctx) return TN_EINVAL;
   ctx->fwd_done = false;
   if (n_primes < 1 || n_primes > TN_MAX_PRIMES - 1)
@@ -911,6 +938,7 @@ tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_li
 
 tn_status tn_energy_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
                           int32_t on_device, double *E) {
+  Nvtx nv("tn_energy_batch");
   if (!ctx) return TN_EINVAL;
   if (!E) return fail(ctx, TN_EINVAL, "E is NULL");
   Program *p;
@@ -927,6 +955,7 @@ tn_status tn_energy_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h
 
 tn_status tn_config_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
                           int32_t on_device, double *E, int8_t *sigma) {
+  Nvtx nv("tn_config_batch");
   if (!ctx) return TN_EINVAL;
   Program *p;
   RunArgs ra;
@@ -950,6 +979,7 @@ tn_status tn_config_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h
 tn_status tn_count_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
                          int32_t on_device, int32_t n_primes, uint64_t *limbs, int32_t limbs_per,
                          double *E, int32_t *status) {
+  Nvtx nv("tn_count_batch");
   if (!ctx) return TN_EINVAL;
   if (n_primes < 1 || n_primes > TN_MAX_PRIMES - 1)
     return fail(ctx, TN_EINVAL, "n_primes must be in [1, 8]");
@@ -988,6 +1018,7 @@ tn_status tn_count_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
 
 tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limbs,
                        int32_t limbs_per, int32_t *status) {
+  Nvtx nv("tn_batch_run");
   if (B < 0 || (B > 0 && !ctxs)) return TN_EINVAL;
   // group the contexts whose graph, dtype and plan coincide; each group runs
   // as one batch on its first context
@@ -1162,6 +1193,7 @@ tn_status tn_plan_launches(const tn_ctx *ctx, int32_t mode, int64_t *counts) {
 // kernel parameters, so the call only queues kernel launches.
 tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev, float *E_dev,
                             void *cuda_stream) {
+  Nvtx nv("tn_energy_noalloc");
   if (!ctx) return TN_EINVAL;
   if (ctx->e_scale != 1.0) return fail(ctx, TN_ESTATE, "Max-2-SAT contexts have no noalloc path");
   if (!E_dev) return fail(ctx, TN_EINVAL, "E_dev is NULL");

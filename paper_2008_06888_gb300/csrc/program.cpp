@@ -1255,7 +1255,21 @@ bool build_program(const Net &net, const Plan &plan, ProgMode mode, Dtype dt, in
         }
         if (o.kind == OP_CHAIN) {
           const ChainParams &c = pr->chains[o.idx];
-          std::fprintf(stderr, " chain mode %d outer %lld t %d gates", c.mode, (long long)c.outer, c.t);
+          std::fprintf(stderr, " chain mode %d outer %lld t %d", c.mode, (long long)c.outer, c.t);
+          if (c.mode == 1) {
+            // memory position (log2 of the element offset) of each register leg
+            // in the input and the output layout (-1: not a leg there)
+            for (int side = 0; side < 2; ++side) {
+              std::fprintf(stderr, side ? " rout" : " rin");
+              for (int b = 0; b < c.t; ++b) {
+                const int64_t o = side ? c.hi_out[1 << b] : c.hi_in[1 << b];
+                int q = -1;
+                if (o > 0) for (q = 0; (int64_t(1) << q) < o; ++q) {}
+                std::fprintf(stderr, " %d", q);
+              }
+            }
+          }
+          std::fprintf(stderr, " gates");
           for (int g = 0; g < c.ngates; ++g)
             std::fprintf(stderr, " (%d,%d,%d,%d,%d)", c.g[g].kind, c.g[g].ls, c.g[g].nb, c.g[g].lsb[0],
                          c.g[g].nb > 1 ? c.g[g].lsb[1] : 9);

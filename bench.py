@@ -8,8 +8,14 @@ instance the step computes E_min (forward contraction keeping checkpoints) and
 the ground state sigma* (argmax traceback).  Couplings are resident in HBM
 before the timed region.  Metric: instances/s over all ranks.
 
+The default line also carries sub-records measured in the same run: the
+max-plus GEMM on the two step shapes that carry the 3-regular N = 200
+contraction, and the 2048-instance mixed-size +-J batch (E_min + exact count)
+against its one-by-one paths.  cpu_baseline is the CPU oracle on all host
+cores (one process per core, each on a bounded prefix of its own instance).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
-  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+  python bench.py --impl reference ...   # the CPU oracle, a bounded sample per step
   python bench.py --workload mixed|cubic|max2sat|sample   # the other workloads (one JSON line each)
 
 Multi-GPU (torchrun): every rank contracts its own instances (weak scaling, no
@@ -51,6 +57,8 @@ def parse():
     ap.add_argument("--mode", default="config", choices=["config", "energy"],
                     help="config: E_min + sigma* (the workload); energy: E_min only (profiling)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the GEMM and mixed-batch sub-records of the default run")
     ap.add_argument("--restarts", type=int, default=ORDER_RESTARTS,
                     help="greedy restarts of the (untimed) order search")
     ap.add_argument("--quiet", action="store_true", help="print only value and kernel shares")
@@ -82,12 +90,12 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def alu_peak_tops(sm_mhz):
-    # 152 SMs x 128 FP32 lanes x clock: one lane-instruction per lane per
-    # clock; a tropical multiply-add is an add and a max, counted as 2 ops,
-    # so the tropical-op peak equals the lane-instruction rate x 2 only when
-    # both run fused; we count 2 ops per MAC against 2 lane-instructions.
-    return 152 * 128 * sm_mhz * 1e6 * 1e-12
+def alu_peak_tops(sm_mhz, sms=None):
+    # SMs x 128 FP32 lanes x clock: one lane-instruction per lane per clock
+    # (the device's SM count unless given)
+    if sms is None:
+        sms = sm_count()
+    return sms * 128 * sm_mhz * 1e6 * 1e-12
 
 
 class Clocks:
@@ -173,74 +181,174 @@ def make_instances(rank, batch, side=L):
             for k in range(batch)]
 
 
-def oracle_sample(inst, budget_s=20.0):
-    """Time the CPU oracle on eliminations at full frontier width, extrapolate to one instance."""
-    import oracle as O
+# ---- CPU oracle baseline: the oracle as it stands (numpy float64 variable
+# elimination, row-by-row order, sigma* by its argmax backtracking), one
+# single-threaded process per host core, each on its own instance.
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def elimination_work(inst, order):
+    """Cumulative table entries of the oracle's eliminations along ``order`` (the
+    union scope of each bucket, q^|scope| entries): its work is proportional to
+    them, which converts a timed prefix of eliminations into a fraction of an
+    instance."""
+    q = inst["q"]
+    scopes = [set(e) for e in inst["edges"].tolist()] + [{i} for i in range(inst["n"])]
+    out, tot = [], 0.0
+    for v in order:
+        bucket = [s for s in scopes if v in s]
+        scopes = [s for s in scopes if v not in s]
+        u = set().union(*bucket)
+        tot += float(q) ** len(u)
+        out.append(tot)
+        scopes.append(u - {v})
+    return out
+
+
+def _oracle_prefix(job):
+    """Worker: the oracle on the first k eliminations of instance `seed` (seconds)."""
+    seed, k = job
     import instances as I
-    order = I.square_sweep_order(L)
-    k0 = L + 1                       # frontier full after the first row
+    import oracle as O
+    inst = I.square_lattice(L, coupling="gauss", field_sigma=FIELD_SIGMA, seed=seed)
     t0 = time.perf_counter()
-    O.solve(inst, order=order, count=False, config=True, max_eliminations=k0)
-    t_head = time.perf_counter() - t0
-    k1 = k0
-    t_full = None
-    while True:
-        k1 = min(L * L, k1 + 8)
+    O.solve(inst, order=I.square_sweep_order(L), count=False, config=True, max_eliminations=k)
+    return time.perf_counter() - t0
+
+
+class OracleBaseline:
+    """Each step: every host core runs the oracle on the first k eliminations of
+    its own 24x24 instance; the instances-worth of work done is the sum of the
+    prefixes' shares of a whole instance's table entries (elimination_work),
+    and the step's time is the wall time until the last core finishes."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        import instances as I
+        self.cores = cores or host_cores()
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(v, "1")
+        # spawn: no fork of a process that may hold a CUDA context
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        inst = I.square_lattice(L, coupling="gauss", field_sigma=FIELD_SIGMA, seed=0)
+        self.work = elimination_work(inst, I.square_sweep_order(L))
+        self.k = L + 1
+
+    def calibrate(self, budget_s):
+        """Choose the prefix length so that a step (every core busy, sharing the
+        host's memory bandwidth) takes about budget_s of wall time."""
+        k0 = L + 5
+        jobs = [(1 + c, k0) for c in range(self.cores)]
+        t0 = max(self.pool.map(_oracle_prefix, jobs, chunksize=1))
+        per = t0 / self.work[k0 - 1]
+        k = k0
+        while k < len(self.work) and self.work[k] * per < budget_s:
+            k += 1
+        self.k = k
+        return k
+
+    def step(self, base_seed=0):
+        jobs = [(base_seed + c, self.k) for c in range(self.cores)]
         t0 = time.perf_counter()
-        O.solve(inst, order=order, count=False, config=True, max_eliminations=k1)
-        t_full = time.perf_counter() - t0
-        if t_full >= budget_s or k1 >= L * L:
-            break
-    per_spin = max(t_full - t_head, 1e-9) / (k1 - k0)
-    est = t_head + per_spin * (L * L - k0)
-    return est, k1, t_full
+        times = self.pool.map(_oracle_prefix, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+        frac = self.work[self.k - 1] / self.work[-1]
+        return self.cores * frac, wall, max(times)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def describe(self):
+        frac = self.work[self.k - 1] / self.work[-1]
+        return (f"CPU oracle (numpy float64 variable elimination, row-by-row order, sigma* by "
+                f"argmax backtracking) on {self.cores} host cores, one single-threaded process "
+                f"per core, each on its own instance: the first {self.k} of {L * L} "
+                f"eliminations, {100 * frac:.2f}% of an instance's table entries (work is "
+                f"proportional to them); value = instances-worth of entries / wall time")
+
+
+def cpu_baseline(budget_s=10.0):
+    ob = OracleBaseline()
+    try:
+        ob.calibrate(budget_s)
+        inst_done, wall, _ = ob.step(base_seed=100)
+        return {"value": inst_done / wall, "unit": "instances/s", "cores": ob.cores,
+                "kind": "oracle", "sample": ob.describe() + f" ({wall:.1f} s wall)"}
+    finally:
+        ob.close()
+
+
+def workload_config(batch, world):
+    return {"workload": WORKLOAD, "global_batch": batch * world,
+            "instances_per_step_per_gpu": batch,
+            "l2": "flushed between timed steps (256 MB write)"}
 
 
 def run_reference(args):
+    """The oracle on the host cores, same metric, unit and config as the native arm;
+    each step a bounded sample (see OracleBaseline) sized to a few seconds."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    inst = make_instances(0, 1)[0]
-    times = []
-    for i in range(args.warmup + args.steps):
-        est, k1, tf = oracle_sample(inst, budget_s=8.0)
-        if i >= args.warmup:
-            times.append(est)
-    val = 1.0 / float(np.mean(times))
-    sample = (f"CPU oracle (numpy float64 variable elimination, row-by-row order) on the first "
-              f"{k1} of {L*L} eliminations of one instance per step, extrapolated to a whole "
-              f"instance from the full-width eliminations")
+    ob = OracleBaseline()
+    try:
+        ob.calibrate(5.0)
+        done, walls = 0.0, []
+        for i in range(args.warmup + args.steps):
+            d, wall, _ = ob.step(base_seed=1000 + i * ob.cores)
+            if i >= args.warmup:
+                done += d
+                walls.append(wall)
+        desc = ob.describe()
+    finally:
+        ob.close()
+    val = done / sum(walls)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "instances/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "ms_per_step": 1e3 * float(np.mean(walls)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": 1, "order": "row-by-row (oracle)"},
-            "cpu_baseline": {"value": val, "unit": "instances/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "config": workload_config(args.batch, world),
+            "cpu_baseline": {"value": val, "unit": "instances/s", "cores": ob.cores,
+                             "kind": "oracle", "sample": desc},
             "e2e": {"value": val, "unit": "instances/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_gemm(args):
-    """Max-plus GEMM through tn_maxplus_gemm: square 4096^3, batched shapes and the dominant
-    step shapes of the 3-regular N = 200 contraction."""
+GEMM_SHAPES = [(1, 4096, 4096, 4096), (64, 512, 512, 512), (16, 1024, 1024, 256),
+               (8, 131072, 1024, 512), (32, 2048, 256, 16384)]
+# the two steps that carry 99% of the multiply-adds of the 3-regular N = 200
+# contraction (greedy order): (batch, M, N, K)
+GEMM_3REG = [(8, 131072, 1024, 512), (32, 2048, 256, 16384)]
+
+
+def sm_count():
+    """SMs of the current device (152 on a GB300; that figure without a device)."""
+    import torch
+    if not torch.cuda.is_available():
+        return 152
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def measure_gemm(shapes, reps=5):
+    """Max-plus GEMM through tn_maxplus_gemm, FP32 and INT32, CUDA events."""
     import torch
     from paper_2008_06888_gb300 import binding as B
-    torch.cuda.set_device(0)
     pk, how = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
-    # non-tensor FP32 peak, an FMA counted as 2 ops: 152 SMs x 128 lanes x 2 x clock
-    peak_ops = 152 * 128 * 2 * sm_max * 1e6
-    issue_peak = 152 * 128 * sm_max * 1e6
+    sms = sm_count()
+    # non-tensor FP32 peak, an FMA counted as 2 ops: SMs x 128 lanes x 2 x clock
+    peak_ops = sms * 128 * 2 * sm_max * 1e6
+    issue_peak = sms * 128 * sm_max * 1e6
     out = {}
-    clocks = Clocks(0)
-    clocks.start()
     for dt in (torch.float32, torch.int32):
-        # square and batched shapes, plus the two steps that carry 99% of the
-        # multiply-adds of the 3-regular N = 200 contraction (greedy order)
-        for (bt, M, N, K) in [(1, 4096, 4096, 4096), (64, 512, 512, 512), (16, 1024, 1024, 256),
-                              (8, 131072, 1024, 512), (32, 2048, 256, 16384)]:
+        for (bt, M, N, K) in shapes:
             if dt == torch.float32:
                 A = torch.randn(bt, M, K, device="cuda")
                 Bm = torch.randn(bt, K, N, device="cuda")
@@ -252,7 +360,6 @@ def run_gemm(args):
                 B.tn_maxplus_gemm(A, Bm, C)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 5
             e0.record()
             for _ in range(reps):
                 B.tn_maxplus_gemm(A, Bm, C)
@@ -262,31 +369,43 @@ def run_gemm(args):
             macs = bt * M * N * K
             ops = 2 * macs / (ms * 1e-3)
             # ALU instructions one multiply-add needs: an add and half a three-input
-            # max (FP32) or an add and a two-input max (INT32, no three-input form)
+            # max (FP32) or an add and a two-input max (INT32)
             ipm = 1.5 if dt == torch.float32 else 2.0
             out[f"{str(dt).split('.')[-1]}_{bt}x{M}x{N}x{K}"] = {
                 "ms": ms, "tropical_Top_s": ops / 1e12, "T_MAC_s": macs / (ms * 1e-3) / 1e12,
                 "frac_of_fp32_nontensor_peak": ops / peak_ops,
                 "alu_issue_frac": ipm * macs / (ms * 1e-3) / issue_peak}
+            del A, Bm, C
+    torch.cuda.empty_cache()
+    return out, {"peak_ops_per_s": peak_ops,
+                 "peak": f"{sms} SMs x 128 FP32 lanes x 2 (FMA = 2 ops) x max SM clock",
+                 "issue_peak_lane_instr_per_s": issue_peak,
+                 "issue_peak": f"{sms} SMs x 128 lanes x max SM clock (one ALU instruction per "
+                               f"lane per clock); alu_issue_frac counts the ALU instructions "
+                               f"the multiply-adds need"}
+
+
+def run_gemm(args):
+    """Max-plus GEMM: square 4096^3, batched shapes and the dominant step shapes of
+    the 3-regular N = 200 contraction."""
+    import torch
+    torch.cuda.set_device(0)
+    clocks = Clocks(0)
+    clocks.start()
+    out, meta = measure_gemm(GEMM_SHAPES)
     clk = clocks.stop()
-    print(json.dumps({"gemm": out, "peak_ops_per_s": peak_ops,
-                      "peak": "152 SMs x 128 FP32 lanes x 2 (FMA = 2 ops) x max SM clock",
-                      "issue_peak_lane_instr_per_s": issue_peak,
-                      "issue_peak": "152 SMs x 128 lanes x max SM clock (one ALU instruction "
-                                    "per lane per clock); alu_issue_frac counts the ALU "
-                                    "instructions the multiply-adds need",
-                      "clocks": clk}), flush=True)
+    print(json.dumps(dict({"gemm": out, "clocks": clk}, **meta)), flush=True)
 
 
-def run_mixed(args):
-    """Mixed batch of +-J square lattices (L uniform in 8..20), E_min and exact count each,
-    through tn_batch_run (grouped batches) against the same instances one by one."""
+def measure_mixed(n_inst, steps, warmup, plain=True):
+    """Mixed batch of +-J square lattices (L uniform in 8..20, base seed 2026), E_min and
+    exact count each, through tn_batch_run (grouped batches), against the same
+    instances one by one (graph-replayed, and the plain path in a child process)."""
     import torch
     import instances as I
     import paper_2008_06888_gb300 as P
     from paper_2008_06888_gb300 import binding as B
-    torch.cuda.set_device(0)
-    insts = I.mixed_square_batch(args.mixed_n, Lmin=8, Lmax=20, seed=2026)
+    insts = I.mixed_square_batch(n_inst, Lmin=8, Lmax=20, seed=2026)
     sgs = [P.SpinGlass(x, order="sweep",
                        seq=I.square_sweep_order(int(round(np.sqrt(x["n"]))))) for x in insts]
     ctxs = [s.ctx for s in sgs]
@@ -302,64 +421,92 @@ def run_mixed(args):
         torch.cuda.synchronize()
         return (time.perf_counter() - t0) / len(sub)
 
-    if args.one_by_one_only:
-        print(json.dumps({"one_by_one_s": one_by_one(), "sample": len(sub)}), flush=True)
-        return
-    for _ in range(args.warmup):
-        st, E, counts, status = B.tn_batch_run(ctxs, limbs_per=4)
-    torch.cuda.synchronize()
-    clocks = Clocks(0)
-    clocks.start()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        st, E, counts, status = B.tn_batch_run(ctxs, limbs_per=4)
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / args.steps
-    clk = clocks.stop()
-    # kernel shares of one batched pass (events around every launch)
-    for c in ctxs:
-        B.tn_profile_reset(c)
-        B.tn_set_profiling(c, True)
-    B.tn_batch_run(ctxs, limbs_per=4)
-    torch.cuda.synchronize()
-    prof = {k: {"launches": 0, "ms": 0.0, "bytes": 0.0, "macs": 0.0} for k in B.KIND_NAMES}
-    for c in ctxs:
-        for i, k in enumerate(B.KIND_NAMES):
-            v = B.tn_profile_get(c, i)
-            for f in prof[k]:
-                prof[k][f] += v[f]
-        B.tn_set_profiling(c, False)
-    total_ms = sum(v["ms"] for v in prof.values())
-    # one by one (each instance its own context, same kernels, no batching), with the
-    # launches of each call replayed from a CUDA graph ...
-    dt1 = one_by_one()
-    # ... and the plain path (every kernel launched directly): a fresh process,
-    # since graph use is fixed per process
-    plain = None
     try:
-        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", "mixed",
-                            "--mixed-n", str(args.mixed_n), "--one-by-one-only"],
-                           env=dict(os.environ, TN_NO_GRAPH="1"), capture_output=True,
-                           text=True, timeout=600)
-        lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
-        if r.returncode == 0 and lines:
-            plain = json.loads(lines[-1])["one_by_one_s"]
-    except Exception:
-        plain = None
-    ok = int(np.sum(status == 0))
-    print(json.dumps({
-        "metric": METRIC, "value": len(insts) / dt, "unit": "instances/s",
-        "workload": f"{len(insts)} +-J square lattices, L uniform in 8..20, E_min + exact count "
-                    f"(3 primes + witness), grouped batches through tn_batch_run",
-        "ms_per_batch": dt * 1e3, "instances_ok": ok,
+        for _ in range(warmup):
+            st, E, counts, status = B.tn_batch_run(ctxs, limbs_per=4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            st, E, counts, status = B.tn_batch_run(ctxs, limbs_per=4)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / steps
+        # kernel shares of one batched pass (events around every launch)
+        for c in ctxs:
+            B.tn_profile_reset(c)
+            B.tn_set_profiling(c, True)
+        B.tn_batch_run(ctxs, limbs_per=4)
+        torch.cuda.synchronize()
+        prof = {k: {"launches": 0, "ms": 0.0, "bytes": 0.0, "macs": 0.0} for k in B.KIND_NAMES}
+        for c in ctxs:
+            for i, k in enumerate(B.KIND_NAMES):
+                v = B.tn_profile_get(c, i)
+                for f in prof[k]:
+                    prof[k][f] += v[f]
+            B.tn_set_profiling(c, False)
+        dt1 = one_by_one()
+        ok = int(np.sum(status == 0))
+    finally:
+        for s_ in sgs:
+            s_.close()
+        torch.cuda.empty_cache()
+    total_ms = sum(v["ms"] for v in prof.values())
+    plain_s = None
+    if plain:
+        # the plain path (every kernel launched directly, no graphs): a fresh
+        # process, since graph use is fixed per process
+        try:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", "mixed",
+                                "--mixed-n", str(n_inst), "--one-by-one-only"],
+                               env=dict(os.environ, TN_NO_GRAPH="1"), capture_output=True,
+                               text=True, timeout=600)
+            lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+            if r.returncode == 0 and lines:
+                plain_s = json.loads(lines[-1])["one_by_one_s"]
+        except Exception:
+            plain_s = None
+    return {
+        "value": len(insts) / dt, "unit": "instances/s",
+        "workload": f"{len(insts)} +-J square lattices, L uniform in 8..20 (base seed 2026), "
+                    f"row-by-row order, E_min + exact count (3 primes + witness), grouped "
+                    f"batches through tn_batch_run",
+        "ms_per_batch": dt * 1e3, "steps": steps, "instances_ok": ok,
         "unbatched_instances_per_s": 1.0 / dt1, "unbatched_sample": len(sub),
         "batched_over_unbatched": (len(insts) / dt) * dt1,
-        "unbatched_plain_instances_per_s": None if plain is None else 1.0 / plain,
-        "batched_over_unbatched_plain": None if plain is None else (len(insts) / dt) * plain,
-        "roofline": roofline_of(prof, clk),
+        "unbatched_plain_instances_per_s": None if plain_s is None else 1.0 / plain_s,
+        "batched_over_unbatched_plain": None if plain_s is None else (len(insts) / dt) * plain_s,
+        "roofline": roofline_of(prof, None),
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
-                        "share": v["ms"] / max(total_ms, 1e-9)} for k, v in prof.items()},
-        "clocks": clk}), flush=True)
+                        "share": v["ms"] / max(total_ms, 1e-9)} for k, v in prof.items()}}
+
+
+def run_mixed(args):
+    import torch
+    torch.cuda.set_device(0)
+    if args.one_by_one_only:
+        import instances as I
+        import paper_2008_06888_gb300 as P
+        insts = I.mixed_square_batch(args.mixed_n, Lmin=8, Lmax=20, seed=2026)
+        sub = list(range(0, len(insts), max(1, len(insts) // 128)))
+        sgs = {k: P.SpinGlass(insts[k], order="sweep",
+                              seq=I.square_sweep_order(int(round(np.sqrt(insts[k]["n"])))))
+               for k in sub}
+        for k in sub[:4]:
+            sgs[k].count(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in sub:
+            sgs[k].count(3)
+        torch.cuda.synchronize()
+        print(json.dumps({"one_by_one_s": (time.perf_counter() - t0) / len(sub),
+                          "sample": len(sub)}), flush=True)
+        return
+    clocks = Clocks(0)
+    clocks.start()
+    rec = measure_mixed(args.mixed_n, args.steps, args.warmup)
+    clk = clocks.stop()
+    rec = dict({"metric": METRIC}, **rec)
+    rec["clocks"] = clk
+    print(json.dumps(rec), flush=True)
 
 
 def roofline_of(prof, clk):
@@ -374,7 +521,7 @@ def roofline_of(prof, clk):
         peak = alu_peak_tops(pk.get("sm_max_mhz", 2070.0))
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
                 "frac": achieved / peak, "traffic": None, "kernel": dom,
-                "peak_source": "152 SMs x 128 lanes x max clock (one lane-op per clock)"}
+                "peak_source": "SMs x 128 lanes x max clock (one lane-op per clock)"}
     achieved = d["bytes"] / launches / (avg_ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": dom,
@@ -667,7 +814,8 @@ def main():
     launches = max(d["launches"], 1)
     avg_ms = d["ms"] / launches
     bound = KIND_BOUND[dom]
-    tropical_gops = 2 * total["macs"] / (ms / 1e3) / 1e9
+    sms = sm_count()
+    tropical_ops = 2 * total["macs"] / (ms / 1e3)
     if bound == "hbm":
         achieved = d["bytes"] / launches / (avg_ms / 1e3) / 1e9
         peak = pk["hbm_gbs"]
@@ -676,40 +824,54 @@ def main():
                 "kernel": dom, "peak_source": how,
                 "bytes_per_launch": d["bytes"] / launches, "avg_launch_ms": avg_ms}
     else:
-        sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
         achieved = 2 * d["macs"] / launches / (avg_ms / 1e3) / 1e12
         peak = alu_peak_tops(pk.get("sm_max_mhz", 2070.0))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
                 "frac": achieved / peak, "traffic": traffic_from_profiles(dom), "kernel": dom,
-                "peak_source": "152 SMs x 128 lanes x max clock (one lane-op per clock)"}
+                "peak_source": f"{sms} SMs x 128 lanes x max clock (one lane-op per clock)"}
+    # the metric's own "% of the FP32 non-tensor peak" for the whole step: tropical
+    # ops (a multiply-add = 2) over SMs x 128 lanes x 2 x clock
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = sms * 128 * 2 * sm_max * 1e6
+    tropical = {"gop_s": tropical_ops / 1e9, "macs_per_step": total["macs"] / args.steps,
+                "frac_of_fp32_nontensor_peak": tropical_ops / fp32_peak,
+                "peak_gop_s": fp32_peak / 1e9,
+                "peak": f"{sms} SMs x 128 FP32 lanes x 2 (FMA = 2 ops) x {sm_max:.0f} MHz"}
+    sg.close()
+    del Jd, hd, flush
+    torch.cuda.empty_cache()
+
+    # sub-records measured in the same run (rank 0, one GPU): the max-plus GEMM on
+    # the 3-regular N = 200 step shapes and the mixed-size batch of +-J lattices
+    sub = {}
+    if rank == 0 and world == 1 and not args.no_sub and args.L == L:
+        g, meta = measure_gemm(GEMM_3REG, reps=3)
+        sub["gemm_3regular_steps"] = dict({"shapes": g}, **meta)
+        sub["mixed_batch"] = measure_mixed(2048, steps=3, warmup=2)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and args.L == L:
-        est, k1, tf = oracle_sample(insts[0], budget_s=15.0)
-        cpu = {"value": 1.0 / est, "unit": "instances/s", "cores": 1, "kind": "oracle",
-               "sample": f"numpy float64 variable elimination, first {k1} of {L*L} "
-                         f"eliminations of one instance ({tf:.1f} s), extrapolated"}
+        cpu = cpu_baseline(10.0)
 
     if rank == 0:
+        cfg = workload_config(args.batch, world)
+        if not (args.L == L and args.mode == "config"):
+            cfg["workload"] = f"square{args.L}x{args.L} Gaussian, mode {args.mode} (profiling run)"
         line = {"metric": METRIC, "value": value, "unit": "instances/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD if (args.L == L and args.mode == "config") else
-                           f"square{args.L}x{args.L} Gaussian, mode {args.mode} (profiling run)",
-                           "global_batch": args.batch * world,
-                           "instances_per_step_per_gpu": args.batch,
-                           "l2": "flushed between timed steps (256 MB write)",
-                           "log2_peak_elements": sg.log2_peak, "log2_macs": sg.log2_ops},
-                "tropical_gops": tropical_gops,
+                "config": cfg,
+                "plan": {"log2_peak_elements": sg.log2_peak, "log2_macs": sg.log2_ops},
+                "tropical": tropical,
                 "unbatched_instances_per_s": unbatched,
                 "roofline": roof,
                 "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
                                 "share": v["ms"] / max(ms_p, 1e-9)} for k, v in prof.items()},
                 "gpu_launches": total["launches"],
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
+        line.update(sub)
         print(json.dumps(line), flush=True)
-    sg.close()
     if world > 1:
         dist.destroy_process_group()
 

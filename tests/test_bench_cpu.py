@@ -58,3 +58,21 @@ def test_traffic_only_for_matching_sources(monkeypatch):
     monkeypatch.setattr(bench, "sources_hash", lambda: "0000000000000000")
     assert bench.traffic_from_profiles("chain") is None
     assert bench.traffic_from_profiles("gate") is None       # no profile for it
+
+
+def test_elimination_work_counts_table_entries():
+    # 2x2 lattice eliminated 0, 1, 2, 3: bucket scopes {0,1,2}, {1,2,3}, {2,3}, {3}
+    import instances as I
+    inst = I.square_lattice(2, coupling="pm1", seed=0)
+    assert bench.elimination_work(inst, [0, 1, 2, 3]) == [8.0, 16.0, 20.0, 22.0]
+    w = bench.elimination_work(I.square_lattice(24, coupling="gauss", seed=0),
+                               I.square_sweep_order(24))
+    assert len(w) == 576 and all(b > a for a, b in zip(w, w[1:]))
+    # the row sweep's frontier holds 25 spins at its widest
+    assert max(b - a for a, b in zip(w, w[1:])) == 2.0 ** 25
+
+
+def test_reference_arm_reports_the_native_config():
+    cfg = bench.workload_config(48, 1)
+    assert cfg["workload"] == bench.WORKLOAD and cfg["global_batch"] == 48
+    assert set(cfg) == {"workload", "global_batch", "instances_per_step_per_gpu", "l2"}

@@ -12,12 +12,14 @@
 #include <map>
 #include <atomic>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 #include <cstdlib>
 #include <stdint.h>
 
 #include "kernels.h"
+#include "perm_bits.h"
 #include "chain_dev.cuh"
 
 namespace tn {
@@ -71,6 +73,38 @@ int num_sms() {
     return 152;
   cache[dev].store(v, std::memory_order_relaxed);
   return v;
+}
+
+// Resident blocks of `kernel` on the device (occupancy of its registers and
+// shared memory), queried once per kernel.
+template <typename K>
+static int64_t resident_slots(K kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, int> per_sm;   // (kernel, device)
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::pair<const void *, int> key(reinterpret_cast<const void *>(kernel), dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = per_sm.find(key);
+  if (it == per_sm.end()) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem) != cudaSuccess ||
+        v <= 0)
+      v = 1;
+    it = per_sm.emplace(key, v).first;
+  }
+  return (int64_t)it->second * num_sms();
+}
+
+// Blocks per instance of a grid-stride kernel with `need` blocks of work per
+// instance, B instances and `slots` resident blocks: whole waves when a
+// multiple of the slots is within 16 waves, else about 8 waves so the last,
+// partial one is a small part of the launch.
+static int64_t wave_blocks(int64_t need, int B, int64_t slots) {
+  if (need * B <= slots) return need;
+  const int64_t whole = slots / std::gcd(slots, (int64_t)B);
+  if (whole <= need && whole * B <= 16 * slots) return whole;
+  return std::min(need, std::max<int64_t>(1, 8 * slots / B));
 }
 
 static inline int grid_for(int64_t n, int threads, int max_blocks = 0) {
@@ -584,14 +618,14 @@ static bool launch_gate2c(const GateParams &p, const T *A, const T *B, T *C, con
       (p.planeA | p.planeC) & 1)
     return false;
   const int64_t nq = p.outer >> 2;
-  int64_t blocks = (nq + 255) / 256;
-  const int64_t cap = std::max<int64_t>(1, num_sms() * 8 / bt.B);
-  if (blocks > cap) blocks = cap;
-  dim3 grid((unsigned)blocks, bt.B);
-#define TN_G2C(KS_, NS_)                                                                   \
-  if (p.Ks == KS_ && p.Ns == NS_) {                                                       \
-    k_gate2c<T, KS_, NS_, 4><<<grid, 256, 0, st>>>(p, g, A, B, C, nA, nB, nC, ps, bt.ib); \
-    return true;                                                                          \
+  const int64_t need = (nq + 255) / 256;
+#define TN_G2C(KS_, NS_)                                                                          \
+  if (p.Ks == KS_ && p.Ns == NS_) {                                                              \
+    const int64_t blocks =                                                                       \
+        wave_blocks(need, bt.B, resident_slots(k_gate2c<T, KS_, NS_, 4>, 256, 0));               \
+    k_gate2c<T, KS_, NS_, 4><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(p, g, A, B, C, nA, nB, \
+                                                                          nC, ps, bt.ib);        \
+    return true;                                                                                 \
   }
   TN_G2C(1, 1)
   TN_G2C(1, 2)
@@ -607,14 +641,12 @@ static bool launch_gate2(const GateParams &p, const T *A, const T *B, T *C, cons
   Gate2 g;
   if (std::getenv("TN_NO_GATE2") || !gate2_form(p, A, B, C, bt.ib, sizeof(T), &g)) return false;
   const int64_t nq = p.outer >> 2;
-  int64_t blocks = (nq + 511) / 512;
-  const int64_t cap = std::max<int64_t>(1, num_sms() * 8 / bt.B);
-  if (blocks > cap) blocks = cap;
-  dim3 grid((unsigned)blocks, bt.B);
-#define TN_G2(KS_, NS_)                                                            \
-  if (p.Ks == KS_ && p.Ns == NS_) {                                                \
-    k_gate2<T, KS_, NS_><<<grid, 256, 0, st>>>(p, g, A, B, C, bt.ib);              \
-    return true;                                                                   \
+  const int64_t need = (nq + 511) / 512;
+#define TN_G2(KS_, NS_)                                                                        \
+  if (p.Ks == KS_ && p.Ns == NS_) {                                                            \
+    const int64_t blocks = wave_blocks(need, bt.B, resident_slots(k_gate2<T, KS_, NS_>, 256, 0)); \
+    k_gate2<T, KS_, NS_><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(p, g, A, B, C, bt.ib);  \
+    return true;                                                                               \
   }
   TN_G2(1, 1)
   TN_G2(1, 2)
@@ -979,10 +1011,184 @@ static cudaError_t run_mpgemm(Dtype dt, const GemmParams &p, const void *A, cons
   return cudaGetLastError();
 }
 
+// ---- split-K form for steps with a handful of outputs and a long K (the
+// contraction of two big tensors into the scalar root, or a few states):
+// blocks take K ranges, reduce their maxima in shared memory and combine
+// them with atomicMax on an order-preserving unsigned key written over C,
+// decoded in place afterwards (max is exact, so the result equals the tiled
+// kernel's).  Counting planes combine per-block sums mod p with a
+// compare-and-swap add.
+constexpr int kSplitOut = 16;          // largest batch * M * N of the split-K form
+constexpr int64_t kSplitMinK = 1 << 14;
+
+static bool splitk_ok(const GemmParams &p) {
+  return p.batch * p.M * p.N <= kSplitOut && p.K >= kSplitMinK;
+}
+
+__device__ __forceinline__ uint32_t order_key(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ uint32_t order_key(int32_t x) { return (uint32_t)x ^ 0x80000000u; }
+__device__ __forceinline__ void from_key(uint32_t k, float *x) {
+  *x = __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+__device__ __forceinline__ void from_key(uint32_t k, int32_t *x) { *x = (int32_t)(k ^ 0x80000000u); }
+
+__device__ __forceinline__ void splitk_out(const GemmParams &p, int o, int64_t *oa, int64_t *ob,
+                                           int64_t *oc) {
+  const int64_t n = o % p.N, m = (o / p.N) % p.M, b = o / (p.N * p.M);
+  *oa = b * p.sAb + m * p.sAm;
+  *ob = b * p.sBb + n * p.sBn;
+  *oc = b * p.sCb + m * p.sCm + n * p.sCn;
+}
+
+// phase 0: keys of the tropical zero; 2: decode keys into values
+template <typename T>
+__global__ void k_splitk_keys(const GemmParams p, T *C, int phase, int64_t ib) {
+  C = inst_ptr(C, ib);
+  const int o = threadIdx.x;
+  if (o >= p.batch * p.M * p.N) return;
+  int64_t oa, ob, oc;
+  splitk_out(p, o, &oa, &ob, &oc);
+  uint32_t *kc = reinterpret_cast<uint32_t *>(C + oc);
+  if (phase == 0) *kc = 0u;
+  else from_key(*kc, C + oc);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mpgemm_splitk(const GemmParams p, const T *__restrict__ A,
+                                                       const T *__restrict__ B, T *C, int64_t ib) {
+  A = inst_ptr(A, ib);
+  B = inst_ptr(B, ib);
+  C = inst_ptr(C, ib);
+  const int nout = (int)(p.batch * p.M * p.N);
+  __shared__ uint32_t red[kSplitOut][8];
+  for (int o = 0; o < nout; ++o) {
+    int64_t oa, ob, oc;
+    splitk_out(p, o, &oa, &ob, &oc);
+    uint32_t best = 0u;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p.K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+      const T v = A[oa + k * p.sAk] + B[ob + k * p.sBk];
+      best = max(best, order_key(v));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, d));
+    if ((threadIdx.x & 31) == 0) red[o][threadIdx.x >> 5] = best;
+  }
+  __syncthreads();
+  if (threadIdx.x < nout) {
+    uint32_t best = 0u;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) best = max(best, red[threadIdx.x][w]);
+    int64_t oa, ob, oc;
+    splitk_out(p, threadIdx.x, &oa, &ob, &oc);
+    atomicMax(reinterpret_cast<uint32_t *>(C + oc), best);
+  }
+}
+
+// counting planes: n_i[o] = sum over k with A + B == C of nA_i nB_i (mod p_i)
+template <typename T>
+__global__ void k_splitk_count_zero(const GemmParams p, uint64_t *nC, int64_t ib) {
+  nC = inst_ptr(nC, ib);
+  const int o = threadIdx.x;
+  if (o >= p.batch * p.M * p.N) return;
+  int64_t oa, ob, oc;
+  splitk_out(p, o, &oa, &ob, &oc);
+  for (int i = 0; i < p.P; ++i) nC[i * p.planeC + oc] = 0ull;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_count_splitk(
+    const GemmParams p, const T *__restrict__ A, const T *__restrict__ B, const T *__restrict__ C,
+    const uint64_t *__restrict__ nA, const uint64_t *__restrict__ nB, uint64_t *nC,
+    const PrimeSet ps, int64_t ib) {
+  A = inst_ptr(A, ib);
+  B = inst_ptr(B, ib);
+  C = inst_ptr(C, ib);
+  nA = inst_ptr(nA, ib);
+  nB = inst_ptr(nB, ib);
+  nC = inst_ptr(nC, ib);
+  const int nout = (int)(p.batch * p.M * p.N);
+  __shared__ uint64_t red[TN_MAX_PRIMES][8];
+  for (int o = 0; o < nout; ++o) {
+    int64_t oa, ob, oc;
+    splitk_out(p, o, &oa, &ob, &oc);
+    const T x = C[oc];
+    uint64_t cnt[TN_MAX_PRIMES];
+#pragma unroll
+    for (int i = 0; i < TN_MAX_PRIMES; ++i) cnt[i] = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p.K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+      if (A[oa + k * p.sAk] + B[ob + k * p.sBk] == x) {
+#pragma unroll
+        for (int i = 0; i < TN_MAX_PRIMES; ++i)
+          if (i < p.P)
+            cnt[i] = addmod61(cnt[i], mulmod61(nA[i * p.planeA + oa + k * p.sAk],
+                                               nB[i * p.planeB + ob + k * p.sBk], ps.c[i]),
+                              ps.c[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < TN_MAX_PRIMES; ++i) {
+      if (i >= p.P) break;
+      uint64_t v = cnt[i];
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) v = addmod61(v, __shfl_xor_sync(0xffffffffu, v, d), ps.c[i]);
+      if ((threadIdx.x & 31) == 0) red[i][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < p.P) {
+      const int i = threadIdx.x;
+      uint64_t v = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = addmod61(v, red[i][w], ps.c[i]);
+      if (v) {
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(nC + i * p.planeC + oc);
+        unsigned long long old = *dst, assumed;
+        do {
+          assumed = old;
+          old = atomicCAS(dst, assumed, (unsigned long long)addmod61(assumed, v, ps.c[i]));
+        } while (old != assumed);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static unsigned splitk_blocks(const GemmParams &p, const Batch &bt) {
+  const int64_t want = (p.K + 256 * 16 - 1) / (256 * 16);   // about 16 k per thread
+  const int64_t cap = std::max<int64_t>(1, (int64_t)num_sms() * 8 / bt.B);
+  return (unsigned)std::max<int64_t>(1, std::min(want, cap));
+}
+
+template <typename T>
+static cudaError_t launch_splitk(const GemmParams &p, const T *A, const T *B, T *C,
+                                 const Batch &bt, cudaStream_t st) {
+  k_splitk_keys<T><<<dim3(1, bt.B), 32, 0, st>>>(p, C, 0, bt.ib);
+  k_mpgemm_splitk<T><<<dim3(splitk_blocks(p, bt), bt.B), 256, 0, st>>>(p, A, B, C, bt.ib);
+  k_splitk_keys<T><<<dim3(1, bt.B), 32, 0, st>>>(p, C, 2, bt.ib);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_count_splitk(const GemmParams &p, const T *A, const T *B, const T *C,
+                                       const uint64_t *nA, const uint64_t *nB, uint64_t *nC,
+                                       const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
+  k_splitk_count_zero<T><<<dim3(1, bt.B), 32, 0, st>>>(p, nC, bt.ib);
+  k_gemm_count_splitk<T><<<dim3(splitk_blocks(p, bt), bt.B), 256, 0, st>>>(p, A, B, C, nA, nB, nC,
+                                                                           ps, bt.ib);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mpgemm(Dtype dt, const GemmParams &p, const void *A, const void *B, void *C,
                           const Batch &bt, cudaStream_t st) {
   const int64_t tiles = p.batch * ((p.M + GBM - 1) / GBM) * ((p.N + GBN - 1) / GBN);
   if (tiles == 0) return cudaSuccess;
+  if (splitk_ok(p)) {
+    if (dt == DT_F32)
+      return launch_splitk(p, (const float *)A, (const float *)B, (float *)C, bt, st);
+    return launch_splitk(p, (const int32_t *)A, (const int32_t *)B, (int32_t *)C, bt, st);
+  }
   const bool v16 = mpgemm16_ok(p, A, B) && bt.ib % 16 == 0 && std::getenv("TN_GEMM_SCALAR") == nullptr;
   // a forced candidate ("variant per_sm"), e.g. for tests
   if (const char *f = std::getenv("TN_GEMM_TILE")) {
@@ -1082,6 +1288,13 @@ cudaError_t launch_gemm_count(Dtype dt, const GemmParams &p, const void *xA, con
                               const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
   int64_t total = p.batch * p.M * p.N;
   if (total == 0) return cudaSuccess;
+  if (splitk_ok(p)) {
+    if (dt == DT_F32)
+      return launch_count_splitk(p, (const float *)xA, (const float *)xB, (const float *)xC, nA,
+                                 nB, nC, ps, bt, st);
+    return launch_count_splitk(p, (const int32_t *)xA, (const int32_t *)xB, (const int32_t *)xC,
+                               nA, nB, nC, ps, bt, st);
+  }
   dim3 blocks(grid_for(total, 256), bt.B);
   if (dt == DT_F32)
     k_gemm_count<float><<<blocks, 256, 0, st>>>(p, (const float *)xA, (const float *)xB,
@@ -1114,9 +1327,78 @@ __global__ void k_permute(const PermParams p, const E *__restrict__ in, E *__res
   }
 }
 
+// ---- q = 2: tiled bit-permutation transpose (PermBits, perm_bits.h).
+
+__device__ __forceinline__ int perm_swz(const PermBits &pb, int L) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    if (i < pb.nsw) L ^= ((L >> (5 + pb.sw_row[i])) & 1) << pb.sw_bank[i];
+  return L;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(256) k_permute2(const PermBits pb, const E *__restrict__ in,
+                                                  E *__restrict__ out, int64_t planeIn,
+                                                  int64_t planeOut, int64_t ib) {
+  // blockIdx.y: residue plane, blockIdx.z: instance
+  const E *src = reinterpret_cast<const E *>(reinterpret_cast<const char *>(in) + blockIdx.z * ib) +
+                 blockIdx.y * planeIn;
+  E *dst = reinterpret_cast<E *>(reinterpret_cast<char *>(out) + blockIdx.z * ib) +
+           blockIdx.y * planeOut;
+  __shared__ E tile[1024];
+  const int n = 1 << pb.nT;
+  // this thread's elements of every tile: local index j = tid + 256 i
+  int rl[4], wl[4];
+  int64_t ro[4], wo[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int j = threadIdx.x + 256 * i;
+    int L = 0;
+    int64_t oi = 0, oo = 0;
+    for (int t = 0; t < pb.nT; ++t)
+      if ((j >> t) & 1) {
+        L |= 1 << pb.rd_local[t];
+        oi += int64_t(1) << pb.rd_in[t];
+        oo += int64_t(1) << pb.wr_out[t];
+      }
+    rl[i] = perm_swz(pb, L);
+    ro[i] = oi;
+    wl[i] = perm_swz(pb, j);
+    wo[i] = oo;
+  }
+  for (int64_t tau = blockIdx.x; tau < pb.tiles; tau += gridDim.x) {
+    int64_t bin = 0, bout = 0;
+    for (int g = 0; g < pb.nseg; ++g) {
+      const int64_t v = (tau >> pb.seg_t[g]) & ((int64_t(1) << pb.seg_len[g]) - 1);
+      bin += v << pb.seg_in[g];
+      bout += v << pb.seg_out[g];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (threadIdx.x + 256 * i < n) tile[rl[i]] = src[bin + ro[i]];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (threadIdx.x + 256 * i < n) dst[bout + wo[i]] = tile[wl[i]];
+    __syncthreads();
+  }
+}
+
 cudaError_t launch_permute(const PermParams &p, const void *xin, void *xout, const uint64_t *nin,
                            uint64_t *nout, const Batch &bt, cudaStream_t st) {
   if (p.total == 0) return cudaSuccess;
+  PermBits pb;
+  if (perm_bits(p, &pb)) {
+    // a few tiles per block; instances and residue planes on the other grid axes
+    const int64_t per_inst = std::max<int64_t>(1, (int64_t)num_sms() * 8 / bt.B);
+    const unsigned gx = (unsigned)std::min<int64_t>(pb.tiles, per_inst);
+    k_permute2<uint32_t><<<dim3(gx, 1, bt.B), 256, 0, st>>>(pb, (const uint32_t *)xin,
+                                                             (uint32_t *)xout, 0, 0, bt.ib);
+    if (p.P > 0)
+      k_permute2<uint64_t><<<dim3(gx, p.P, bt.B), 256, 0, st>>>(pb, nin, nout, p.planeIn,
+                                                                p.planeOut, bt.ib);
+    return cudaGetLastError();
+  }
   int blocks = grid_for(p.total, 256);
   k_permute<uint32_t><<<dim3(blocks, 1, bt.B), 256, 0, st>>>(p, (const uint32_t *)xin,
                                                              (uint32_t *)xout, 0, 0, bt.ib);
@@ -2057,9 +2339,10 @@ cudaError_t launch_rchain_count(Dtype dt, const ChainParams &p, const char *aren
                                 const void *Ax, const uint64_t *An, void *Cx, uint64_t *Cn,
                                 const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
   if (p.t != 3 || p.P != 4) return cudaErrorInvalidValue;
-  int64_t blocks = (p.outer + 255) / 256;
-  const int64_t cap = std::max<int64_t>(1, num_sms() * 2 * 4 / bt.B);
-  if (blocks > cap) blocks = cap;
+  const int64_t need = (p.outer + 255) / 256;
+  const int64_t blocks =
+      dt == DT_F32 ? wave_blocks(need, bt.B, resident_slots(k_rchain_count<float, 3, 4>, 256, 0))
+                   : wave_blocks(need, bt.B, resident_slots(k_rchain_count<int32_t, 3, 4>, 256, 0));
   if (dt == DT_F32)
     k_rchain_count<float, 3, 4><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(
         p, reinterpret_cast<const float *>(arena), reinterpret_cast<const uint64_t *>(arena),

@@ -18,7 +18,9 @@ def built():
 
 
 SHAPES = [(1, 1, 1, 1), (2, 5, 7, 3), (1, 128, 128, 16), (3, 130, 67, 33), (1, 257, 129, 80),
-          (4, 64, 300, 17), (1, 1, 500, 257), (2, 256, 384, 48)]
+          (4, 64, 300, 17), (1, 1, 500, 257), (2, 256, 384, 48),
+          # a few outputs over a long K: the split-K form (reduction to the root)
+          (1, 1, 1, 1 << 16), (2, 2, 3, 1 << 15), (1, 4, 4, 20001)]
 
 
 @pytest.mark.parametrize("dtype", ["float32", "int32"])

@@ -635,3 +635,34 @@ def test_kernel_mix_transposes_gemms_and_counting_gemms_run():
         assert E2 == o["E"] and O.energy(inst, st) == o["E"]
     finally:
         sg.close()
+
+
+def test_chimera5_counts_with_split_k_root_step():
+    """Chimera 5x5 cells in cell-row order: the last step contracts two 2^20-element
+    tensors into the root scalar, a GEMM step with one output and K = 2^20 that
+    runs in the split-K form (values and counting planes).  E_min and the count
+    agree with the oracle, and the traced state reaches E_min."""
+    inst = I.chimera(5, coupling="pm1", seed=7)
+    o = O.solve(inst, order=I.chimera_sweep_order(5), config=False)
+    sg = P.SpinGlass(inst, order="sweep", seq=I.chimera_sweep_order(5))
+    try:
+        assert sg.energy() == o["E"]
+        c, _, E = sg.count(3)
+        assert (E, c) == (o["E"], o["count"])
+        st, E2 = gpu_state(sg)
+        assert E2 == o["E"] and O.energy(inst, st) == o["E"]
+    finally:
+        sg.close()
+
+
+def test_chimera8_planted_energy():
+    """The 512-spin chimera of 8x8 cells (Sec. IV), Mattis-planted: E_min = -sum|J|
+    = -1472 along the cell-row order (peak 2^33 elements, a 103 GB energy arena;
+    the root step contracts two 2^32-element tensors in the split-K form)."""
+    inst, tau = I.planted(I.chimera(8, coupling="pm1", seed=3), seed=4)
+    assert len(inst["J"]) == 1472
+    sg = P.SpinGlass(inst, order="sweep", seq=I.chimera_sweep_order(8))
+    try:
+        assert sg.energy() == -1472.0
+    finally:
+        sg.close()

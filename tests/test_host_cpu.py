@@ -5,7 +5,8 @@ planner and program builder (no GPU):
   evaluate exactly like the original gate lists;
 - tests/host/tile_check.cpp: the coalesced tile copies of compiled chains put
   every element where its owning thread reads it, without bank conflicts;
-- tests/host/sample_check.cpp: the ground-state sampler with brute-force counts."""
+- tests/host/sample_check.cpp: the ground-state sampler with brute-force counts;
+- tests/host/perm_check.cpp: the index map of the tiled q = 2 transpose."""
 import os
 import shutil
 import subprocess
@@ -73,3 +74,18 @@ def test_ground_state_sampler_with_brute_force_counts(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=240)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.strip().splitlines()[-1].endswith("bad 0")
+
+
+@pytest.mark.timeout(300)
+def test_tiled_transpose_map(tmp_path):
+    """tests/host/perm_check.cpp: the q = 2 tiled transpose (k_permute2) writes every
+    output element once from the element the permutation defines, with coalesced
+    32-element warp accesses and no shared-memory bank conflicts."""
+    if shutil.which("g++") is None:
+        pytest.skip("g++ missing")
+    exe = str(tmp_path / "perm_check")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I", CSRC,
+                    os.path.join(ROOT, "tests", "host", "perm_check.cpp"), "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=240)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "wrong 0 bank_conflicts 0 uncoalesced 0" in r.stdout

@@ -243,11 +243,16 @@ tn_status tn_count_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
 
 /*
  * tn_batch_run -- many independent instances, each already built and ordered
- *   (possibly of different sizes).  Contexts with the same graph, dtype and
- *   plan are grouped and each group runs as one batch (tn_count_batch with 3
- *   primes + witness, or tn_energy_batch when limbs == NULL) on the group's
- *   first context.  Outputs per instance k: E[k]; limbs[k*limbs_per ...]; and
- *   status[k].  Returns the first non-OK status, else TN_OK.
+ *   (possibly of different sizes).  Contexts with the same graph, dtype,
+ *   energy map and contraction steps (compared exactly) are grouped and each
+ *   group runs as one batch (as tn_count_batch with 3 primes + witness, or
+ *   tn_energy_batch when limbs == NULL) on the group's first context.  All
+ *   groups are queued before any is waited for, largest first, on a pool of
+ *   non-blocking streams of the library (one stream while any group's context
+ *   is profiling), after the work already queued on each first context's
+ *   stream; the call returns when every result is on the host.  Outputs per
+ *   instance k: E[k]; limbs[k*limbs_per ...]; and status[k].  Returns the
+ *   first non-OK status, else TN_OK.
  */
 tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limbs,
                        int32_t limbs_per, int32_t *status);

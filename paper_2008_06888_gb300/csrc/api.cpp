@@ -12,6 +12,7 @@
 #include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -976,6 +977,82 @@ tn_status tn_config_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h
   return TN_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Non-blocking streams of tn_batch_run, created once per device.
+constexpr int kBatchStreams = 4;
+tn_status batch_streams(tn_ctx *ctx, std::vector<cudaStream_t> *out) {
+  static std::mutex mu;
+  static std::map<int, std::vector<cudaStream_t>> pools;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  std::vector<cudaStream_t> &v = pools[dev];
+  while ((int)v.size() < kBatchStreams) {
+    cudaStream_t st;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    v.push_back(st);
+  }
+  *out = v;
+  return TN_OK;
+}
+
+// Pinned host staging of the calling thread (grown as needed, kept for reuse).
+tn_status pinned_stage(tn_ctx *ctx, size_t bytes, char **out) {
+  thread_local char *buf = nullptr;
+  thread_local size_t cap = 0;
+  if (bytes > cap) {
+    if (buf) cudaFreeHost(buf);
+    buf = nullptr;
+    cap = 0;
+    const size_t want = std::max(bytes, (size_t)1 << 20);
+    CK(cudaHostAlloc(reinterpret_cast<void **>(&buf), want, cudaHostAllocDefault));
+    cap = want;
+  }
+  *out = buf;
+  return TN_OK;
+}
+
+// E, counts and statuses of B instances from their staged root values (raw:
+// 4 bytes each) and residues (res[i * B + b], plane i, the last the witness).
+tn_status finish_counts(tn_ctx *ctx, int B, int n_primes, const char *raw, const uint64_t *res,
+                        uint64_t *limbs, int32_t limbs_per, double *E, int32_t *status) {
+  const int P = n_primes + 1;
+  tn_status first = TN_OK;
+  for (int b = 0; b < B; ++b) {
+    if (E) E[b] = root_energy(ctx, raw + 4 * b);
+    std::vector<uint64_t> r(P), v;
+    for (int i = 0; i < P; ++i) r[i] = res[(size_t)i * B + b];
+    tn_status sb = count_from_residues(ctx, r, n_primes, &v);
+    if (sb == TN_OK && (int)v.size() > limbs_per) {
+      sb = TN_EINVAL;
+      fail(ctx, sb, "limbs_per too small for a count");
+    }
+    uint64_t *out = limbs + (int64_t)b * limbs_per;
+    for (int i = 0; i < limbs_per; ++i) out[i] = (sb == TN_OK && i < (int)v.size()) ? v[i] : 0;
+    if (status) status[b] = sb;
+    if (sb != TN_OK && first == TN_OK) first = sb;
+  }
+  return first;
+}
+
+// queue the copies of B roots (and P residue planes) of a program's batch to host staging
+tn_status stage_results(tn_ctx *ctx, const Program &p, int B, int P, char *raw, uint64_t *res) {
+  CK(cudaMemcpy2DAsync(raw, 4, ctx->d_arena + abs_off(p, p.root), batch_stride(p), 4, B,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  const char *rbase = ctx->d_arena + p.bufs[p.root.buf].off + p.root.noff;
+  for (int i = 0; i < P; ++i)
+    CK(cudaMemcpy2DAsync(res + (size_t)i * B, 8, rbase + (int64_t)i * p.root.plane * 8,
+                         batch_stride(p), 8, B, cudaMemcpyDeviceToHost, ctx->stream));
+  return TN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 tn_status tn_count_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
                          int32_t on_device, int32_t n_primes, uint64_t *limbs, int32_t limbs_per,
                          double *E, int32_t *status) {
@@ -990,30 +1067,11 @@ tn_status tn_count_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
   tn_status s = batch_setup(ctx, B, J, h, on_device, PM_COUNT, P, &p, &ra);
   if (s != TN_OK) return s;
   if ((s = run_program(ctx, *p, 0, -1, ra)) != TN_OK) return s;
-  std::vector<char> raw;
-  if ((s = batch_roots(ctx, *p, B, &raw)) != TN_OK) return s;
+  std::vector<char> raw((size_t)B * 4);
   std::vector<uint64_t> res((size_t)P * B);
-  const char *rbase = ctx->d_arena + p->bufs[p->root.buf].off + p->root.noff;
-  for (int i = 0; i < P; ++i)
-    CK(cudaMemcpy2DAsync(res.data() + (size_t)i * B, 8, rbase + (int64_t)i * p->root.plane * 8,
-                         batch_stride(*p), 8, B, cudaMemcpyDeviceToHost, ctx->stream));
+  if ((s = stage_results(ctx, *p, B, P, raw.data(), res.data())) != TN_OK) return s;
   CK(cudaStreamSynchronize(ctx->stream));
-  tn_status first = TN_OK;
-  for (int b = 0; b < B; ++b) {
-    if (E) E[b] = root_energy(ctx, raw.data() + 4 * b);
-    std::vector<uint64_t> r(P), v;
-    for (int i = 0; i < P; ++i) r[i] = res[(size_t)i * B + b];
-    tn_status sb = count_from_residues(ctx, r, n_primes, &v);
-    if (sb == TN_OK && (int)v.size() > limbs_per) {
-      sb = TN_EINVAL;
-      fail(ctx, sb, "limbs_per too small for a count");
-    }
-    uint64_t *out = limbs + (int64_t)b * limbs_per;
-    for (int i = 0; i < limbs_per; ++i) out[i] = (sb == TN_OK && i < (int)v.size()) ? v[i] : 0;
-    if (status) status[b] = sb;
-    if (sb != TN_OK && first == TN_OK) first = sb;
-  }
-  return first;
+  return finish_counts(ctx, B, n_primes, raw.data(), res.data(), limbs, limbs_per, E, status);
 }
 
 tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limbs,
@@ -1075,31 +1133,105 @@ tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limb
   tn_status first = TN_OK;
   for (int k = 0; k < B; ++k)
     if (!ctxs[k] || !ctxs[k]->ordered) first = TN_ESTATE;
-  for (auto &ids : groups) {
-    tn_ctx *owner = ctxs[ids[0]];
-    const Net &n = owner->net;
+  // Every group is queued before any is waited for: group g runs on stream
+  // g mod kBatchStreams of a pool, largest groups first, so the small groups'
+  // launch-bound steps overlap the large groups' bandwidth-bound ones; the
+  // roots and residues land in pinned host staging, read after one wait.
+  std::sort(groups.begin(), groups.end(), [&](const std::vector<int> &a, const std::vector<int> &b) {
+    const double wa = a.size() * std::exp2(ctxs[a[0]]->plan.log2_peak);
+    const double wb = b.size() * std::exp2(ctxs[b[0]]->plan.log2_peak);
+    return wa > wb;
+  });
+  const int P = limbs ? 4 : 0;   // 3 primes + witness
+  size_t stage_bytes = 0;
+  for (auto &ids : groups) stage_bytes += ids.size() * (4 + 8 * (size_t)P) + 64;
+  char *stage = nullptr;
+  std::vector<cudaStream_t> pool;
+  tn_status ps_status = TN_OK;
+  if (!groups.empty()) {
+    tn_ctx *c0 = ctxs[groups[0][0]];
+    ps_status = ensure_device(c0);
+    if (ps_status == TN_OK) ps_status = batch_streams(c0, &pool);
+    if (ps_status == TN_OK) ps_status = pinned_stage(c0, stage_bytes, &stage);
+  }
+  struct Run {
+    tn_ctx *owner;
+    cudaStream_t orig;
+    Program *p = nullptr;
+    char *raw = nullptr;
+    uint64_t *res = nullptr;
+    tn_status s = TN_OK;
+  };
+  std::vector<Run> runs(groups.size());
+  size_t off = 0;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const std::vector<int> &ids = groups[gi];
+    Run &r = runs[gi];
+    r.owner = ctxs[ids[0]];
+    r.orig = r.owner->stream;
+    if (ps_status != TN_OK) {
+      r.s = ps_status;
+      continue;
+    }
+    const Net &n = r.owner->net;
     const int G = (int)ids.size();
+    r.res = reinterpret_cast<uint64_t *>(stage + off);
+    off += (size_t)G * 8 * P;
+    r.raw = stage + off;
+    off += ((size_t)G * 4 + 63) / 64 * 64;
     std::vector<float> J((size_t)G * n.m), h(n.h.empty() ? 0 : (size_t)G * n.n);
     for (int g = 0; g < G; ++g) {
       const Net &ng = ctxs[ids[g]]->net;
       std::copy(ng.J.begin(), ng.J.end(), J.begin() + (size_t)g * n.m);
       if (!h.empty()) std::copy(ng.h.begin(), ng.h.end(), h.begin() + (size_t)g * n.n);
     }
+    // the pool stream starts after the work already queued on the context's
+    // stream; with profiling on, the groups share one stream so that the
+    // per-launch event times do not include other groups' concurrent kernels
+    bool prof = false;
+    for (auto &g2 : groups) prof = prof || ctxs[g2[0]]->profiling;
+    cudaStream_t st = pool[prof ? 0 : gi % pool.size()];
+    if (cudaStreamSynchronize(r.orig) != cudaSuccess) {
+      r.s = fail(r.owner, TN_ECUDA, "stream of a batch context failed");
+      continue;
+    }
+    r.owner->stream = st;
+    RunArgs ra;
+    r.s = batch_setup(r.owner, G, J.data(), h.empty() ? nullptr : h.data(), 0,
+                      limbs ? PM_COUNT : PM_ENERGY, P, &r.p, &ra);
+    if (r.s == TN_OK) r.s = run_program(r.owner, *r.p, 0, -1, ra);
+    if (r.s == TN_OK) r.s = stage_results(r.owner, *r.p, G, P, r.raw, r.res);
+  }
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    const std::vector<int> &ids = groups[gi];
+    Run &r = runs[gi];
+    const int G = (int)ids.size();
+    if (r.owner->stream != r.orig) {
+      tn_ctx *ctx = r.owner;
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      ctx->stream = r.orig;
+      if (e != cudaSuccess && r.s == TN_OK)
+        r.s = fail(ctx, TN_ECUDA, std::string("batch group: ") + cudaGetErrorString(e));
+    }
     std::vector<double> Eg(G);
     std::vector<int32_t> sg(G, TN_OK);
-    tn_status s;
-    if (limbs) {
+    tn_status s = r.s;
+    if (s == TN_OK && limbs) {
       std::vector<uint64_t> lg((size_t)G * limbs_per);
-      s = tn_count_batch(owner, G, J.data(), h.empty() ? nullptr : h.data(), 0, 3, lg.data(),
-                         limbs_per, Eg.data(), sg.data());
+      s = finish_counts(r.owner, G, 3, r.raw, r.res, lg.data(), limbs_per, Eg.data(), sg.data());
       for (int g = 0; g < G; ++g)
         std::copy(lg.begin() + (size_t)g * limbs_per, lg.begin() + (size_t)(g + 1) * limbs_per,
                   limbs + (int64_t)ids[g] * limbs_per);
+    } else if (s == TN_OK) {
+      for (int g = 0; g < G; ++g) Eg[g] = root_energy(r.owner, r.raw + 4 * g);
     } else {
-      s = tn_energy_batch(owner, G, J.data(), h.empty() ? nullptr : h.data(), 0, Eg.data());
-      if (s != TN_OK) std::fill(sg.begin(), sg.end(), s);
+      std::fill(sg.begin(), sg.end(), s);
+      if (limbs)
+        for (int g = 0; g < G; ++g)
+          std::fill(limbs + (int64_t)ids[g] * limbs_per, limbs + (int64_t)(ids[g] + 1) * limbs_per,
+                    0ull);
     }
-    if (s != TN_OK && owner != nullptr)
+    if (s != TN_OK)
       for (int g = 0; g < G; ++g)
         if (sg[g] == TN_OK) sg[g] = s == TN_EOVERFLOW ? TN_OK : s;
     for (int g = 0; g < G; ++g) {

@@ -666,3 +666,37 @@ def test_chimera8_planted_energy():
         assert sg.energy() == -1472.0
     finally:
         sg.close()
+
+
+@pytest.mark.parametrize("seed", [1, 3])
+def test_cfg5a_rrg200_gauss_degeneracy(seed):
+    """3-regular N = 200, J ~ N(0, 1) float32, h = 0 (App. D): the degeneracy is the
+    global flip pair, exactly 2; two independent greedy orders give the same E_min
+    (within the float32 tolerance) and the same count, and the traced state
+    reaches E_min (the oracle's elimination width is out of its reach here)."""
+    inst = I.random_regular3(200, coupling="gauss", seed=seed)
+    res = []
+    for order_seed in (1, 2):
+        sg = P.SpinGlass(inst, order="greedy", seed=order_seed, restarts=1024)
+        try:
+            assert sg.log2_peak <= 28
+            c, _, E = sg.count(3)
+            st, E2 = gpu_state(sg)
+            assert E2 == E
+            check_energy(inst, O.energy(inst, st), E)
+            res.append((E, c))
+        finally:
+            sg.close()
+    assert res[0][1] == res[1][1] == 2
+    assert close(res[0][0], res[1][0])
+
+
+def test_cfg5a_rrg200_planted_count():
+    """Mattis-planted 3-regular N = 200: E_min = -sum|J| and exactly 2 ground states."""
+    inst, tau = I.planted(I.random_regular3(200, coupling="gauss", seed=3), seed=5)
+    sg = P.SpinGlass(inst, order="greedy", seed=1, restarts=1024)
+    try:
+        c, _, E = sg.count(3)
+        assert close(E, -float(np.abs(inst["J"].astype(np.float64)).sum())) and c == 2
+    finally:
+        sg.close()

@@ -26,6 +26,11 @@ using namespace tn;
 
 // 61-bit primes p_i = 2^61 - c_i; the last one used by a call is the witness.
 static const uint64_t kPrimeC[TN_MAX_PRIMES] = {1, 31, 45, 229, 259, 283, 339, 391, 403};
+// 31-bit primes p_j = 2^31 - c_j of the one-prime-per-pass counts (4-byte
+// planes): enough passes to cover 8 61-bit primes, plus a witness.
+static const int kPasses31Max = 17;
+static const uint64_t kPrime31C[kPasses31Max] = {1,   19,  61,  69,  85,  99,  105, 151, 159,
+                                                 171, 225, 249, 295, 325, 379, 399, 411};
 
 struct tn_ctx {
   Net net;
@@ -69,6 +74,10 @@ struct tn_ctx {
   // number of violated clauses; 1 and 0 otherwise)
   double e_scale = 1.0, e_offset = 0.0;
   bool host_couplings = true;   // net.J / net.h hold the couplings in use
+  // counts one 31-bit prime per pass (4-byte planes): its program and the
+  // prime of the pass in flight
+  std::unique_ptr<Program> prog_pass;
+  uint64_t pass_c = 1;
 };
 
 static std::string g_build_err;
@@ -297,6 +306,8 @@ tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_
   const Batch &bt = ra.bt;
   PrimeSet ps;
   for (int i = 0; i < TN_MAX_PRIMES; ++i) ps.c[i] = kPrimeC[i];
+  ps.r32 = p.rbytes == 4;
+  if (ps.r32) ps.c[0] = ctx->pass_c;   // one 31-bit prime per pass
   auto X = [&](const Loc &l) -> void * { return l.buf < 0 ? nullptr : ar + abs_off(p, l); };
   auto Nn = [&](const Loc &l) -> uint64_t * {
     return l.buf < 0 ? nullptr : (uint64_t *)(ar + p.bufs[l.buf].off + l.noff);
@@ -316,7 +327,8 @@ tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_
     }
     switch (op.kind) {
       case OP_LEAVES:
-        e = launch_leaves(p.dt, p.q, p.d_leaves, (int)p.leaves.size(), ra.J, ra.h, ar, p.P, bt, st);
+        e = launch_leaves(p.dt, p.q, p.d_leaves, (int)p.leaves.size(), ra.J, ra.h, ar, p.P,
+                          p.rbytes, bt, st);
         break;
       case OP_PERM:
         e = launch_permute(p.perms[op.idx], X(op.in0), X(op.out), Nn(op.in0), Nn(op.out), bt, st);
@@ -383,7 +395,8 @@ void account_range(tn_ctx *ctx, const Program &p, int b, int e, int B) {
 tn_status run_program(tn_ctx *ctx, Program &p, int op_begin, int op_end, const RunArgs &ra) {
   if (op_end < 0) op_end = (int)p.ops.size();
   static const bool no_graph = std::getenv("TN_NO_GRAPH") != nullptr;
-  if (ctx->profiling || no_graph) return run_ops(ctx, p, op_begin, op_end, ctx->stream, true, ra);
+  if (ctx->profiling || no_graph || p.rbytes == 4)
+    return run_ops(ctx, p, op_begin, op_end, ctx->stream, true, ra);
   Program::Graph *g = nullptr;
   for (auto &x : p.graphs)
     if (x.begin == op_begin && x.end == op_end && x.B == ra.bt.B && x.J == ra.J) g = &x;
@@ -613,6 +626,12 @@ tn_status count_from_residues(tn_ctx *ctx, const std::vector<uint64_t> &res, int
   return TN_OK;
 }
 
+tn_status finish_count(tn_ctx *ctx, const std::vector<uint64_t> &res,
+                       const std::vector<uint64_t> &pr, uint64_t *limbs, int32_t *n_limbs,
+                       double *ln_count);
+tn_status count_in_passes(tn_ctx *ctx, int n_primes, uint64_t *limbs, int32_t *n_limbs,
+                          double *ln_count, double *E);
+
 }  // namespace
 
 extern "C" {
@@ -764,6 +783,8 @@ tn_status tn_order(tn_ctx *ctx, int32_t method, const int32_t *seq, int32_t seq_
     if (pg) free_program(pg.get());
     pg.reset();
   }
+  if (ctx->prog_pass) free_program(ctx->prog_pass.get());
+  ctx->prog_pass.reset();
   ctx->plan = p;
   ctx->ordered = true;
   ctx->have_state = false;
@@ -905,7 +926,16 @@ tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_li
   if (s != TN_OK) return s;
   const int P = n_primes + 1;  // + witness
   Program *p;
-  if ((s = get_program(ctx, PM_COUNT, P, &p)) != TN_OK) return s;
+  const bool force_passes = std::getenv("TN_COUNT_PASSES") != nullptr;
+  if (force_passes) return count_in_passes(ctx, n_primes, limbs, n_limbs, ln_count, E);
+  s = get_program(ctx, PM_COUNT, P, &p);
+  if (s == TN_ENOMEM) {
+    // the residue planes of P 61-bit primes do not fit: one 31-bit prime per pass
+    if (ctx->prog[PM_COUNT]) free_program(ctx->prog[PM_COUNT].get());
+    ctx->prog[PM_COUNT].reset();
+    return count_in_passes(ctx, n_primes, limbs, n_limbs, ln_count, E);
+  }
+  if (s != TN_OK) return s;
   if ((s = run_program(ctx, *p)) != TN_OK) return s;
   char raw[4];
   std::vector<uint64_t> res(P);
@@ -916,11 +946,23 @@ tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_li
                        cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (E) *E = root_energy(ctx, raw);
-  std::vector<uint64_t> r(res.begin(), res.begin() + n_primes), pr;
-  for (int i = 0; i < n_primes; ++i) pr.push_back((1ull << 61) - kPrimeC[i]);
-  std::vector<uint64_t> v = crt(r, pr);
-  uint64_t pw = (1ull << 61) - kPrimeC[n_primes];
-  if (limbs_mod(v, pw) != res[n_primes])
+  std::vector<uint64_t> pr;
+  for (int i = 0; i <= n_primes; ++i) pr.push_back((1ull << 61) - kPrimeC[i]);
+  return finish_count(ctx, res, pr, limbs, n_limbs, ln_count);
+}
+
+}  // extern "C"
+
+namespace {
+
+// count from residues res[i] modulo primes pr[i], the last pair the witness
+tn_status finish_count(tn_ctx *ctx, const std::vector<uint64_t> &res,
+                       const std::vector<uint64_t> &pr, uint64_t *limbs, int32_t *n_limbs,
+                       double *ln_count) {
+  const size_t n = pr.size() - 1;
+  std::vector<uint64_t> r(res.begin(), res.begin() + n), p(pr.begin(), pr.begin() + n);
+  std::vector<uint64_t> v = crt(r, p);
+  if (limbs_mod(v, pr[n]) != res[n])
     return fail(ctx, TN_EOVERFLOW, "count exceeds the product of the primes (witness mismatch)");
   if (n_limbs) {
     if (limbs && *n_limbs < (int32_t)v.size())
@@ -935,6 +977,52 @@ tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_li
   }
   return TN_OK;
 }
+
+// The degeneracy with one 31-bit prime per pass: the program keeps a single
+// 4-byte residue plane (values + 4 bytes per element instead of 4 + 8 (n + 1)),
+// so instances whose planes for n 61-bit primes do not fit in device memory
+// still count exactly.  Enough passes to reach the range of n 61-bit primes,
+// then one witness pass; Garner's CRT over the pass residues on the host.
+tn_status count_in_passes(tn_ctx *ctx, int n_primes, uint64_t *limbs, int32_t *n_limbs,
+                          double *ln_count, double *E) {
+  const int n31 = (61 * n_primes + 30) / 31;
+  if (n31 + 1 > kPasses31Max) return fail(ctx, TN_EINVAL, "too many primes for counting passes");
+  if (!ctx->ordered) return fail(ctx, TN_ESTATE, "tn_order has not been called");
+  if (!ctx->prog_pass) {
+    std::unique_ptr<Program> pg(new Program());
+    std::string err;
+    if (!build_program(ctx->net, ctx->plan, PM_COUNT, ctx->dt, 1, 0, pg.get(), &err, 4))
+      return fail(ctx, TN_EINVAL, err);
+    if (!pg->leaves.empty()) {
+      CK(cudaMalloc(&pg->d_leaves, pg->leaves.size() * sizeof(LeafDesc)));
+      CK(cudaMemcpy(pg->d_leaves, pg->leaves.data(), pg->leaves.size() * sizeof(LeafDesc),
+                    cudaMemcpyHostToDevice));
+    }
+    ctx->prog_pass = std::move(pg);
+  }
+  Program &p = *ctx->prog_pass;
+  tn_status s = ensure_arena(ctx, p.arena_bytes);
+  if (s != TN_OK) return s;
+  std::vector<uint64_t> res(n31 + 1), pr(n31 + 1);
+  char raw[4];
+  for (int j = 0; j <= n31; ++j) {
+    ctx->pass_c = kPrime31C[j];
+    pr[j] = (1ull << 31) - kPrime31C[j];
+    if ((s = run_program(ctx, p)) != TN_OK) return s;
+    const char *base = ctx->d_arena + p.bufs[p.root.buf].off;
+    uint32_t r = 0;
+    if (j == 0) CK(cudaMemcpyAsync(raw, base + p.root.xoff, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&r, base + p.root.noff, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    res[j] = r;
+  }
+  if (E) *E = root_energy(ctx, raw);
+  return finish_count(ctx, res, pr, limbs, n_limbs, ln_count);
+}
+
+}  // namespace
+
+extern "C" {
 
 
 tn_status tn_energy_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
@@ -1359,6 +1447,7 @@ tn_status tn_energy_noalloc(tn_ctx *ctx, const float *J_dev, const float *h_dev,
   cudaStream_t st = (cudaStream_t)cuda_stream;
   PrimeSet ps;
   for (int i = 0; i < TN_MAX_PRIMES; ++i) ps.c[i] = kPrimeC[i];
+  ps.r32 = 0;
   auto X = [&](const Loc &l) -> void * { return l.buf < 0 ? nullptr : base + abs_off(p, l); };
   const Batch one;
   // this call only queues work: no GEMM tile timing (it would wait on the stream)
@@ -1503,6 +1592,7 @@ const char *tn_last_error(const tn_ctx *ctx) {
 void tn_destroy(tn_ctx *ctx) {
   if (!ctx) return;
   for (auto &p : ctx->prog) if (p) free_program(p.get());
+  if (ctx->prog_pass) free_program(ctx->prog_pass.get());
   if (ctx->dev_ready) {
     cudaFree(ctx->d_J);
     cudaFree(ctx->d_h);

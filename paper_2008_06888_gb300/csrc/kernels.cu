@@ -61,6 +61,35 @@ __device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b, uint64_t c)
   return s >= p ? s - p : s;
 }
 
+// The same for p = 2^31 - c (c < 2^10) on 4-byte residues: the 62-bit product
+// is folded twice with 2^31 = c (mod p).
+static constexpr uint64_t M31 = (1ull << 31) - 1;
+__device__ __forceinline__ uint32_t mulmod31(uint32_t a, uint32_t b, uint64_t c) {
+  const uint64_t x = (uint64_t)a * b;                  // < 2^62
+  const uint64_t y = (x >> 31) * c + (x & M31);        // < 2^41
+  const uint64_t z = (y >> 31) * c + (y & M31);        // < 2^31 + 2^20 < 2p
+  const uint64_t p = M31 + 1 - c;
+  return (uint32_t)(z >= p ? z - p : z);
+}
+__device__ __forceinline__ uint32_t addmod31(uint32_t a, uint32_t b, uint64_t c) {
+  const uint32_t p = (uint32_t)(M31 + 1 - c);
+  const uint32_t s = a + b;                            // < 2p < 2^32
+  return s >= p ? s - p : s;
+}
+// residue arithmetic by plane width
+__device__ __forceinline__ uint64_t mulmodR(uint64_t a, uint64_t b, uint64_t c) {
+  return mulmod61(a, b, c);
+}
+__device__ __forceinline__ uint32_t mulmodR(uint32_t a, uint32_t b, uint64_t c) {
+  return mulmod31(a, b, c);
+}
+__device__ __forceinline__ uint64_t addmodR(uint64_t a, uint64_t b, uint64_t c) {
+  return addmod61(a, b, c);
+}
+__device__ __forceinline__ uint32_t addmodR(uint32_t a, uint32_t b, uint64_t c) {
+  return addmod31(a, b, c);
+}
+
 // Streaming multiprocessors of the current device (GB300: 152), queried once
 // per device; grid sizes are multiples of it.
 int num_sms() {
@@ -123,7 +152,7 @@ template <> __device__ __forceinline__ int32_t to_val<int32_t>(float x) { return
 
 // Bond tensor [[J, -J], [-J, J]] (Sec. II) plus the absorbed vertex tensors
 // diag(h, -h); Potts bond J delta(a, b).  One thread per leaf element.
-template <typename T>
+template <typename T, typename R>
 __global__ void k_leaves(const LeafDesc *__restrict__ d, int nleaves, int q,
                          const float *__restrict__ J, const float *__restrict__ h, char *arena,
                          int P, int64_t jstride, int64_t hstride, int64_t ib) {
@@ -160,35 +189,39 @@ __global__ void k_leaves(const LeafDesc *__restrict__ d, int nleaves, int q,
   int idx = (L.kind == 0) ? a * q + b : a;
   reinterpret_cast<T *>(arena + L.off_x)[idx] = v;
   if (P > 0) {
-    uint64_t *n = reinterpret_cast<uint64_t *>(arena + L.off_n);
-    for (int i = 0; i < P; ++i) n[i * L.plane + idx] = 1ull;
+    R *n = reinterpret_cast<R *>(arena + L.off_n);
+    for (int i = 0; i < P; ++i) n[i * L.plane + idx] = R(1);
   }
 }
 
 cudaError_t launch_leaves(Dtype dt, int q, const LeafDesc *d_leaves, int nleaves, const float *J,
-                          const float *h, char *arena, int P, const Batch &bt, cudaStream_t st) {
+                          const float *h, char *arena, int P, int rbytes, const Batch &bt,
+                          cudaStream_t st) {
   if (nleaves == 0) return cudaSuccess;
   int64_t total = (int64_t)nleaves * q * q;
   int threads = 256;
   dim3 grid((unsigned)((total + threads - 1) / threads), bt.B);
-  if (dt == DT_F32)
-    k_leaves<float><<<grid, threads, 0, st>>>(d_leaves, nleaves, q, J, h, arena, P, bt.jstride,
-                                               bt.hstride, bt.ib);
-  else
-    k_leaves<int32_t><<<grid, threads, 0, st>>>(d_leaves, nleaves, q, J, h, arena, P, bt.jstride,
-                                                 bt.hstride, bt.ib);
+#define TN_LEAVES(T_, R_)                                                                       \
+  k_leaves<T_, R_><<<grid, threads, 0, st>>>(d_leaves, nleaves, q, J, h, arena, P, bt.jstride, \
+                                            bt.hstride, bt.ib)
+  if (dt == DT_F32) {
+    if (rbytes == 4) TN_LEAVES(float, uint32_t); else TN_LEAVES(float, uint64_t);
+  } else {
+    if (rbytes == 4) TN_LEAVES(int32_t, uint32_t); else TN_LEAVES(int32_t, uint64_t);
+  }
+#undef TN_LEAVES
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- gate contraction
 
 // C[o, n] = max_k A[o, k] + B[o, k, n], one outer index per thread.
-template <typename T, bool COUNT>
+template <typename T, bool COUNT, typename R = uint64_t>
 __global__ void __launch_bounds__(256) k_gate(const GateParams p, const T *__restrict__ A,
                                               const T *__restrict__ B, T *__restrict__ C,
-                                              const uint64_t *__restrict__ nA,
-                                              const uint64_t *__restrict__ nB,
-                                              uint64_t *__restrict__ nC, const PrimeSet ps,
+                                              const R *__restrict__ nA,
+                                              const R *__restrict__ nB,
+                                              R *__restrict__ nC, const PrimeSet ps,
                                               int64_t ib) {
   A = inst_ptr(A, ib);
   C = inst_ptr(C, ib);
@@ -216,7 +249,7 @@ __global__ void __launch_bounds__(256) k_gate(const GateParams p, const T *__res
     }
     for (int n = 0; n < p.Ns; ++n) {
       T best = Lim<T>::neg();
-      uint64_t cnt[TN_MAX_PRIMES];
+      R cnt[TN_MAX_PRIMES];
 #pragma unroll
       for (int i = 0; i < TN_MAX_PRIMES; ++i) cnt[i] = 0;
       for (int k = 0; k < p.Ks; ++k) {
@@ -229,11 +262,11 @@ __global__ void __launch_bounds__(256) k_gate(const GateParams p, const T *__res
 #pragma unroll
             for (int i = 0; i < TN_MAX_PRIMES; ++i) {
               if (i < p.P) {
-                uint64_t na = nA[i * p.planeA + oa + p.kA[k]];
-                uint64_t t = (p.hasB && !p.unitB)
-                                 ? mulmod61(na, nB[i * p.planeB + ob + p.kB[k] + p.nB[n]], ps.c[i])
-                                 : na;
-                cnt[i] = gt ? t : addmod61(cnt[i], t, ps.c[i]);
+                R na = nA[i * p.planeA + oa + p.kA[k]];
+                R t = (p.hasB && !p.unitB)
+                          ? mulmodR(na, nB[i * p.planeB + ob + p.kB[k] + p.nB[n]], ps.c[i])
+                          : na;
+                cnt[i] = gt ? t : addmodR(cnt[i], t, ps.c[i]);
               }
             }
           }
@@ -609,7 +642,7 @@ template <typename T>
 static bool launch_gate2c(const GateParams &p, const T *A, const T *B, T *C, const uint64_t *nA,
                           const uint64_t *nB, uint64_t *nC, const PrimeSet &ps, const Batch &bt,
                           cudaStream_t st) {
-  if (p.P != 4 || std::getenv("TN_NO_GATE2")) return false;
+  if (p.P != 4 || ps.r32 || std::getenv("TN_NO_GATE2")) return false;
   GateParams q = p;
   q.P = 0;   // gate2_form checks the value layout; the planes share it
   Gate2 g;
@@ -684,6 +717,17 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
                      : launch_gate2c<int32_t>(p, (const int32_t *)xA, (const int32_t *)xB,
                                               (int32_t *)xC, nA, nB, nC, ps, bt, st);
     if (streamed) return cudaGetLastError();
+  }
+  if (cnt && ps.r32) {
+    const uint32_t *a = (const uint32_t *)nA, *b = (const uint32_t *)nB;
+    uint32_t *c = (uint32_t *)nC;
+    if (dt == DT_F32)
+      k_gate<float, true, uint32_t><<<blocks, threads, 0, st>>>(
+          p, (const float *)xA, (const float *)xB, (float *)xC, a, b, c, ps, bt.ib);
+    else
+      k_gate<int32_t, true, uint32_t><<<blocks, threads, 0, st>>>(
+          p, (const int32_t *)xA, (const int32_t *)xB, (int32_t *)xC, a, b, c, ps, bt.ib);
+    return cudaGetLastError();
   }
   if (dt == DT_F32) {
     if (cnt)
@@ -1088,20 +1132,38 @@ __global__ void __launch_bounds__(256) k_mpgemm_splitk(const GemmParams p, const
 }
 
 // counting planes: n_i[o] = sum over k with A + B == C of nA_i nB_i (mod p_i)
-template <typename T>
-__global__ void k_splitk_count_zero(const GemmParams p, uint64_t *nC, int64_t ib) {
+// *dst = *dst + v (mod p) by compare-and-swap
+__device__ __forceinline__ void cas_addmod(uint64_t *dst, uint64_t v, uint64_t c) {
+  unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+  unsigned long long old = *d, assumed;
+  do {
+    assumed = old;
+    old = atomicCAS(d, assumed, (unsigned long long)addmod61(assumed, v, c));
+  } while (old != assumed);
+}
+__device__ __forceinline__ void cas_addmod(uint32_t *dst, uint32_t v, uint64_t c) {
+  unsigned int *d = reinterpret_cast<unsigned int *>(dst);
+  unsigned int old = *d, assumed;
+  do {
+    assumed = old;
+    old = atomicCAS(d, assumed, addmod31(assumed, v, c));
+  } while (old != assumed);
+}
+
+template <typename R>
+__global__ void k_splitk_count_zero(const GemmParams p, R *nC, int64_t ib) {
   nC = inst_ptr(nC, ib);
   const int o = threadIdx.x;
   if (o >= p.batch * p.M * p.N) return;
   int64_t oa, ob, oc;
   splitk_out(p, o, &oa, &ob, &oc);
-  for (int i = 0; i < p.P; ++i) nC[i * p.planeC + oc] = 0ull;
+  for (int i = 0; i < p.P; ++i) nC[i * p.planeC + oc] = R(0);
 }
 
-template <typename T>
+template <typename T, typename R>
 __global__ void __launch_bounds__(256) k_gemm_count_splitk(
     const GemmParams p, const T *__restrict__ A, const T *__restrict__ B, const T *__restrict__ C,
-    const uint64_t *__restrict__ nA, const uint64_t *__restrict__ nB, uint64_t *nC,
+    const R *__restrict__ nA, const R *__restrict__ nB, R *nC,
     const PrimeSet ps, int64_t ib) {
   A = inst_ptr(A, ib);
   B = inst_ptr(B, ib);
@@ -1110,12 +1172,12 @@ __global__ void __launch_bounds__(256) k_gemm_count_splitk(
   nB = inst_ptr(nB, ib);
   nC = inst_ptr(nC, ib);
   const int nout = (int)(p.batch * p.M * p.N);
-  __shared__ uint64_t red[TN_MAX_PRIMES][8];
+  __shared__ R red[TN_MAX_PRIMES][8];
   for (int o = 0; o < nout; ++o) {
     int64_t oa, ob, oc;
     splitk_out(p, o, &oa, &ob, &oc);
     const T x = C[oc];
-    uint64_t cnt[TN_MAX_PRIMES];
+    R cnt[TN_MAX_PRIMES];
 #pragma unroll
     for (int i = 0; i < TN_MAX_PRIMES; ++i) cnt[i] = 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p.K;
@@ -1124,32 +1186,25 @@ __global__ void __launch_bounds__(256) k_gemm_count_splitk(
 #pragma unroll
         for (int i = 0; i < TN_MAX_PRIMES; ++i)
           if (i < p.P)
-            cnt[i] = addmod61(cnt[i], mulmod61(nA[i * p.planeA + oa + k * p.sAk],
-                                               nB[i * p.planeB + ob + k * p.sBk], ps.c[i]),
-                              ps.c[i]);
+            cnt[i] = addmodR(cnt[i], mulmodR(nA[i * p.planeA + oa + k * p.sAk],
+                                             nB[i * p.planeB + ob + k * p.sBk], ps.c[i]),
+                             ps.c[i]);
       }
     }
 #pragma unroll
     for (int i = 0; i < TN_MAX_PRIMES; ++i) {
       if (i >= p.P) break;
-      uint64_t v = cnt[i];
+      R v = cnt[i];
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) v = addmod61(v, __shfl_xor_sync(0xffffffffu, v, d), ps.c[i]);
+      for (int d = 16; d > 0; d >>= 1) v = addmodR(v, (R)__shfl_xor_sync(0xffffffffu, v, d), ps.c[i]);
       if ((threadIdx.x & 31) == 0) red[i][threadIdx.x >> 5] = v;
     }
     __syncthreads();
     if (threadIdx.x < p.P) {
       const int i = threadIdx.x;
-      uint64_t v = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = addmod61(v, red[i][w], ps.c[i]);
-      if (v) {
-        unsigned long long *dst = reinterpret_cast<unsigned long long *>(nC + i * p.planeC + oc);
-        unsigned long long old = *dst, assumed;
-        do {
-          assumed = old;
-          old = atomicCAS(dst, assumed, (unsigned long long)addmod61(assumed, v, ps.c[i]));
-        } while (old != assumed);
-      }
+      R v = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = addmodR(v, red[i][w], ps.c[i]);
+      if (v) cas_addmod(nC + i * p.planeC + oc, v, ps.c[i]);
     }
     __syncthreads();
   }
@@ -1170,13 +1225,13 @@ static cudaError_t launch_splitk(const GemmParams &p, const T *A, const T *B, T 
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename R>
 static cudaError_t launch_count_splitk(const GemmParams &p, const T *A, const T *B, const T *C,
-                                       const uint64_t *nA, const uint64_t *nB, uint64_t *nC,
-                                       const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
-  k_splitk_count_zero<T><<<dim3(1, bt.B), 32, 0, st>>>(p, nC, bt.ib);
-  k_gemm_count_splitk<T><<<dim3(splitk_blocks(p, bt), bt.B), 256, 0, st>>>(p, A, B, C, nA, nB, nC,
-                                                                           ps, bt.ib);
+                                       const R *nA, const R *nB, R *nC, const PrimeSet &ps,
+                                       const Batch &bt, cudaStream_t st) {
+  k_splitk_count_zero<R><<<dim3(1, bt.B), 32, 0, st>>>(p, nC, bt.ib);
+  k_gemm_count_splitk<T, R><<<dim3(splitk_blocks(p, bt), bt.B), 256, 0, st>>>(
+      p, A, B, C, nA, nB, nC, ps, bt.ib);
   return cudaGetLastError();
 }
 
@@ -1245,10 +1300,10 @@ cudaError_t launch_mpgemm(Dtype dt, const GemmParams &p, const void *A, const vo
 
 // Counting planes of a GEMM step: n_i[b,m,n] = sum over the k with
 // A.x + B.x == C.x of A.n_i B.n_i (mod p_i).  One output per thread.
-template <typename T>
+template <typename T, typename R>
 __global__ void k_gemm_count(const GemmParams p, const T *__restrict__ A, const T *__restrict__ B,
-                             const T *__restrict__ C, const uint64_t *__restrict__ nA,
-                             const uint64_t *__restrict__ nB, uint64_t *__restrict__ nC,
+                             const T *__restrict__ C, const R *__restrict__ nA,
+                             const R *__restrict__ nB, R *__restrict__ nC,
                              const PrimeSet ps, int64_t ib) {
   A = inst_ptr(A, ib);
   B = inst_ptr(B, ib);
@@ -1263,7 +1318,7 @@ __global__ void k_gemm_count(const GemmParams p, const T *__restrict__ A, const 
     const int64_t oa = b * p.sAb + m * p.sAm, ob = b * p.sBb + n * p.sBn;
     const int64_t oc = b * p.sCb + m * p.sCm + n * p.sCn;
     const T x = C[oc];
-    uint64_t cnt[TN_MAX_PRIMES];
+    R cnt[TN_MAX_PRIMES];
 #pragma unroll
     for (int i = 0; i < TN_MAX_PRIMES; ++i) cnt[i] = 0;
     for (int64_t k = 0; k < p.K; ++k) {
@@ -1271,10 +1326,10 @@ __global__ void k_gemm_count(const GemmParams p, const T *__restrict__ A, const 
 #pragma unroll
         for (int i = 0; i < TN_MAX_PRIMES; ++i)
           if (i < p.P)
-            cnt[i] = addmod61(cnt[i],
-                              mulmod61(nA[i * p.planeA + oa + k * p.sAk],
-                                       nB[i * p.planeB + ob + k * p.sBk], ps.c[i]),
-                              ps.c[i]);
+            cnt[i] = addmodR(cnt[i],
+                             mulmodR(nA[i * p.planeA + oa + k * p.sAk],
+                                     nB[i * p.planeB + ob + k * p.sBk], ps.c[i]),
+                             ps.c[i]);
       }
     }
 #pragma unroll
@@ -1288,20 +1343,35 @@ cudaError_t launch_gemm_count(Dtype dt, const GemmParams &p, const void *xA, con
                               const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
   int64_t total = p.batch * p.M * p.N;
   if (total == 0) return cudaSuccess;
+  const uint32_t *a4 = (const uint32_t *)nA, *b4 = (const uint32_t *)nB;
+  uint32_t *c4 = (uint32_t *)nC;
   if (splitk_ok(p)) {
     if (dt == DT_F32)
-      return launch_count_splitk(p, (const float *)xA, (const float *)xB, (const float *)xC, nA,
-                                 nB, nC, ps, bt, st);
-    return launch_count_splitk(p, (const int32_t *)xA, (const int32_t *)xB, (const int32_t *)xC,
-                               nA, nB, nC, ps, bt, st);
+      return ps.r32 ? launch_count_splitk(p, (const float *)xA, (const float *)xB,
+                                          (const float *)xC, a4, b4, c4, ps, bt, st)
+                    : launch_count_splitk(p, (const float *)xA, (const float *)xB,
+                                          (const float *)xC, nA, nB, nC, ps, bt, st);
+    return ps.r32 ? launch_count_splitk(p, (const int32_t *)xA, (const int32_t *)xB,
+                                        (const int32_t *)xC, a4, b4, c4, ps, bt, st)
+                  : launch_count_splitk(p, (const int32_t *)xA, (const int32_t *)xB,
+                                        (const int32_t *)xC, nA, nB, nC, ps, bt, st);
   }
   dim3 blocks(grid_for(total, 256), bt.B);
-  if (dt == DT_F32)
-    k_gemm_count<float><<<blocks, 256, 0, st>>>(p, (const float *)xA, (const float *)xB,
-                                                (const float *)xC, nA, nB, nC, ps, bt.ib);
-  else
-    k_gemm_count<int32_t><<<blocks, 256, 0, st>>>(p, (const int32_t *)xA, (const int32_t *)xB,
-                                                  (const int32_t *)xC, nA, nB, nC, ps, bt.ib);
+  if (dt == DT_F32) {
+    if (ps.r32)
+      k_gemm_count<float, uint32_t><<<blocks, 256, 0, st>>>(
+          p, (const float *)xA, (const float *)xB, (const float *)xC, a4, b4, c4, ps, bt.ib);
+    else
+      k_gemm_count<float, uint64_t><<<blocks, 256, 0, st>>>(
+          p, (const float *)xA, (const float *)xB, (const float *)xC, nA, nB, nC, ps, bt.ib);
+  } else {
+    if (ps.r32)
+      k_gemm_count<int32_t, uint32_t><<<blocks, 256, 0, st>>>(
+          p, (const int32_t *)xA, (const int32_t *)xB, (const int32_t *)xC, a4, b4, c4, ps, bt.ib);
+    else
+      k_gemm_count<int32_t, uint64_t><<<blocks, 256, 0, st>>>(
+          p, (const int32_t *)xA, (const int32_t *)xB, (const int32_t *)xC, nA, nB, nC, ps, bt.ib);
+  }
   return cudaGetLastError();
 }
 
@@ -1394,7 +1464,10 @@ cudaError_t launch_permute(const PermParams &p, const void *xin, void *xout, con
     const unsigned gx = (unsigned)std::min<int64_t>(pb.tiles, per_inst);
     k_permute2<uint32_t><<<dim3(gx, 1, bt.B), 256, 0, st>>>(pb, (const uint32_t *)xin,
                                                              (uint32_t *)xout, 0, 0, bt.ib);
-    if (p.P > 0)
+    if (p.P > 0 && p.rbytes == 4)
+      k_permute2<uint32_t><<<dim3(gx, p.P, bt.B), 256, 0, st>>>(
+          pb, (const uint32_t *)nin, (uint32_t *)nout, p.planeIn, p.planeOut, bt.ib);
+    else if (p.P > 0)
       k_permute2<uint64_t><<<dim3(gx, p.P, bt.B), 256, 0, st>>>(pb, nin, nout, p.planeIn,
                                                                 p.planeOut, bt.ib);
     return cudaGetLastError();
@@ -1402,7 +1475,10 @@ cudaError_t launch_permute(const PermParams &p, const void *xin, void *xout, con
   int blocks = grid_for(p.total, 256);
   k_permute<uint32_t><<<dim3(blocks, 1, bt.B), 256, 0, st>>>(p, (const uint32_t *)xin,
                                                              (uint32_t *)xout, 0, 0, bt.ib);
-  if (p.P > 0)
+  if (p.P > 0 && p.rbytes == 4)
+    k_permute<uint32_t><<<dim3(blocks, p.P, bt.B), 256, 0, st>>>(
+        p, (const uint32_t *)nin, (uint32_t *)nout, p.planeIn, p.planeOut, bt.ib);
+  else if (p.P > 0)
     k_permute<uint64_t><<<dim3(blocks, p.P, bt.B), 256, 0, st>>>(p, nin, nout, p.planeIn,
                                                                  p.planeOut, bt.ib);
   return cudaGetLastError();
@@ -1513,9 +1589,9 @@ __device__ __forceinline__ void apply_gate(const ChainGate &g, const T *src, T *
 }
 
 // Counting version: values and P residue planes (plane stride `tile`).
-template <typename T, int Q>
-__device__ __forceinline__ void apply_gate_count(const ChainGate &g, T *s, uint64_t *sn,
-                                                 const T *sB, const uint64_t *sBn, int nBel,
+template <typename T, int Q, typename R>
+__device__ __forceinline__ void apply_gate_count(const ChainGate &g, T *s, R *sn,
+                                                 const T *sB, const R *sBn, int nBel,
                                                  int tile, int P, const PrimeSet &ps) {
   if (g.kind == 0) {
     const int n = tile / Q;
@@ -1534,18 +1610,18 @@ __device__ __forceinline__ void apply_gate_count(const ChainGate &g, T *s, uint6
         out[v] = best;
       }
       for (int pl = 0; pl < P; ++pl) {
-        uint64_t *np = sn + (int64_t)pl * tile;
-        const uint64_t *bp = sBn + (int64_t)pl * nBel;
-        uint64_t nin[Q], nout[Q];
+        R *np = sn + (int64_t)pl * tile;
+        const R *bp = sBn + (int64_t)pl * nBel;
+        R nin[Q], nout[Q];
 #pragma unroll
         for (int u = 0; u < Q; ++u) nin[u] = np[x + u * g.ls];
 #pragma unroll
         for (int v = 0; v < Q; ++v) {
-          uint64_t c = 0;
+          R c = 0;
 #pragma unroll
           for (int u = 0; u < Q; ++u) {
             const int64_t bi = bo + u * g.sBk + v * g.sBn;
-            if (in[u] + sB[bi] == out[v]) c = addmod61(c, mulmod61(nin[u], bp[bi], ps.c[pl]), ps.c[pl]);
+            if (in[u] + sB[bi] == out[v]) c = addmodR(c, mulmodR(nin[u], bp[bi], ps.c[pl]), ps.c[pl]);
           }
           nout[v] = c;
         }
@@ -1560,16 +1636,16 @@ __device__ __forceinline__ void apply_gate_count(const ChainGate &g, T *s, uint6
       const int64_t bo = gate_boff<Q>(g, i);
       s[i] = s[i] + sB[bo];
       for (int pl = 0; pl < P; ++pl)
-        sn[(int64_t)pl * tile + i] = mulmod61(sn[(int64_t)pl * tile + i], sBn[(int64_t)pl * nBel + bo],
-                                              ps.c[pl]);
+        sn[(int64_t)pl * tile + i] = mulmodR(sn[(int64_t)pl * tile + i], sBn[(int64_t)pl * nBel + bo],
+                                             ps.c[pl]);
     }
   }
 }
 
 // Copy every gate's B (values, and planes when P > 0) into shared memory.
-template <typename T>
+template <typename T, typename R>
 __device__ __forceinline__ void load_gate_operands(const ChainParams &p, const T *X,
-                                                   const uint64_t *Xn, T *sB, uint64_t *sBn,
+                                                   const R *Xn, T *sB, R *sBn,
                                                    int stride_el) {
   for (int gi = 0; gi < p.ngates; ++gi) {
     const ChainGate &g = p.g[gi];
@@ -1589,12 +1665,12 @@ __device__ __forceinline__ int64_t tile_elem_off(const ChainParams &p, int i) {
 
 constexpr int kGateBMax = 27;  // q^3 elements of one gate operand
 
-template <typename T, int Q, bool COUNT>
+template <typename T, int Q, bool COUNT, typename R = uint64_t>
 __global__ void __launch_bounds__(256) k_chain(const ChainParams p, const T *__restrict__ X,
-                                               const uint64_t *__restrict__ Xn,
+                                               const R *__restrict__ Xn,
                                                const T *__restrict__ Ax,
-                                               const uint64_t *__restrict__ An,
-                                               T *__restrict__ Cx, uint64_t *__restrict__ Cn,
+                                               const R *__restrict__ An,
+                                               T *__restrict__ Cx, R *__restrict__ Cn,
                                                const PrimeSet ps, int64_t ib) {
   X = inst_ptr(X, ib);
   Ax = inst_ptr(Ax, ib);
@@ -1607,10 +1683,10 @@ __global__ void __launch_bounds__(256) k_chain(const ChainParams p, const T *__r
   extern __shared__ __align__(16) char smem[];
   T *s = reinterpret_cast<T *>(smem);
   T *sB = s + p.tile;
-  uint64_t *sn = reinterpret_cast<uint64_t *>(
+  R *sn = reinterpret_cast<R *>(
       smem + ((sizeof(T) * (p.tile + TN_CHAIN_MAX_G * kGateBMax) + 15) / 16) * 16);
-  uint64_t *sBn = sn + (int64_t)p.P * p.tile;
-  load_gate_operands<T>(p, X, Xn, sB, sBn, kGateBMax);
+  R *sBn = sn + (int64_t)p.P * p.tile;
+  load_gate_operands<T, R>(p, X, Xn, sB, sBn, kGateBMax);
   for (int64_t o = blockIdx.x; o < p.outer; o += gridDim.x) {
     int64_t r = o, base = 0;
     for (int sg = p.nseg - 1; sg >= 0; --sg) {
@@ -1633,7 +1709,7 @@ __global__ void __launch_bounds__(256) k_chain(const ChainParams p, const T *__r
     __syncthreads();
     for (int gi = 0; gi < p.ngates; ++gi) {
       if (COUNT)
-        apply_gate_count<T, Q>(p.g[gi], s, sn, sB + gi * kGateBMax,
+        apply_gate_count<T, Q, R>(p.g[gi], s, sn, sB + gi * kGateBMax,
                                sBn + (int64_t)gi * p.P * kGateBMax, kGateBMax, p.tile, p.P, ps);
       else
         apply_gate<T, Q>(p.g[gi], s, s, sB + gi * kGateBMax, p.tile);
@@ -1653,23 +1729,24 @@ size_t chain_smem_bytes(const ChainParams &p, size_t elem) {
   return a + (size_t)p.P * 8 * (p.tile + (size_t)TN_CHAIN_MAX_G * kGateBMax);
 }
 
-template <typename T, int Q, bool COUNT>
+template <typename T, int Q, bool COUNT, typename R = uint64_t>
 static cudaError_t launch_chain_t(const ChainParams &p, const char *arena, const void *Ax,
                                   const uint64_t *An, void *Cx, uint64_t *Cn, const PrimeSet &ps,
                                   const Batch &bt, cudaStream_t st) {
   size_t sm = chain_smem_bytes(p, sizeof(T));
   static size_t configured = 0;
   if (sm > 48 * 1024 && sm > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_chain<T, Q, COUNT>,
+    cudaError_t e = cudaFuncSetAttribute(k_chain<T, Q, COUNT, R>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     configured = sm;
   }
   const int64_t gmax = num_sms() * 8;
   int64_t blocks = p.outer < gmax ? p.outer : gmax;
-  k_chain<T, Q, COUNT><<<dim3((unsigned)blocks, bt.B), 256, sm, st>>>(
-      p, reinterpret_cast<const T *>(arena), reinterpret_cast<const uint64_t *>(arena),
-      static_cast<const T *>(Ax), An, static_cast<T *>(Cx), Cn, ps, bt.ib);
+  k_chain<T, Q, COUNT, R><<<dim3((unsigned)blocks, bt.B), 256, sm, st>>>(
+      p, reinterpret_cast<const T *>(arena), reinterpret_cast<const R *>(arena),
+      static_cast<const T *>(Ax), reinterpret_cast<const R *>(An), static_cast<T *>(Cx),
+      reinterpret_cast<R *>(Cn), ps, bt.ib);
   return cudaGetLastError();
 }
 
@@ -1683,9 +1760,19 @@ cudaError_t launch_chain(Dtype dt, const ChainParams &p, const char *arena, cons
                          const uint64_t *An, void *Cx, uint64_t *Cn, const PrimeSet &ps,
                          const Batch &bt, cudaStream_t st) {
   if (p.outer == 0) return cudaSuccess;
-  if (p.mode == 1 && p.P > 0) return launch_rchain_count(dt, p, arena, Ax, An, Cx, Cn, ps, bt, st);
+  if (p.mode == 1 && p.P > 0) {
+    if (ps.r32) return cudaErrorInvalidValue;   // register counting chains: 8-byte planes
+    return launch_rchain_count(dt, p, arena, Ax, An, Cx, Cn, ps, bt, st);
+  }
   if (p.mode == 1) return launch_rchain(dt, p, arena, Ax, Cx, bt, st);
   const bool c = p.P > 0;
+  if (c && ps.r32) {
+    if (dt == DT_F32)
+      return p.q == 2 ? launch_chain_t<float, 2, true, uint32_t>(p, arena, Ax, An, Cx, Cn, ps, bt, st)
+                      : launch_chain_t<float, 3, true, uint32_t>(p, arena, Ax, An, Cx, Cn, ps, bt, st);
+    return p.q == 2 ? launch_chain_t<int32_t, 2, true, uint32_t>(p, arena, Ax, An, Cx, Cn, ps, bt, st)
+                    : launch_chain_t<int32_t, 3, true, uint32_t>(p, arena, Ax, An, Cx, Cn, ps, bt, st);
+  }
   if (dt == DT_F32) {
     if (p.q == 2) return c ? launch_chain_t<float, 2, true>(p, arena, Ax, An, Cx, Cn, ps, bt, st)
                            : launch_chain_t<float, 2, false>(p, arena, Ax, An, Cx, Cn, ps, bt, st);
@@ -1715,7 +1802,7 @@ __device__ void trace_chain(const ChainTrace &ct, const T *X, int8_t *state, int
     }
     *sbase = b;
   }
-  load_gate_operands<T>(p, X, nullptr, sB, nullptr, kGateBMax);
+  load_gate_operands<T, uint64_t>(p, X, nullptr, sB, nullptr, kGateBMax);
   __syncthreads();
   const int64_t base = *sbase;
   for (int i = threadIdx.x; i < p.tile; i += blockDim.x) buf[i] = X[base + tile_elem_off<Q>(p, i)];
@@ -1906,7 +1993,7 @@ __global__ void __launch_bounds__(256, MINB) k_rchain(const ChainParams p,
   __shared__ T sB[TN_CHAIN_MAX_G * kGateBMax];
   extern __shared__ __align__(16) char rstage[];
   T *stage = reinterpret_cast<T *>(rstage);
-  load_gate_operands<T>(p, X, nullptr, sB, nullptr, kGateBMax);
+  load_gate_operands<T, uint64_t>(p, X, nullptr, sB, nullptr, kGateBMax);
   __syncthreads();
   I sS[RB];
 #pragma unroll
@@ -2464,7 +2551,7 @@ __device__ void trace_rchain(const ChainTrace &ct, const T *X, int8_t *state, in
     trace_tchain<T>(ct, X, state, err, buf, sBg);
     return;
   }
-  load_gate_operands<T>(p, X, nullptr, sBg, nullptr, kGateBMax);
+  load_gate_operands<T, uint64_t>(p, X, nullptr, sBg, nullptr, kGateBMax);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) {

@@ -20,9 +20,11 @@ struct Batch {
 int num_sms();
 
 // Leaves (Sec. II bond / vertex tensors).  x: base of the value arena (bytes),
-// counts: when P > 0 every leaf element gets count 1 in each residue plane.
+// counts: when P > 0 every leaf element gets count 1 in each residue plane
+// (planes of rbytes = 8- or 4-byte residues).
 cudaError_t launch_leaves(Dtype dt, int q, const LeafDesc *d_leaves, int nleaves, const float *J,
-                          const float *h, char *arena, int P, const Batch &bt, cudaStream_t st);
+                          const float *h, char *arena, int P, int rbytes, const Batch &bt,
+                          cudaStream_t st);
 
 // Gate contraction (small B); xA/xB/xC value pointers, nA/nB/nC plane-0
 // pointers (counting only).

@@ -189,6 +189,7 @@ struct Builder {
   const Plan &plan;
   Program &pr;
   int q, P;
+  int rb;                                // bytes of one residue
   std::vector<std::vector<int>> order;   // memory leg order of each plan tensor
   std::vector<Loc> loc;
   std::string err;
@@ -198,7 +199,8 @@ struct Builder {
   std::vector<char> unit;
 
   Builder(const Net &n, const Plan &p, Program &r)
-      : net(n), plan(p), pr(r), q(r.q), P(r.P), order(p.legset.size()), loc(p.legset.size()),
+      : net(n), plan(p), pr(r), q(r.q), P(r.P), rb(r.rbytes), order(p.legset.size()),
+        loc(p.legset.size()),
         unit(p.legset.size(), 0) {
     for (int i = 0; i < p.n_leaves; ++i) unit[i] = 1;
     for (const PStep &st : p.steps)
@@ -214,7 +216,7 @@ struct Builder {
   Loc new_tensor(int64_t elems) {
     BufInfo b;
     int64_t xb = align_up(elems * 4);
-    b.bytes = xb + (P > 0 ? align_up((int64_t)P * elems * 8) : 0);
+    b.bytes = xb + (P > 0 ? align_up((int64_t)P * elems * rb) : 0);
     if (b.bytes == 0) b.bytes = kAlign;
     pr.bufs.push_back(b);
     Loc l;
@@ -230,7 +232,7 @@ struct Builder {
     b.first = std::min(b.first, op);
     b.last = std::max(b.last, op);
   }
-  double elem_bytes() const { return 4.0 + 8.0 * P; }
+  double elem_bytes() const { return 4.0 + (double)rb * P; }
   int push(Op op) {
     auto el = [&](const Loc &l) { return l.buf < 0 ? 0.0 : (double)l.plane; };
     if (op.kind == OP_PERM) op.bytes = 2 * el(op.out) * elem_bytes();
@@ -257,7 +259,7 @@ struct Builder {
       order[i] = plan.legset[i];
       Loc l = L;
       l.xoff = L.xoff + pr.leaf_elem[i] * 4;
-      l.noff = L.noff + pr.leaf_elem[i] * 8;
+      l.noff = L.noff + pr.leaf_elem[i] * rb;
       loc[i] = l;
     }
     Op op;
@@ -293,6 +295,7 @@ struct Builder {
     pp.planeIn = loc[t].plane;
     pp.planeOut = out.plane;
     pp.P = P;
+    pp.rbytes = rb;
     pr.perms.push_back(pp);
     Op op;
     op.kind = OP_PERM;
@@ -1144,7 +1147,8 @@ struct Builder {
   bool build(ProgMode mode, int64_t seg_bytes) {
     fuse = std::getenv("TN_NO_FUSION") == nullptr;
     // register chains: q = 2 values, or q = 2 counts with 3 primes + witness
-    regmode = q == 2 && (P == 0 || P == 4) && std::getenv("TN_TILE_CHAINS") == nullptr;
+    regmode = q == 2 && (P == 0 || (P == 4 && rb == 8)) &&
+              std::getenv("TN_TILE_CHAINS") == nullptr;
     fold = std::getenv("TN_NO_FOLD") == nullptr;
     // values: 6 register legs (2^6 states per thread) with folded tables,
     // 5 for the unfolded gate lists; counts: 3 legs (values + 4 residue planes)
@@ -1220,12 +1224,17 @@ void plan_memory(Program &pr) {
 int64_t abs_off(const Program &pr, const Loc &l) { return pr.bufs[l.buf].off + l.xoff; }
 
 bool build_program(const Net &net, const Plan &plan, ProgMode mode, Dtype dt, int P,
-                   int64_t seg_bytes, Program *pr, std::string *err) {
+                   int64_t seg_bytes, Program *pr, std::string *err, int rbytes) {
   *pr = Program();
   pr->mode = mode;
   pr->dt = dt;
   pr->q = net.q;
   pr->P = P;
+  if (rbytes != 4 && rbytes != 8) {
+    *err = "residue width must be 4 or 8 bytes";
+    return false;
+  }
+  pr->rbytes = rbytes;
   Builder bd(net, plan, *pr);
   if (!bd.build(mode, seg_bytes)) {
     *err = bd.err.empty() ? "program: lowering failed" : bd.err;
@@ -1289,7 +1298,7 @@ bool build_program(const Net &net, const Plan &plan, ProgMode mode, Dtype dt, in
     const Net::Leaf &L = net.leaves[i];
     LeafDesc d{};
     d.off_x = lbase + pr->leaves_loc.xoff + pr->leaf_elem[i] * 4;
-    d.off_n = lbase + pr->leaves_loc.noff + pr->leaf_elem[i] * 8;
+    d.off_n = lbase + pr->leaves_loc.noff + pr->leaf_elem[i] * pr->rbytes;
     d.plane = pr->leaves_loc.plane;
     d.kind = L.kind;
     d.edge = L.edge;
@@ -1316,7 +1325,7 @@ bool build_program(const Net &net, const Plan &plan, ProgMode mode, Dtype dt, in
   auto patch = [&](ChainParams &cp, const std::vector<Loc> &bl) {
     for (int g = 0; g < cp.ngates; ++g) {
       cp.g[g].offB = abs_off(*pr, bl[g]) / 4;
-      cp.g[g].offBn = (pr->bufs[bl[g].buf].off + bl[g].noff) / 8;
+      cp.g[g].offBn = (pr->bufs[bl[g].buf].off + bl[g].noff) / pr->rbytes;
       cp.g[g].planeB = bl[g].plane;
     }
   };

@@ -40,6 +40,7 @@ struct Program {
   ProgMode mode;
   Dtype dt;
   int q = 2, P = 0;
+  int rbytes = 8;                    // bytes of one residue of the counting planes
   std::vector<BufInfo> bufs;
   std::vector<Op> ops;
   std::vector<GateParams> gates;
@@ -79,8 +80,10 @@ struct Program {
 
 // Build the program for a plan.  seg_bytes: traceback checkpoint segment
 // budget (PM_CONFIG; <= 0 keeps every intermediate).
+// rbytes: bytes of one residue of the counting planes (8: 61-bit primes; 4:
+// 31-bit primes, the one-prime-per-pass counts).
 bool build_program(const Net &net, const Plan &plan, ProgMode mode, Dtype dt, int P,
-                   int64_t seg_bytes, Program *pr, std::string *err);
+                   int64_t seg_bytes, Program *pr, std::string *err, int rbytes = 8);
 
 int64_t abs_off(const Program &pr, const Loc &l);  // arena byte offset of values
 

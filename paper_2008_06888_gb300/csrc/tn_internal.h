@@ -64,6 +64,7 @@ struct PermParams {
   int64_t sin[TN_MAX_RANK];
   int64_t planeIn, planeOut;
   int P;
+  int rbytes;        // bytes of one residue (8, or 4 for 31-bit primes)
 };
 
 // One leaf tensor built from the couplings (Sec. II bond / vertex tensors).
@@ -197,7 +198,9 @@ struct ChainTrace {
   ChainParams p;
 };
 
-// 61-bit pseudo-Mersenne primes p = 2^61 - c (reduction after Crandall).
+// 61-bit pseudo-Mersenne primes p = 2^61 - c (reduction after Crandall), or,
+// for counts run one prime per pass in 4-byte planes, 31-bit ones 2^31 - c.
 struct PrimeSet {
   uint64_t c[TN_MAX_PRIMES];
+  int32_t r32;   // 1: residue planes hold uint32 residues of primes 2^31 - c
 };

@@ -151,6 +151,19 @@ def test_count_primes_are_61_bit_primes():
         assert _is_prime(p) and c < 1024
 
 
+def test_pass_primes_are_31_bit_primes():
+    """The one-prime-per-pass counts use 2^31 - c primes with c < 1024 (the
+    device reduction folds the 62-bit product twice, which needs c < 2^10)."""
+    src = open(os.path.join(ROOT, "paper_2008_06888_gb300", "csrc", "api.cpp")).read()
+    m = re.search(r"kPrime31C\[kPasses31Max\]\s*=\s*\{([^}]*)\}", src)
+    cs = [int(x) for x in m.group(1).split(",")]
+    assert len(set(cs)) == len(cs) == 17
+    for c in cs:
+        assert _is_prime((1 << 31) - c) and c < 1024
+    # enough passes for 8 61-bit primes plus a witness
+    assert (61 * 8 + 30) // 31 + 1 <= len(cs)
+
+
 def test_no_gpu_fails_loudly():
     import torch
     if torch.cuda.is_available():

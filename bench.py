@@ -16,7 +16,7 @@ cores (one process per core, each on a bounded prefix of its own instance).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
   python bench.py --impl reference ...   # the CPU oracle, a bounded sample per step
-  python bench.py --workload mixed|cubic|max2sat|sample   # the other workloads (one JSON line each)
+  python bench.py --workload mixed|cubic|max2sat|sample|chimera   # other workloads (one JSON line each)
 
 Multi-GPU (torchrun): every rank contracts its own instances (weak scaling, no
 data exchange); the slowest rank's time is reported.
@@ -63,9 +63,11 @@ def parse():
                     help="greedy restarts of the (untimed) order search")
     ap.add_argument("--quiet", action="store_true", help="print only value and kernel shares")
     ap.add_argument("--workload", default="square24",
-                    choices=["square24", "mixed", "cubic", "max2sat", "sample"],
+                    choices=["square24", "mixed", "cubic", "max2sat", "sample", "chimera"],
                     help="mixed: batch of +-J lattices with L uniform in 8..20, E_min + count")
     ap.add_argument("--mixed-n", type=int, default=2048, help="instances of the mixed batch")
+    ap.add_argument("--chimera-L", type=int, default=8,
+                    help="chimera workload: L x L unit cells (8: 512 spins)")
     ap.add_argument("--one-by-one-only", action="store_true",
                     help="mixed workload: time only the one-by-one sample (run by bench.py "
                          "itself with TN_NO_GRAPH=1 for the plain unbatched path)")
@@ -676,6 +678,50 @@ def run_ensemble(args):
         "cpu_baseline": None, "clocks": clk}), flush=True)
 
 
+def run_chimera(args):
+    """Chimera L x L K_{4,4} cells (L = 8: 512 spins, 1472 couplers), +-J, h = 0, cell-row
+    order: E_min and the exact ground-state count with 3 primes' range (at L = 8 the 61-bit
+    planes would need ~1.1 TB, so the count runs in 31-bit passes: 6 + a witness), and the
+    residual entropy ln(count) / N.  Instances one after another (seeds 1..steps)."""
+    import torch
+    import instances as I
+    import paper_2008_06888_gb300 as P
+    from paper_2008_06888_gb300 import binding as B
+    torch.cuda.set_device(0)
+    L8 = args.chimera_L
+    seq = I.chimera_sweep_order(L8)
+    rows = []
+    clocks = Clocks(0)
+    clocks.start()
+    t_all = 0.0
+    for k in range(args.warmup + args.steps):
+        inst = I.chimera(L8, coupling="pm1", seed=1 + k)
+        sg = P.SpinGlass(inst, order="sweep", seq=seq)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E = sg.energy()
+        t1 = time.perf_counter()
+        c, ln, E2 = sg.count(3)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        sg.close()
+        if k >= args.warmup:
+            t_all += t2 - t0
+            rows.append({"seed": 1 + k, "E_min": E, "count": str(c), "entropy_per_spin": ln / inst["n"],
+                         "energy_s": t1 - t0, "count_s": t2 - t1, "E_count_pass": E2})
+    clk = clocks.stop()
+    n = len(rows)
+    print(json.dumps({
+        "metric": METRIC, "value": n / t_all, "unit": "instances/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(n, 1),
+        "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"chimera {L8}x{L8} K44 cells ({8 * L8 * L8} spins), +-J, h=0, "
+                               f"cell-row order; E_min + exact count (range of 3 61-bit "
+                               f"primes; in 31-bit passes when their planes do not fit) per "
+                               f"instance"},
+        "instances": rows, "clocks": clk}), flush=True)
+
+
 def run_sample(args):
     """Uniform ground-state samples (tn_sample) of a degenerate 16x16 +-J lattice:
     256 steps, each one batched count of 2 x 16 pinned instances."""
@@ -720,6 +766,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "sample":
         return run_sample(args)
+    if args.workload == "chimera":
+        return run_chimera(args)
     import torch
     import torch.distributed as dist
 

@@ -185,12 +185,17 @@ tn_status tn_gradient(tn_ctx *ctx, float *dJ, float *dh, int32_t on_device);
 
 /*
  * tn_count -- ground-state degeneracy with the counting tuples of Sec. II.
- *   n_primes in [1, 8] 61-bit primes carry n exactly up to their product
- *   (~2^(61*n_primes)); one extra witness prime checks the reconstruction and
- *   TN_EOVERFLOW is returned when it disagrees.  limbs: little-endian 64-bit
- *   limbs of the count, capacity *n_limbs on input, limbs used on output.
- *   ln_count (may be NULL): natural log of the count.  *E (may be NULL):
- *   E_min of the same pass.
+ *   n_primes in [1, 8] sets the range: the count is exact up to about
+ *   2^(61*n_primes).  The residues are kept modulo ceil(61*n_primes/31)
+ *   31-bit primes 2^31 - c in 4-byte planes when those fit in 9 planes
+ *   (n_primes <= 4; TN_COUNT_61 forces the other form), else modulo n_primes
+ *   61-bit primes 2^61 - c in 8-byte planes; one extra witness prime checks
+ *   the reconstruction and TN_EOVERFLOW is returned when it disagrees.  When
+ *   the planes do not fit in device memory the count runs once per 31-bit
+ *   prime with a single plane (TN_COUNT_PASSES forces this).  limbs:
+ *   little-endian 64-bit limbs of the count, capacity *n_limbs on input,
+ *   limbs used on output.  ln_count (may be NULL): natural log of the count.
+ *   *E (may be NULL): E_min of the same pass.
  */
 tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_limbs,
                    double *ln_count, double *E);
@@ -228,10 +233,11 @@ tn_status tn_sample(tn_ctx *ctx, int32_t n_samples, uint64_t seed, const int32_t
  * tn_energy_batch -- E_min of each instance.
  * tn_config_batch -- E_min and the ground state (sigma: B*n_spins int8, host,
  *   may be NULL; same conventions as tn_config).
- * tn_count_batch -- E_min and degeneracy of each instance with n_primes
- *   primes + witness (as tn_count); limbs: B*limbs_per little-endian 64-bit
- *   limbs; status[b] (may be NULL) is TN_OK, TN_EOVERFLOW or TN_EINVAL (count
- *   needs more than limbs_per limbs).  Returns the first non-OK status.
+ * tn_count_batch -- E_min and degeneracy of each instance with the range of
+ *   n_primes 61-bit primes + witness (residue planes as tn_count); limbs:
+ *   B*limbs_per little-endian 64-bit limbs; status[b] (may be NULL) is TN_OK,
+ *   TN_EOVERFLOW or TN_EINVAL (count needs more than limbs_per limbs).
+ *   Returns the first non-OK status.
  */
 tn_status tn_energy_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
                           int32_t on_device, double *E);

@@ -13,8 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtn.so")
-SOURCES = ["kernels.cu", "noalloc.cu", "planner.cpp", "program.cpp", "api.cpp", "jit.cpp",
-           "sampler.cpp"]
+SOURCES = ["kernels.cu", "gate_count_i32.cu", "gate_count_f32.cu", "noalloc.cu", "planner.cpp",
+           "program.cpp", "api.cpp", "jit.cpp", "sampler.cpp"]
 # headers the run-time compiled chain kernels include (embedded into jit.cpp)
 JIT_HEADERS = [("kJitTnInternal", "tn_internal.h"), ("kJitChainDev", "chain_dev.cuh")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

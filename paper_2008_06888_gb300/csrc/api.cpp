@@ -50,7 +50,7 @@ struct tn_ctx {
   char *d_arena = nullptr;
   int64_t arena_cap = 0;
   std::unique_ptr<Program> prog[3];
-  int prog_P = 0;
+  int prog_P = 0, prog_rb = 8;
   bool have_state = false;
   bool fwd_done = false;   // tn_forward ran last; its checkpoints are live
   cudaStream_t cap_stream = nullptr;   // private stream for graph capture
@@ -180,10 +180,10 @@ tn_status ensure_device(tn_ctx *ctx) {
   return TN_OK;
 }
 
-tn_status get_program(tn_ctx *ctx, ProgMode mode, int P, Program **out) {
+tn_status get_program(tn_ctx *ctx, ProgMode mode, int P, Program **out, int rb = 8) {
   if (!ctx->ordered) return fail(ctx, TN_ESTATE, "tn_order has not been called");
   std::unique_ptr<Program> &slot = ctx->prog[mode];
-  if (!slot || (mode == PM_COUNT && ctx->prog_P != P)) {
+  if (!slot || (mode == PM_COUNT && (ctx->prog_P != P || ctx->prog_rb != rb))) {
     if (slot) free_program(slot.get());
     slot.reset(new Program());
     int64_t seg = 0;
@@ -205,7 +205,7 @@ tn_status get_program(tn_ctx *ctx, ProgMode mode, int P, Program **out) {
     }
     std::string err;
     if (!build_program(ctx->net, ctx->plan, mode, ctx->dt, mode == PM_COUNT ? P : 0, seg,
-                       slot.get(), &err)) {
+                       slot.get(), &err, mode == PM_COUNT ? rb : 8)) {
       slot.reset();
       return fail(ctx, TN_EINVAL, err);
     }
@@ -225,7 +225,10 @@ tn_status get_program(tn_ctx *ctx, ProgMode mode, int P, Program **out) {
       CK(cudaMemcpy(p.d_chain_traces, p.chain_traces.data(),
                     p.chain_traces.size() * sizeof(ChainTrace), cudaMemcpyHostToDevice));
     }
-    if (mode == PM_COUNT) ctx->prog_P = P;
+    if (mode == PM_COUNT) {
+      ctx->prog_P = P;
+      ctx->prog_rb = rb;
+    }
     // large value chains run as kernels compiled for their gate sequence; if
     // that fails they stay on the interpreting kernel (TN_JIT_STRICT: error)
     std::string jerr;
@@ -305,9 +308,9 @@ tn_status run_ops(tn_ctx *ctx, Program &p, int op_begin, int op_end, cudaStream_
   char *ar = ctx->d_arena;
   const Batch &bt = ra.bt;
   PrimeSet ps;
-  for (int i = 0; i < TN_MAX_PRIMES; ++i) ps.c[i] = kPrimeC[i];
   ps.r32 = p.rbytes == 4;
-  if (ps.r32) ps.c[0] = ctx->pass_c;   // one 31-bit prime per pass
+  for (int i = 0; i < TN_MAX_PRIMES; ++i) ps.c[i] = ps.r32 ? kPrime31C[i] : kPrimeC[i];
+  if (p.pass_prime) ps.c[0] = ctx->pass_c;   // one 31-bit prime per pass
   auto X = [&](const Loc &l) -> void * { return l.buf < 0 ? nullptr : ar + abs_off(p, l); };
   auto Nn = [&](const Loc &l) -> uint64_t * {
     return l.buf < 0 ? nullptr : (uint64_t *)(ar + p.bufs[l.buf].off + l.noff);
@@ -395,7 +398,7 @@ void account_range(tn_ctx *ctx, const Program &p, int b, int e, int B) {
 tn_status run_program(tn_ctx *ctx, Program &p, int op_begin, int op_end, const RunArgs &ra) {
   if (op_end < 0) op_end = (int)p.ops.size();
   static const bool no_graph = std::getenv("TN_NO_GRAPH") != nullptr;
-  if (ctx->profiling || no_graph || p.rbytes == 4)
+  if (ctx->profiling || no_graph || p.pass_prime)
     return run_ops(ctx, p, op_begin, op_end, ctx->stream, true, ra);
   Program::Graph *g = nullptr;
   for (auto &x : p.graphs)
@@ -557,7 +560,7 @@ tn_status ensure_batch(tn_ctx *ctx, int B) {
 }
 
 tn_status batch_setup(tn_ctx *ctx, int B, const float *J, const float *h, int on_device,
-                      ProgMode mode, int P, Program **out, RunArgs *ra) {
+                      ProgMode mode, int P, Program **out, RunArgs *ra, int rb = 8) {
   const Net &n = ctx->net;
   if (B < 1) return fail(ctx, TN_EINVAL, "batch size must be >= 1");
   if (n.m > 0 && !J) return fail(ctx, TN_EINVAL, "J is NULL");
@@ -576,7 +579,7 @@ tn_status batch_setup(tn_ctx *ctx, int B, const float *J, const float *h, int on
   tn_status s = ensure_device(ctx);
   if (s != TN_OK) return s;
   Program *p;
-  if ((s = get_program(ctx, mode, P, &p)) != TN_OK) return s;
+  if ((s = get_program(ctx, mode, P, &p, rb)) != TN_OK) return s;
   const int64_t stride = batch_stride(*p);
   if ((s = ensure_arena(ctx, stride * B)) != TN_OK) return s;
   if ((s = ensure_batch(ctx, B)) != TN_OK) return s;
@@ -615,13 +618,37 @@ tn_status check_trace_err(tn_ctx *ctx) {
 }
 
 // exact count of one instance from its residues (the last one is the witness)
-tn_status count_from_residues(tn_ctx *ctx, const std::vector<uint64_t> &res, int n_primes,
+// Residue planes that carry the range of n 61-bit primes (plus a witness):
+// ceil(61 n / 31) 31-bit primes in 4-byte planes when they fit in
+// TN_MAX_PRIMES planes (half the bytes per residue and a cheaper modular
+// product), else n 61-bit primes in 8-byte planes.  TN_COUNT_61 forces the
+// latter.
+struct CountRep {
+  int P, rb;
+  std::vector<uint64_t> primes;   // P primes, the last the witness
+};
+CountRep count_rep(int n_primes) {
+  CountRep r;
+  const int n31 = (61 * n_primes + 30) / 31;
+  if (n31 + 1 <= TN_MAX_PRIMES && std::getenv("TN_COUNT_61") == nullptr) {
+    r.P = n31 + 1;
+    r.rb = 4;
+    for (int i = 0; i < r.P; ++i) r.primes.push_back((1ull << 31) - kPrime31C[i]);
+  } else {
+    r.P = n_primes + 1;
+    r.rb = 8;
+    for (int i = 0; i < r.P; ++i) r.primes.push_back((1ull << 61) - kPrimeC[i]);
+  }
+  return r;
+}
+
+// exact count from residues res[i] modulo rep.primes[i] (the last one the witness)
+tn_status count_from_residues(tn_ctx *ctx, const std::vector<uint64_t> &res, const CountRep &rep,
                               std::vector<uint64_t> *v) {
-  std::vector<uint64_t> r(res.begin(), res.begin() + n_primes), pr;
-  for (int i = 0; i < n_primes; ++i) pr.push_back((1ull << 61) - kPrimeC[i]);
+  const size_t n = rep.primes.size() - 1;
+  std::vector<uint64_t> r(res.begin(), res.begin() + n), pr(rep.primes.begin(), rep.primes.begin() + n);
   *v = crt(r, pr);
-  const uint64_t pw = (1ull << 61) - kPrimeC[n_primes];
-  if (limbs_mod(*v, pw) != res[n_primes])
+  if (limbs_mod(*v, rep.primes[n]) != res[n])
     return fail(ctx, TN_EOVERFLOW, "count exceeds the product of the primes (witness mismatch)");
   return TN_OK;
 }
@@ -924,13 +951,13 @@ tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_li
     return fail(ctx, TN_EINVAL, "n_primes must be in [1, 8]");
   tn_status s = ensure_device(ctx);
   if (s != TN_OK) return s;
-  const int P = n_primes + 1;  // + witness
+  const CountRep rep = count_rep(n_primes);
   Program *p;
   const bool force_passes = std::getenv("TN_COUNT_PASSES") != nullptr;
   if (force_passes) return count_in_passes(ctx, n_primes, limbs, n_limbs, ln_count, E);
-  s = get_program(ctx, PM_COUNT, P, &p);
+  s = get_program(ctx, PM_COUNT, rep.P, &p, rep.rb);
   if (s == TN_ENOMEM) {
-    // the residue planes of P 61-bit primes do not fit: one 31-bit prime per pass
+    // the residue planes do not fit: one 31-bit prime per pass
     if (ctx->prog[PM_COUNT]) free_program(ctx->prog[PM_COUNT].get());
     ctx->prog[PM_COUNT].reset();
     return count_in_passes(ctx, n_primes, limbs, n_limbs, ln_count, E);
@@ -938,17 +965,15 @@ tn_status tn_count(tn_ctx *ctx, int32_t n_primes, uint64_t *limbs, int32_t *n_li
   if (s != TN_OK) return s;
   if ((s = run_program(ctx, *p)) != TN_OK) return s;
   char raw[4];
-  std::vector<uint64_t> res(P);
+  std::vector<uint64_t> res(rep.P, 0);
   const char *base = ctx->d_arena + p->bufs[p->root.buf].off;
   CK(cudaMemcpyAsync(raw, base + p->root.xoff, 4, cudaMemcpyDeviceToHost, ctx->stream));
-  for (int i = 0; i < P; ++i)
-    CK(cudaMemcpyAsync(&res[i], base + p->root.noff + (int64_t)i * p->root.plane * 8, 8,
+  for (int i = 0; i < rep.P; ++i)   // little-endian: a 4-byte residue fills the low half
+    CK(cudaMemcpyAsync(&res[i], base + p->root.noff + (int64_t)i * p->root.plane * rep.rb, rep.rb,
                        cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (E) *E = root_energy(ctx, raw);
-  std::vector<uint64_t> pr;
-  for (int i = 0; i <= n_primes; ++i) pr.push_back((1ull << 61) - kPrimeC[i]);
-  return finish_count(ctx, res, pr, limbs, n_limbs, ln_count);
+  return finish_count(ctx, res, rep.primes, limbs, n_limbs, ln_count);
 }
 
 }  // extern "C"
@@ -993,6 +1018,7 @@ tn_status count_in_passes(tn_ctx *ctx, int n_primes, uint64_t *limbs, int32_t *n
     std::string err;
     if (!build_program(ctx->net, ctx->plan, PM_COUNT, ctx->dt, 1, 0, pg.get(), &err, 4))
       return fail(ctx, TN_EINVAL, err);
+    pg->pass_prime = true;
     if (!pg->leaves.empty()) {
       CK(cudaMalloc(&pg->d_leaves, pg->leaves.size() * sizeof(LeafDesc)));
       CK(cudaMemcpy(pg->d_leaves, pg->leaves.data(), pg->leaves.size() * sizeof(LeafDesc),
@@ -1105,15 +1131,16 @@ tn_status pinned_stage(tn_ctx *ctx, size_t bytes, char **out) {
 
 // E, counts and statuses of B instances from their staged root values (raw:
 // 4 bytes each) and residues (res[i * B + b], plane i, the last the witness).
-tn_status finish_counts(tn_ctx *ctx, int B, int n_primes, const char *raw, const uint64_t *res,
-                        uint64_t *limbs, int32_t limbs_per, double *E, int32_t *status) {
-  const int P = n_primes + 1;
+tn_status finish_counts(tn_ctx *ctx, int B, const CountRep &rep, const char *raw,
+                        const uint64_t *res, uint64_t *limbs, int32_t limbs_per, double *E,
+                        int32_t *status) {
+  const int P = rep.P;
   tn_status first = TN_OK;
   for (int b = 0; b < B; ++b) {
     if (E) E[b] = root_energy(ctx, raw + 4 * b);
     std::vector<uint64_t> r(P), v;
     for (int i = 0; i < P; ++i) r[i] = res[(size_t)i * B + b];
-    tn_status sb = count_from_residues(ctx, r, n_primes, &v);
+    tn_status sb = count_from_residues(ctx, r, rep, &v);
     if (sb == TN_OK && (int)v.size() > limbs_per) {
       sb = TN_EINVAL;
       fail(ctx, sb, "limbs_per too small for a count");
@@ -1126,14 +1153,17 @@ tn_status finish_counts(tn_ctx *ctx, int B, int n_primes, const char *raw, const
   return first;
 }
 
-// queue the copies of B roots (and P residue planes) of a program's batch to host staging
+// queue the copies of B roots (and P residue planes) of a program's batch to host
+// staging; 4-byte residues land in the low halves of the (zeroed) 8-byte slots
 tn_status stage_results(tn_ctx *ctx, const Program &p, int B, int P, char *raw, uint64_t *res) {
   CK(cudaMemcpy2DAsync(raw, 4, ctx->d_arena + abs_off(p, p.root), batch_stride(p), 4, B,
                        cudaMemcpyDeviceToHost, ctx->stream));
   const char *rbase = ctx->d_arena + p.bufs[p.root.buf].off + p.root.noff;
+  const int rb = p.rbytes;
+  if (rb != 8) std::memset(res, 0, (size_t)P * B * 8);
   for (int i = 0; i < P; ++i)
-    CK(cudaMemcpy2DAsync(res + (size_t)i * B, 8, rbase + (int64_t)i * p.root.plane * 8,
-                         batch_stride(p), 8, B, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpy2DAsync(res + (size_t)i * B, 8, rbase + (int64_t)i * p.root.plane * rb,
+                         batch_stride(p), rb, B, cudaMemcpyDeviceToHost, ctx->stream));
   return TN_OK;
 }
 
@@ -1149,17 +1179,18 @@ tn_status tn_count_batch(tn_ctx *ctx, int32_t B, const float *J, const float *h,
   if (n_primes < 1 || n_primes > TN_MAX_PRIMES - 1)
     return fail(ctx, TN_EINVAL, "n_primes must be in [1, 8]");
   if (!limbs || limbs_per < 1) return fail(ctx, TN_EINVAL, "limbs buffer missing");
-  const int P = n_primes + 1;
+  const CountRep rep = count_rep(n_primes);
+  const int P = rep.P;
   Program *p;
   RunArgs ra;
-  tn_status s = batch_setup(ctx, B, J, h, on_device, PM_COUNT, P, &p, &ra);
+  tn_status s = batch_setup(ctx, B, J, h, on_device, PM_COUNT, P, &p, &ra, rep.rb);
   if (s != TN_OK) return s;
   if ((s = run_program(ctx, *p, 0, -1, ra)) != TN_OK) return s;
   std::vector<char> raw((size_t)B * 4);
   std::vector<uint64_t> res((size_t)P * B);
   if ((s = stage_results(ctx, *p, B, P, raw.data(), res.data())) != TN_OK) return s;
   CK(cudaStreamSynchronize(ctx->stream));
-  return finish_counts(ctx, B, n_primes, raw.data(), res.data(), limbs, limbs_per, E, status);
+  return finish_counts(ctx, B, rep, raw.data(), res.data(), limbs, limbs_per, E, status);
 }
 
 tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limbs,
@@ -1230,7 +1261,8 @@ tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limb
     const double wb = b.size() * std::exp2(ctxs[b[0]]->plan.log2_peak);
     return wa > wb;
   });
-  const int P = limbs ? 4 : 0;   // 3 primes + witness
+  const CountRep rep = count_rep(3);   // the range of 3 61-bit primes + witness
+  const int P = limbs ? rep.P : 0;
   size_t stage_bytes = 0;
   for (auto &ids : groups) stage_bytes += ids.size() * (4 + 8 * (size_t)P) + 64;
   char *stage = nullptr;
@@ -1286,7 +1318,7 @@ tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limb
     r.owner->stream = st;
     RunArgs ra;
     r.s = batch_setup(r.owner, G, J.data(), h.empty() ? nullptr : h.data(), 0,
-                      limbs ? PM_COUNT : PM_ENERGY, P, &r.p, &ra);
+                      limbs ? PM_COUNT : PM_ENERGY, P, &r.p, &ra, rep.rb);
     if (r.s == TN_OK) r.s = run_program(r.owner, *r.p, 0, -1, ra);
     if (r.s == TN_OK) r.s = stage_results(r.owner, *r.p, G, P, r.raw, r.res);
   }
@@ -1306,7 +1338,7 @@ tn_status tn_batch_run(int32_t B, tn_ctx *const *ctxs, double *E, uint64_t *limb
     tn_status s = r.s;
     if (s == TN_OK && limbs) {
       std::vector<uint64_t> lg((size_t)G * limbs_per);
-      s = finish_counts(r.owner, G, 3, r.raw, r.res, lg.data(), limbs_per, Eg.data(), sg.data());
+      s = finish_counts(r.owner, G, rep, r.raw, r.res, lg.data(), limbs_per, Eg.data(), sg.data());
       for (int g = 0; g < G; ++g)
         std::copy(lg.begin() + (size_t)g * limbs_per, lg.begin() + (size_t)(g + 1) * limbs_per,
                   limbs + (int64_t)ids[g] * limbs_per);
@@ -1385,7 +1417,9 @@ tn_status tn_plan_info(const tn_ctx *ctx, int32_t *n_steps, int32_t *n_transpose
     *arena_config = pc.arena_bytes;
   }
   if (arena_count) {
-    if (!build_program(ctx->net, ctx->plan, PM_COUNT, ctx->dt, 4, 0, &pn, &err)) return TN_EINVAL;
+    const CountRep rep = count_rep(3);
+    if (!build_program(ctx->net, ctx->plan, PM_COUNT, ctx->dt, rep.P, 0, &pn, &err, rep.rb))
+      return TN_EINVAL;
     *arena_count = pn.arena_bytes;
   }
   return TN_OK;
@@ -1397,7 +1431,9 @@ tn_status tn_plan_launches(const tn_ctx *ctx, int32_t mode, int64_t *counts) {
   Program pg;
   std::string err;
   const ProgMode pm = mode == 0 ? PM_ENERGY : mode == 1 ? PM_CONFIG : PM_COUNT;
-  if (!build_program(ctx->net, ctx->plan, pm, ctx->dt, pm == PM_COUNT ? 4 : 0, 0, &pg, &err))
+  const CountRep rep = count_rep(3);
+  if (!build_program(ctx->net, ctx->plan, pm, ctx->dt, pm == PM_COUNT ? rep.P : 0, 0, &pg, &err,
+                     pm == PM_COUNT ? rep.rb : 8))
     return TN_EINVAL;
   for (int k = 0; k < 7; ++k) counts[k] = 0;
   for (const Op &op : pg.ops) {

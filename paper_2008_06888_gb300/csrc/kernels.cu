@@ -21,6 +21,7 @@
 #include "kernels.h"
 #include "perm_bits.h"
 #include "chain_dev.cuh"
+#include "modarith.cuh"
 
 namespace tn {
 
@@ -36,59 +37,7 @@ template <> struct Lim<int32_t> {
   __device__ __forceinline__ static int32_t neg() { return -(1 << 30); }
 };
 
-static constexpr uint64_t M61 = (1ull << 61) - 1;
-
-// a * b mod p for p = 2^61 - c, a, b < p, c < 2^10.  The 122-bit product is
-// folded twice with 2^61 = c (mod p) (pseudo-Mersenne reduction, Crandall 1992).
-__device__ __forceinline__ uint64_t mulmod61(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t lo = a * b;
-  uint64_t hi = __umul64hi(a, b);
-  uint64_t x1 = (hi << 3) | (lo >> 61);   // product >> 61, < 2^61
-  uint64_t x0 = lo & M61;
-  uint64_t t_lo = x1 * c;
-  uint64_t t_hi = __umul64hi(x1, c);
-  uint64_t y_lo = t_lo + x0;
-  uint64_t y_hi = t_hi + (y_lo < t_lo ? 1ull : 0ull);
-  uint64_t y1 = (y_hi << 3) | (y_lo >> 61);  // < 2^11
-  uint64_t z = y1 * c + (y_lo & M61);        // < 2^61 + 2^21 < 2p
-  uint64_t p = M61 + 1 - c;
-  return z >= p ? z - p : z;
-}
-
-__device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t p = M61 + 1 - c;
-  uint64_t s = a + b;
-  return s >= p ? s - p : s;
-}
-
-// The same for p = 2^31 - c (c < 2^10) on 4-byte residues: the 62-bit product
-// is folded twice with 2^31 = c (mod p).
-static constexpr uint64_t M31 = (1ull << 31) - 1;
-__device__ __forceinline__ uint32_t mulmod31(uint32_t a, uint32_t b, uint64_t c) {
-  const uint64_t x = (uint64_t)a * b;                  // < 2^62
-  const uint64_t y = (x >> 31) * c + (x & M31);        // < 2^41
-  const uint64_t z = (y >> 31) * c + (y & M31);        // < 2^31 + 2^20 < 2p
-  const uint64_t p = M31 + 1 - c;
-  return (uint32_t)(z >= p ? z - p : z);
-}
-__device__ __forceinline__ uint32_t addmod31(uint32_t a, uint32_t b, uint64_t c) {
-  const uint32_t p = (uint32_t)(M31 + 1 - c);
-  const uint32_t s = a + b;                            // < 2p < 2^32
-  return s >= p ? s - p : s;
-}
-// residue arithmetic by plane width
-__device__ __forceinline__ uint64_t mulmodR(uint64_t a, uint64_t b, uint64_t c) {
-  return mulmod61(a, b, c);
-}
-__device__ __forceinline__ uint32_t mulmodR(uint32_t a, uint32_t b, uint64_t c) {
-  return mulmod31(a, b, c);
-}
-__device__ __forceinline__ uint64_t addmodR(uint64_t a, uint64_t b, uint64_t c) {
-  return addmod61(a, b, c);
-}
-__device__ __forceinline__ uint32_t addmodR(uint32_t a, uint32_t b, uint64_t c) {
-  return addmod31(a, b, c);
-}
+// modular arithmetic of the residue planes: modarith.cuh
 
 // Streaming multiprocessors of the current device (GB300: 152), queried once
 // per device; grid sizes are multiples of it.
@@ -498,13 +447,32 @@ static bool gate2_form(const GateParams &p, const void *A, const void *B, const 
 // four outer indices).  Per output the terms are taken in k order: the first
 // term and every larger one replace (value, counts), an equal one adds its
 // counts mod p -- the rule of k_gate, so the results are identical.
-template <typename T, int KS, int NS, int P>
+// four consecutive residues (16-byte aligned): two 16-byte accesses for 8-byte
+// residues, one for 4-byte ones
+__device__ __forceinline__ void ld4(const uint64_t *p, uint64_t *o) {
+  const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(p);
+  const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(p + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const uint32_t *p, uint32_t *o) {
+  const uint4 a = *reinterpret_cast<const uint4 *>(p);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void st4(uint64_t *p, const uint64_t *v) {
+  *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(v[0], v[1]);
+  *reinterpret_cast<ulonglong2 *>(p + 2) = make_ulonglong2(v[2], v[3]);
+}
+__device__ __forceinline__ void st4(uint32_t *p, const uint32_t *v) {
+  *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+}
+
+template <typename T, int KS, int NS, int P, typename R = uint64_t>
 __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 g,
                                                 const T *__restrict__ A, const T *__restrict__ B,
                                                 T *__restrict__ C,
-                                                const uint64_t *__restrict__ nA,
-                                                const uint64_t *__restrict__ nB,
-                                                uint64_t *__restrict__ nC, const PrimeSet ps,
+                                                const R *__restrict__ nA,
+                                                const R *__restrict__ nB,
+                                                R *__restrict__ nC, const PrimeSet ps,
                                                 int64_t ib) {
   typedef typename Vec4<T>::t V;
   A = inst_ptr(A, ib);
@@ -516,7 +484,7 @@ __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 
     nB = inst_ptr(nB, ib);
   }
   __shared__ T sBt[16];            // index: bd0 | bd1 << 1 | k << 2 | n << 3
-  __shared__ uint64_t sBn[P][16];
+  __shared__ R sBn[P][16];
   const bool mulB = p.hasB && !p.unitB;
   if (threadIdx.x < 16) {
     const int i = threadIdx.x, b0 = i & 1, b1 = (i >> 1) & 1, k = (i >> 2) & 1, n = (i >> 3) & 1;
@@ -524,7 +492,7 @@ __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 
     const int64_t off = ok ? p.kB[k] + p.nB[n] + b0 * g.sb[0] + b1 * g.sb[1] : 0;
     sBt[i] = ok ? B[off] : T(0);
 #pragma unroll
-    for (int r = 0; r < P; ++r) sBn[r][i] = (ok && mulB) ? nB[r * p.planeB + off] : 1ull;
+    for (int r = 0; r < P; ++r) sBn[r][i] = (ok && mulB) ? nB[r * p.planeB + off] : R(1);
   }
   __syncthreads();
   const int pb0 = g.nbd > 0 ? g.pb[0] : 62, pb1 = g.nbd > 1 ? g.pb[1] : 62;
@@ -534,7 +502,7 @@ __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nq; t += stride) {
     const int64_t j0 = t << 2;
     T a[KS][4];
-    uint64_t na[P][KS][4];
+    R na[P][KS][4];
     if (KS == 1 || pk >= 2) {
       int64_t base = j0;
       if (KS == 2) {
@@ -547,11 +515,7 @@ __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 
         const V v = *reinterpret_cast<const V *>(A + e);
         a[k][0] = v.x; a[k][1] = v.y; a[k][2] = v.z; a[k][3] = v.w;
 #pragma unroll
-        for (int r = 0; r < P; ++r) {
-          const ulonglong2 c0 = *reinterpret_cast<const ulonglong2 *>(nA + r * p.planeA + e);
-          const ulonglong2 c1 = *reinterpret_cast<const ulonglong2 *>(nA + r * p.planeA + e + 2);
-          na[r][k][0] = c0.x; na[r][k][1] = c0.y; na[r][k][2] = c1.x; na[r][k][3] = c1.y;
-        }
+        for (int r = 0; r < P; ++r) ld4(nA + r * p.planeA + e, na[r][k]);
       }
     } else {
       // the contracted leg is one of the two lowest bits: 8 contiguous elements
@@ -565,13 +529,9 @@ __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 
           a[k][q4] = pk == 0 ? blk[2 * q4 + k] : blk[((q4 >> 1) << 2) | (k << 1) | (q4 & 1)];
 #pragma unroll
       for (int r = 0; r < P; ++r) {
-        uint64_t cb[8];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(nA + r * p.planeA + 2 * j0 + 2 * h);
-          cb[2 * h] = c.x;
-          cb[2 * h + 1] = c.y;
-        }
+        R cb[8];
+        ld4(nA + r * p.planeA + 2 * j0, cb);
+        ld4(nA + r * p.planeA + 2 * j0 + 4, cb + 4);
 #pragma unroll
         for (int q4 = 0; q4 < 4; ++q4)
 #pragma unroll
@@ -580,7 +540,7 @@ __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 
       }
     }
     T out[NS][4];
-    uint64_t cout[P][NS][4];
+    R cout[P][NS][4];
 #pragma unroll
     for (int q4 = 0; q4 < 4; ++q4) {
       const int64_t j = j0 + q4;
@@ -588,10 +548,10 @@ __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 
 #pragma unroll
       for (int n = 0; n < NS; ++n) {
         T best = a[0][q4] + sBt[bd | (n << 3)];
-        uint64_t cnt[P];
+        R cnt[P];
 #pragma unroll
         for (int r = 0; r < P; ++r)
-          cnt[r] = mulB ? mulmod61(na[r][0][q4], sBn[r][bd | (n << 3)], ps.c[r]) : na[r][0][q4];
+          cnt[r] = mulB ? mulmodR(na[r][0][q4], sBn[r][bd | (n << 3)], ps.c[r]) : na[r][0][q4];
 #pragma unroll
         for (int k = 1; k < KS; ++k) {
           const int bi = bd | (k << 2) | (n << 3);
@@ -600,9 +560,8 @@ __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 
             const bool gt = v > best;
 #pragma unroll
             for (int r = 0; r < P; ++r) {
-              const uint64_t tr =
-                  mulB ? mulmod61(na[r][k][q4], sBn[r][bi], ps.c[r]) : na[r][k][q4];
-              cnt[r] = gt ? tr : addmod61(cnt[r], tr, ps.c[r]);
+              const R tr = mulB ? mulmodR(na[r][k][q4], sBn[r][bi], ps.c[r]) : na[r][k][q4];
+              cnt[r] = gt ? tr : addmodR(cnt[r], tr, ps.c[r]);
             }
             best = gt ? v : best;
           }
@@ -617,7 +576,7 @@ __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 
     for (int h = 0; h < NS; ++h) {
       const int q0 = 4 * h;   // flat output index f = NS * q4 + n covers [q0, q0 + 4)
       T o4[4];
-      uint64_t c4[P][4];
+      R c4[P][4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int f = q0 + e, q4 = f / NS, n = f % NS;
@@ -629,11 +588,7 @@ __global__ void __launch_bounds__(256) k_gate2c(const GateParams p, const Gate2 
       v.x = o4[0]; v.y = o4[1]; v.z = o4[2]; v.w = o4[3];
       *reinterpret_cast<V *>(C + NS * j0 + q0) = v;
 #pragma unroll
-      for (int r = 0; r < P; ++r) {
-        uint64_t *dst = nC + r * p.planeC + NS * j0 + q0;
-        *reinterpret_cast<ulonglong2 *>(dst) = make_ulonglong2(c4[r][0], c4[r][1]);
-        *reinterpret_cast<ulonglong2 *>(dst + 2) = make_ulonglong2(c4[r][2], c4[r][3]);
-      }
+      for (int r = 0; r < P; ++r) st4(nC + r * p.planeC + NS * j0 + q0, c4[r]);
     }
   }
 }
@@ -642,28 +597,38 @@ template <typename T>
 static bool launch_gate2c(const GateParams &p, const T *A, const T *B, T *C, const uint64_t *nA,
                           const uint64_t *nB, uint64_t *nC, const PrimeSet &ps, const Batch &bt,
                           cudaStream_t st) {
-  if (p.P != 4 || ps.r32 || std::getenv("TN_NO_GATE2")) return false;
+  // 4 planes of 8-byte residues or 7 of 4-byte ones
+  if (!((p.P == 4 && !ps.r32) || (p.P == 7 && ps.r32)) || std::getenv("TN_NO_GATE2")) return false;
   GateParams q = p;
   q.P = 0;   // gate2_form checks the value layout; the planes share it
   Gate2 g;
   if (!gate2_form(q, A, B, C, bt.ib, sizeof(T), &g)) return false;
+  const int rb = ps.r32 ? 4 : 8;
   if ((reinterpret_cast<uintptr_t>(nA) | reinterpret_cast<uintptr_t>(nC)) % 16 ||
-      (p.planeA | p.planeC) & 1)
+      (p.planeA * rb) % 16 || (p.planeC * rb) % 16)
     return false;
   const int64_t nq = p.outer >> 2;
   const int64_t need = (nq + 255) / 256;
-#define TN_G2C(KS_, NS_)                                                                          \
-  if (p.Ks == KS_ && p.Ns == NS_) {                                                              \
-    const int64_t blocks =                                                                       \
-        wave_blocks(need, bt.B, resident_slots(k_gate2c<T, KS_, NS_, 4>, 256, 0));               \
-    k_gate2c<T, KS_, NS_, 4><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(p, g, A, B, C, nA, nB, \
-                                                                          nC, ps, bt.ib);        \
-    return true;                                                                                 \
+#define TN_G2C(KS_, NS_, P_, R_)                                                                 \
+  if (p.Ks == KS_ && p.Ns == NS_) {                                                            \
+    const int64_t blocks =                                                                     \
+        wave_blocks(need, bt.B, resident_slots(k_gate2c<T, KS_, NS_, P_, R_>, 256, 0));        \
+    k_gate2c<T, KS_, NS_, P_, R_><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(               \
+        p, g, A, B, C, reinterpret_cast<const R_ *>(nA), reinterpret_cast<const R_ *>(nB),     \
+        reinterpret_cast<R_ *>(nC), ps, bt.ib);                                                \
+    return true;                                                                               \
   }
-  TN_G2C(1, 1)
-  TN_G2C(1, 2)
-  TN_G2C(2, 1)
-  TN_G2C(2, 2)
+  if (ps.r32) {
+    TN_G2C(1, 1, 7, uint32_t)
+    TN_G2C(1, 2, 7, uint32_t)
+    TN_G2C(2, 1, 7, uint32_t)
+    TN_G2C(2, 2, 7, uint32_t)
+  } else {
+    TN_G2C(1, 1, 4, uint64_t)
+    TN_G2C(1, 2, 4, uint64_t)
+    TN_G2C(2, 1, 4, uint64_t)
+    TN_G2C(2, 2, 4, uint64_t)
+  }
 #undef TN_G2C
   return false;
 }
@@ -717,6 +682,13 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
                      : launch_gate2c<int32_t>(p, (const int32_t *)xA, (const int32_t *)xB,
                                               (int32_t *)xC, nA, nB, nC, ps, bt, st);
     if (streamed) return cudaGetLastError();
+    if (ps.r32 && !std::getenv("TN_NO_GATE_TC")) {
+      const uint32_t *a = (const uint32_t *)nA, *b = (const uint32_t *)nB;
+      uint32_t *c = (uint32_t *)nC;
+      if (dt == DT_F32 ? launch_gate_tc_f32(p, xA, xB, xC, a, b, c, ps, bt, st)
+                       : launch_gate_tc_i32(p, xA, xB, xC, a, b, c, ps, bt, st))
+        return cudaGetLastError();
+    }
   }
   if (cnt && ps.r32) {
     const uint32_t *a = (const uint32_t *)nA, *b = (const uint32_t *)nB;
@@ -1760,10 +1732,7 @@ cudaError_t launch_chain(Dtype dt, const ChainParams &p, const char *arena, cons
                          const uint64_t *An, void *Cx, uint64_t *Cn, const PrimeSet &ps,
                          const Batch &bt, cudaStream_t st) {
   if (p.outer == 0) return cudaSuccess;
-  if (p.mode == 1 && p.P > 0) {
-    if (ps.r32) return cudaErrorInvalidValue;   // register counting chains: 8-byte planes
-    return launch_rchain_count(dt, p, arena, Ax, An, Cx, Cn, ps, bt, st);
-  }
+  if (p.mode == 1 && p.P > 0) return launch_rchain_count(dt, p, arena, Ax, An, Cx, Cn, ps, bt, st);
   if (p.mode == 1) return launch_rchain(dt, p, arena, Ax, Cx, bt, st);
   const bool c = p.P > 0;
   if (c && ps.r32) {
@@ -2284,14 +2253,15 @@ __global__ void __launch_bounds__(NT, MINB) k_tchain(const ChainParams p,
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// ---- counting register chains (q = 2, P = 4 residue planes): every thread
-// keeps the 2^RB values and their 4 residues in registers.  A tie adds the
+// ---- counting register chains (q = 2; 4 residue planes of 61-bit primes or 7
+// of 31-bit primes): every thread keeps the 2^RB values and their residues in
+// registers.  A tie adds the
 // counts of the tied states; the gate's own counts multiply in unless it is a
 // leaf (all counts 1).
 
-template <int RB, int NP, bool UNIT, typename T>
-__device__ __forceinline__ void rcc_replace(int J, T (&v)[1 << RB], uint64_t (&n)[NP][1 << RB],
-                                            const ChainGate &g, const T *sB, const uint64_t *sBn,
+template <int RB, int NP, bool UNIT, typename T, typename R>
+__device__ __forceinline__ void rcc_replace(int J, T (&v)[1 << RB], R (&n)[NP][1 << RB],
+                                            const ChainGate &g, const T *sB, const R *sBn,
                                             int64_t base, const PrimeSet &ps) {
   int wm = 0, wf = 0;
   if (g.nb > 0) leg_sel(g, 0, base, &wm, &wf);
@@ -2309,18 +2279,18 @@ __device__ __forceinline__ void rcc_replace(int J, T (&v)[1 << RB], uint64_t (&n
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) {
       const uint64_t c = ps.c[pl];
-      const uint64_t na = n[pl][e], nb = n[pl][e1];
+      const R na = n[pl][e], nb = n[pl][e1];
       if (UNIT) {
         // leaf operand: counts of the tied states add (at least one is tied)
-        const uint64_t both = addmod61(na, nb, c);
+        const R both = addmodR(na, nb, c);
         n[pl][e] = t00 ? (t10 ? both : na) : nb;
         n[pl][e1] = t01 ? (t11 ? both : na) : nb;
       } else {
-        const uint64_t *bn = sBn + pl * kGateBMax;
-        const uint64_t a0 = mulmod61(na, bn[i00], c), b0 = mulmod61(nb, bn[i10], c);
-        const uint64_t a1 = mulmod61(na, bn[i01], c), b1 = mulmod61(nb, bn[i11], c);
-        n[pl][e] = t00 ? (t10 ? addmod61(a0, b0, c) : a0) : b0;
-        n[pl][e1] = t01 ? (t11 ? addmod61(a1, b1, c) : a1) : b1;
+        const R *bn = sBn + pl * kGateBMax;
+        const R a0 = mulmodR(na, bn[i00], c), b0 = mulmodR(nb, bn[i10], c);
+        const R a1 = mulmodR(na, bn[i01], c), b1 = mulmodR(nb, bn[i11], c);
+        n[pl][e] = t00 ? (t10 ? addmodR(a0, b0, c) : a0) : b0;
+        n[pl][e1] = t01 ? (t11 ? addmodR(a1, b1, c) : a1) : b1;
       }
     }
     v[e] = o0;
@@ -2328,9 +2298,9 @@ __device__ __forceinline__ void rcc_replace(int J, T (&v)[1 << RB], uint64_t (&n
   }
 }
 
-template <int RB, int NP, typename T>
-__device__ __forceinline__ void rcc_diag(T (&v)[1 << RB], uint64_t (&n)[NP][1 << RB],
-                                         const ChainGate &g, const T *sB, const uint64_t *sBn,
+template <int RB, int NP, typename T, typename R>
+__device__ __forceinline__ void rcc_diag(T (&v)[1 << RB], R (&n)[NP][1 << RB],
+                                         const ChainGate &g, const T *sB, const R *sBn,
                                          int64_t base, const PrimeSet &ps) {
   int m0 = 0, f0 = 0, m1 = 0, f1 = 0;
   leg_sel(g, 0, base, &m0, &f0);
@@ -2349,18 +2319,18 @@ __device__ __forceinline__ void rcc_diag(T (&v)[1 << RB], uint64_t (&n)[NP][1 <<
     const int bo = x0 * s0 + x1 * s1;
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl)
-      n[pl][e] = mulmod61(n[pl][e], sBn[pl * kGateBMax + bo], ps.c[pl]);
+      n[pl][e] = mulmodR(n[pl][e], sBn[pl * kGateBMax + bo], ps.c[pl]);
   }
 }
 
-template <typename T, int RB, int NP>
+template <typename T, int RB, int NP, typename R = uint64_t>
 __global__ void __launch_bounds__(256, 2) k_rchain_count(const ChainParams p,
                                                          const T *__restrict__ X,
-                                                         const uint64_t *__restrict__ Xn,
+                                                         const R *__restrict__ Xn,
                                                          const T *__restrict__ A,
-                                                         const uint64_t *__restrict__ An,
+                                                         const R *__restrict__ An,
                                                          T *__restrict__ C,
-                                                         uint64_t *__restrict__ Cn,
+                                                         R *__restrict__ Cn,
                                                          const PrimeSet ps, int64_t ib) {
   X = inst_ptr(X, ib);
   Xn = inst_ptr(Xn, ib);
@@ -2369,9 +2339,9 @@ __global__ void __launch_bounds__(256, 2) k_rchain_count(const ChainParams p,
   C = inst_ptr(C, ib);
   Cn = inst_ptr(Cn, ib);
   __shared__ T sB[TN_CHAIN_MAX_G * kGateBMax];
-  __shared__ uint64_t sBn[TN_CHAIN_MAX_G * NP * kGateBMax];
+  __shared__ R sBn[TN_CHAIN_MAX_G * NP * kGateBMax];
   __shared__ int64_t soff[1 << RB];
-  load_gate_operands<T>(p, X, Xn, sB, sBn, kGateBMax);
+  load_gate_operands<T, R>(p, X, Xn, sB, sBn, kGateBMax);
   for (int e = threadIdx.x; e < (1 << RB); e += blockDim.x) soff[e] = p.hi_off[e];
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -2382,7 +2352,7 @@ __global__ void __launch_bounds__(256, 2) k_rchain_count(const ChainParams p,
       r >>= p.seg_sh[sg];
     }
     T v[1 << RB];
-    uint64_t n[NP][1 << RB];
+    R n[NP][1 << RB];
 #pragma unroll
     for (int e = 0; e < (1 << RB); ++e) {
       const int64_t off = base + soff[e];
@@ -2393,7 +2363,7 @@ __global__ void __launch_bounds__(256, 2) k_rchain_count(const ChainParams p,
     for (int gi = 0; gi < p.ngates; ++gi) {
       const ChainGate &g = p.g[gi];
       const T *gB = sB + gi * kGateBMax;
-      const uint64_t *gBn = sBn + (int64_t)gi * NP * kGateBMax;
+      const R *gBn = sBn + (int64_t)gi * NP * kGateBMax;
       if (g.kind != 0) {
         rcc_diag<RB, NP>(v, n, g, gB, gBn, base, ps);
         continue;
@@ -2425,19 +2395,23 @@ __global__ void __launch_bounds__(256, 2) k_rchain_count(const ChainParams p,
 cudaError_t launch_rchain_count(Dtype dt, const ChainParams &p, const char *arena,
                                 const void *Ax, const uint64_t *An, void *Cx, uint64_t *Cn,
                                 const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
-  if (p.t != 3 || p.P != 4) return cudaErrorInvalidValue;
+  if (p.t != 3 || !((p.P == 4 && !ps.r32) || (p.P == 7 && ps.r32))) return cudaErrorInvalidValue;
   const int64_t need = (p.outer + 255) / 256;
-  const int64_t blocks =
-      dt == DT_F32 ? wave_blocks(need, bt.B, resident_slots(k_rchain_count<float, 3, 4>, 256, 0))
-                   : wave_blocks(need, bt.B, resident_slots(k_rchain_count<int32_t, 3, 4>, 256, 0));
-  if (dt == DT_F32)
-    k_rchain_count<float, 3, 4><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(
-        p, reinterpret_cast<const float *>(arena), reinterpret_cast<const uint64_t *>(arena),
-        static_cast<const float *>(Ax), An, static_cast<float *>(Cx), Cn, ps, bt.ib);
-  else
-    k_rchain_count<int32_t, 3, 4><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(
-        p, reinterpret_cast<const int32_t *>(arena), reinterpret_cast<const uint64_t *>(arena),
-        static_cast<const int32_t *>(Ax), An, static_cast<int32_t *>(Cx), Cn, ps, bt.ib);
+#define TN_RCC(T_, NP_, R_)                                                                      \
+  do {                                                                                           \
+    const int64_t blocks =                                                                       \
+        wave_blocks(need, bt.B, resident_slots(k_rchain_count<T_, 3, NP_, R_>, 256, 0));         \
+    k_rchain_count<T_, 3, NP_, R_><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(                \
+        p, reinterpret_cast<const T_ *>(arena), reinterpret_cast<const R_ *>(arena),             \
+        static_cast<const T_ *>(Ax), reinterpret_cast<const R_ *>(An), static_cast<T_ *>(Cx),    \
+        reinterpret_cast<R_ *>(Cn), ps, bt.ib);                                                  \
+  } while (0)
+  if (dt == DT_F32) {
+    if (ps.r32) TN_RCC(float, 7, uint32_t); else TN_RCC(float, 4, uint64_t);
+  } else {
+    if (ps.r32) TN_RCC(int32_t, 7, uint32_t); else TN_RCC(int32_t, 4, uint64_t);
+  }
+#undef TN_RCC
   return cudaGetLastError();
 }
 

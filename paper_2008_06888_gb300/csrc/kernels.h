@@ -32,6 +32,16 @@ cudaError_t launch_gate(Dtype dt, const GateParams &p, const void *xA, const voi
                         const uint64_t *nA, const uint64_t *nB, uint64_t *nC, const PrimeSet &ps,
                         const Batch &bt, cudaStream_t st);
 
+// Counting gate contraction with compile-time (K, N, planes) forms for 4-byte
+// residue planes (gate_count_*.cu); false when the step has no such form (the
+// generic kernel runs it).
+bool launch_gate_tc_i32(const GateParams &p, const void *A, const void *B, void *C,
+                        const uint32_t *nA, const uint32_t *nB, uint32_t *nC, const PrimeSet &ps,
+                        const Batch &bt, cudaStream_t st);
+bool launch_gate_tc_f32(const GateParams &p, const void *A, const void *B, void *C,
+                        const uint32_t *nA, const uint32_t *nB, uint32_t *nC, const PrimeSet &ps,
+                        const Batch &bt, cudaStream_t st);
+
 // Register-tiled max-plus GEMM (128 x 128 tiles, cp.async staging), values only.
 // The tile configuration of a shape class is chosen by timing the candidates
 // on its first launch outside stream capture (set_gemm_autotune(false) on the

@@ -1147,7 +1147,7 @@ struct Builder {
   bool build(ProgMode mode, int64_t seg_bytes) {
     fuse = std::getenv("TN_NO_FUSION") == nullptr;
     // register chains: q = 2 values, or q = 2 counts with 3 primes + witness
-    regmode = q == 2 && (P == 0 || (P == 4 && rb == 8)) &&
+    regmode = q == 2 && (P == 0 || (P == 4 && rb == 8) || (P == 7 && rb == 4)) &&
               std::getenv("TN_TILE_CHAINS") == nullptr;
     fold = std::getenv("TN_NO_FOLD") == nullptr;
     // values: 6 register legs (2^6 states per thread) with folded tables,

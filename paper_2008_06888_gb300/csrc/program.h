@@ -41,6 +41,7 @@ struct Program {
   Dtype dt;
   int q = 2, P = 0;
   int rbytes = 8;                    // bytes of one residue of the counting planes
+  bool pass_prime = false;           // one 31-bit prime per pass: plane 0's prime is set per run
   std::vector<BufInfo> bufs;
   std::vector<Op> ops;
   std::vector<GateParams> gates;

@@ -115,3 +115,37 @@ def test_chimera8_counts_in_passes():
     assert E0 == E and int(c) >= 2 and int(c) % 2 == 0
     assert E >= -1472 and int(E) % 2 == 0     # +-J: E_min = n_edges (mod 2)
     assert 0.0 < s < 0.1
+
+
+@pytest.mark.parametrize("case", list(_cases())[:4], ids=lambda c: c[0])
+def test_31_and_61_bit_planes_give_the_same_counts(case, monkeypatch):
+    """The default residue planes (ceil(61 n / 31) 31-bit primes, 4 bytes each) and
+    the 61-bit ones (TN_COUNT_61) reconstruct the same integers as the oracle; five
+    61-bit primes (beyond nine 31-bit planes) take the 61-bit form."""
+    name, inst, kw = case
+    o = O.solve(inst, order=kw.get("seq"), config=False)
+    sg = P.SpinGlass(inst, **kw)
+    try:
+        c31, _, E31 = sg.count(3)
+        c5, _, E5 = sg.count(5)
+        monkeypatch.setenv("TN_COUNT_61", "1")
+        c61, _, E61 = sg.count(3)
+        assert c31 == c61 == c5 == o["count"] and E31 == E61 == E5
+    finally:
+        sg.close()
+
+
+def test_count_batch_31_bit_planes_beyond_2_to_the_61(monkeypatch):
+    """J = 0 on an 8 x 8 lattice, three coupling sets in one batch: 2^64 ground
+    states each, beyond one 61-bit prime, exact with the default planes (six 31-bit
+    primes and a witness)."""
+    base = I.square_lattice(8, coupling="pm1", seed=0)
+    sg = P.SpinGlass(dict(base, J=np.zeros_like(base["J"])), order="sweep",
+                     seq=I.square_sweep_order(8))
+    try:
+        Jz = np.zeros((3, len(base["J"])), np.float32)
+        E, counts, status = sg.count_batch(Jz, limbs_per=4)
+        assert np.all(status == 0) and all(c == 1 << 64 for c in counts)
+        assert np.all(E == 0.0)
+    finally:
+        sg.close()

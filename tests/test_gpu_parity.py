@@ -682,7 +682,9 @@ def test_cfg5a_rrg200_gauss_degeneracy(seed):
             assert sg.log2_peak <= 28
             c, _, E = sg.count(3)
             st, E2 = gpu_state(sg)
-            assert E2 == E
+            # the counting and the traceback programs add the float32 couplings in
+            # different orders (folded chain tables), so their E_min agree to rounding
+            assert close(E2, E)
             check_energy(inst, O.energy(inst, st), E)
             res.append((E, c))
         finally:

@@ -617,6 +617,8 @@ struct Builder {
   bool regmode = false;         // q == 2 values: register chains (ChainParams mode 1)
   bool fold = true;             // fold diagonal gates into replace tables (values only)
   int kRB = 6;                  // register legs of a register chain (4 to 6; 3 when counting)
+  bool grow_inner = false;      // rank-raising chains put the new leg innermost (else slowest)
+  int grow_pos(int R) const { return grow_inner ? R - 1 : 0; }
   int tmax = 11, wlow = 5;
   // chains still accepting gates, by the tensor they currently produce; a chain
   // is emitted when a step needs its output as a whole tensor
@@ -654,8 +656,11 @@ struct Builder {
   bool rank_fusion() const { return regmode && fold && P == 0 && kRB >= 5; }
 
   // a step adding one leg to `big` (no contraction, one batch leg at most): the
-  // chain starts from big, the new leg innermost; gate 0 is the diagonal gate
-  // adding the small operand over (new leg, batch leg)
+  // chain starts from big, the new leg slowest (or innermost with
+  // TN_GROW_INNER); gate 0 is the diagonal gate adding the small operand over
+  // (new leg, batch leg).  Slowest keeps the register legs of the chains that
+  // follow out of the low memory positions, where the warp tiles' copies would
+  // have to fall back to 4-byte accesses.
   bool try_grow(const PStep &st, int big, int small, CGate *g, std::vector<int> *ord) {
     if (!rank_fusion()) return false;
     const std::vector<int> &ob = order[big], &os = order[small];
@@ -667,11 +672,12 @@ struct Builder {
     const int R = (int)ob.size() + 1;
     if (R < kRB + 8) return false;
     *ord = ob;
-    ord->push_back(N[0]);
+    if (grow_inner) ord->push_back(N[0]);
+    else ord->insert(ord->begin(), N[0]);
     *g = CGate();
     g->kind = 1;
     g->btensor = small;
-    g->bpos.push_back(R - 1);
+    g->bpos.push_back(grow_pos(R));
     g->sBb[0] = stride(os, N[0]);
     if (!st.batch.empty()) {
       g->bpos.push_back(pos_of(*ord, st.batch[0]));
@@ -743,7 +749,8 @@ struct Builder {
     if (grow_ord) {
       // the new leg is a register leg of the chain
       m.grow = true;
-      if (pos_of(m.rpos, (int)ord.size() - 1) < 0) m.rpos.push_back((int)ord.size() - 1);
+      const int gp = grow_pos((int)ord.size());
+      if (pos_of(m.rpos, gp) < 0) m.rpos.push_back(gp);
     }
     m.state = ord;
     if (g.kind == 2) {
@@ -776,7 +783,7 @@ struct Builder {
   ChainParams reg_chain_params(const Macro &m, std::vector<Loc> *blocs) {
     ChainParams cp{};
     // positions are those of the state between the gates; the input lacks the
-    // grown leg (innermost), the output lacks the contracted one
+    // grown leg, the output lacks the contracted one
     const std::vector<int> &ord = m.state.empty() ? order[m.out] : m.state;
     const int R = (int)ord.size();
     std::vector<int> S = reg_legs(m);
@@ -784,7 +791,8 @@ struct Builder {
     auto s_state = [&](int p) { return int64_t(1) << (R - 1 - p); };
     auto s_in = [&](int p) -> int64_t {
       if (!m.grow) return s_state(p);
-      return p == R - 1 ? 0 : int64_t(1) << (R - 2 - p);
+      if (p == grow_pos(R)) return 0;
+      return grow_inner ? int64_t(1) << (R - 2 - p) : s_state(p);
     };
     auto s_out = [&](int p) -> int64_t {
       if (!m.contract) return s_state(p);
@@ -1073,14 +1081,14 @@ struct Builder {
         std::vector<Loc> bl;
         ct.p = chain_params(m, &bl);
         // the state between the gates; outer legs are read from the chain's
-        // input (without the grown leg, the innermost one, if any)
+        // input (without the grown leg, if any)
         const std::vector<int> &ord = m.state.empty() ? order[m.out] : m.state;
         const int R = (int)ord.size();
         std::vector<int> T = regmode ? reg_legs(m) : local_set(R, m.touched);
         for (int p = 0; p < R; ++p) {
           if (pos_of(T, p) >= 0) continue;
           ct.out_spin[ct.nout] = ord[p];
-          ct.out_stride[ct.nout] = m.grow ? ipow(q, R - 2 - p) : ipow(q, R - 1 - p);
+          ct.out_stride[ct.nout] = (m.grow && grow_inner) ? ipow(q, R - 2 - p) : ipow(q, R - 1 - p);
           int rank = 0;   // bit of this outer leg in tau: outer legs faster than it
           for (int p2 = p + 1; p2 < R; ++p2) rank += pos_of(T, p2) < 0;
           ct.out_rank[ct.nout] = rank;
@@ -1150,6 +1158,7 @@ struct Builder {
     regmode = q == 2 && (P == 0 || (P == 4 && rb == 8) || (P == 7 && rb == 4)) &&
               std::getenv("TN_TILE_CHAINS") == nullptr;
     fold = std::getenv("TN_NO_FOLD") == nullptr;
+    grow_inner = std::getenv("TN_GROW_INNER") != nullptr;
     // values: 6 register legs (2^6 states per thread) with folded tables,
     // 5 for the unfolded gate lists; counts: 3 legs (values + 4 residue planes)
     kRB = fold ? 6 : 5;

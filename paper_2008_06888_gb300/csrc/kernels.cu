@@ -1310,6 +1310,102 @@ __global__ void k_gemm_count(const GemmParams p, const T *__restrict__ A, const 
   }
 }
 
+// Counting planes of a GEMM step, tiled: a block owns 32 x 32 outputs (lanes
+// along n, each warp four rows), k slabs of 16 with the values and residues
+// of A and B staged in shared memory, and C's values read once.  Each output
+// sums the products of the counts over the k that reach its value.
+constexpr int GCT = 32, GCK = 16;
+
+template <typename T, typename R, int P>
+__global__ void __launch_bounds__(256) k_gemm_count_t(const GemmParams p, const T *__restrict__ A,
+                                                      const T *__restrict__ B,
+                                                      const T *__restrict__ C,
+                                                      const R *__restrict__ nA,
+                                                      const R *__restrict__ nB,
+                                                      R *__restrict__ nC, const PrimeSet ps,
+                                                      int64_t ib) {
+  A = inst_ptr(A, ib);
+  B = inst_ptr(B, ib);
+  C = inst_ptr(C, ib);
+  nA = inst_ptr(nA, ib);
+  nB = inst_ptr(nB, ib);
+  nC = inst_ptr(nC, ib);
+  __shared__ T sA[GCT][GCK + 1], sB[GCK][GCT];
+  __shared__ R sAn[P][GCT][GCK + 1], sBn[P][GCK][GCT];
+  __shared__ unsigned char okA[GCT][GCK + 1], okB[GCK][GCT];
+  const int64_t tm = (p.M + GCT - 1) / GCT, tn = (p.N + GCT - 1) / GCT;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t tile = blockIdx.x; tile < p.batch * tm * tn; tile += gridDim.x) {
+    const int64_t b = tile / (tm * tn), m0 = (tile / tn) % tm * GCT, n0 = tile % tn * GCT;
+    const int64_t n = n0 + tx;
+    T x[4];
+    R acc[4][P];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t m = m0 + ty * 4 + r;
+      x[r] = (m < p.M && n < p.N) ? C[b * p.sCb + m * p.sCm + n * p.sCn] : T(0);
+#pragma unroll
+      for (int i = 0; i < P; ++i) acc[r][i] = 0;
+    }
+    for (int64_t k0 = 0; k0 < p.K; k0 += GCK) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < GCT * GCK; e += 256) {
+        // A tile [m][k] (k fastest), B tile [k][n] (n fastest)
+        const int am = e / GCK, ak = e % GCK;
+        const int64_t gm = m0 + am, gk = k0 + ak;
+        const bool va = gm < p.M && gk < p.K;
+        const int64_t oa = b * p.sAb + gm * p.sAm + gk * p.sAk;
+        sA[am][ak] = va ? A[oa] : T(0);
+        okA[am][ak] = va;
+#pragma unroll
+        for (int i = 0; i < P; ++i) sAn[i][am][ak] = va ? nA[i * p.planeA + oa] : R(0);
+        const int bk = e / GCT, bn = e % GCT;
+        const int64_t hk = k0 + bk, hn = n0 + bn;
+        const bool vb = hk < p.K && hn < p.N;
+        const int64_t ob = b * p.sBb + hk * p.sBk + hn * p.sBn;
+        sB[bk][bn] = vb ? B[ob] : T(0);
+        okB[bk][bn] = vb;
+#pragma unroll
+        for (int i = 0; i < P; ++i) sBn[i][bk][bn] = vb ? nB[i * p.planeB + ob] : R(0);
+      }
+      __syncthreads();
+      const int kn = (int)((p.K - k0) < GCK ? (p.K - k0) : GCK);
+      for (int k = 0; k < kn; ++k) {
+        const T bv = sB[k][tx];
+        const bool bok = okB[k][tx];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int am = ty * 4 + r;
+          if (bok && okA[am][k] && sA[am][k] + bv == x[r]) {
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+              acc[r][i] = addmodR(acc[r][i], mulmodR(sAn[i][am][k], sBn[i][k][tx], ps.c[i]), ps.c[i]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t m = m0 + ty * 4 + r;
+      if (m >= p.M || n >= p.N) continue;
+      const int64_t oc = b * p.sCb + m * p.sCm + n * p.sCn;
+#pragma unroll
+      for (int i = 0; i < P; ++i) nC[i * p.planeC + oc] = acc[r][i];
+    }
+  }
+}
+
+template <typename T, typename R, int P>
+static void launch_gemm_count_t(const GemmParams &p, const void *A, const void *B, const void *C,
+                                const void *nA, const void *nB, void *nC, const PrimeSet &ps,
+                                const Batch &bt, cudaStream_t st) {
+  const int64_t tiles = p.batch * ((p.M + GCT - 1) / GCT) * ((p.N + GCT - 1) / GCT);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * 8));
+  k_gemm_count_t<T, R, P><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(
+      p, (const T *)A, (const T *)B, (const T *)C, (const R *)nA, (const R *)nB, (R *)nC, ps,
+      bt.ib);
+}
+
 cudaError_t launch_gemm_count(Dtype dt, const GemmParams &p, const void *xA, const void *xB,
                               const void *xC, const uint64_t *nA, const uint64_t *nB, uint64_t *nC,
                               const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
@@ -1327,6 +1423,25 @@ cudaError_t launch_gemm_count(Dtype dt, const GemmParams &p, const void *xA, con
                                         (const int32_t *)xC, a4, b4, c4, ps, bt, st)
                   : launch_count_splitk(p, (const int32_t *)xA, (const int32_t *)xB,
                                         (const int32_t *)xC, nA, nB, nC, ps, bt, st);
+  }
+  if (!std::getenv("TN_GEMM_COUNT_FLAT")) {
+    // tiled forms for the residue layouts in use
+    const bool f = dt == DT_F32;
+    if (ps.r32 && p.P == 7) {
+      if (f) launch_gemm_count_t<float, uint32_t, 7>(p, xA, xB, xC, nA, nB, nC, ps, bt, st);
+      else launch_gemm_count_t<int32_t, uint32_t, 7>(p, xA, xB, xC, nA, nB, nC, ps, bt, st);
+      return cudaGetLastError();
+    }
+    if (ps.r32 && p.P == 1) {
+      if (f) launch_gemm_count_t<float, uint32_t, 1>(p, xA, xB, xC, nA, nB, nC, ps, bt, st);
+      else launch_gemm_count_t<int32_t, uint32_t, 1>(p, xA, xB, xC, nA, nB, nC, ps, bt, st);
+      return cudaGetLastError();
+    }
+    if (!ps.r32 && p.P == 4) {
+      if (f) launch_gemm_count_t<float, uint64_t, 4>(p, xA, xB, xC, nA, nB, nC, ps, bt, st);
+      else launch_gemm_count_t<int32_t, uint64_t, 4>(p, xA, xB, xC, nA, nB, nC, ps, bt, st);
+      return cudaGetLastError();
+    }
   }
   dim3 blocks(grid_for(total, 256), bt.B);
   if (dt == DT_F32) {

@@ -702,3 +702,23 @@ def test_cfg5a_rrg200_planted_count():
         assert close(E, -float(np.abs(inst["J"].astype(np.float64)).sum())) and c == 2
     finally:
         sg.close()
+
+
+@pytest.mark.parametrize("planes", ["31-bit", "61-bit"])
+def test_tiled_counting_gemm_matches_flat_kernel(planes, monkeypatch):
+    """The counting GEMM steps (chimera 4x4 cells, greedy order: K = 2..16 with many
+    outputs) give the oracle's count through the tiled kernel and through the
+    one-output-per-thread kernel (TN_GEMM_COUNT_FLAT), for both residue widths."""
+    if planes == "61-bit":
+        monkeypatch.setenv("TN_COUNT_61", "1")
+    inst = I.chimera(4, coupling="pm1", seed=5)
+    o = O.solve(inst, order=I.chimera_sweep_order(4), config=False)
+    sg = P.SpinGlass(inst, order="greedy", seed=2, restarts=16)
+    try:
+        assert B.tn_plan_launches(sg.ctx, "count")["gemm"] > 0
+        c1, _, E1 = sg.count(3)
+        monkeypatch.setenv("TN_GEMM_COUNT_FLAT", "1")
+        c2, _, E2 = sg.count(3)
+        assert (E1, c1) == (E2, c2) == (o["E"], o["count"])
+    finally:
+        sg.close()

@@ -658,9 +658,9 @@ struct Builder {
   // a step adding one leg to `big` (no contraction, one batch leg at most): the
   // chain starts from big, the new leg slowest (or innermost with
   // TN_GROW_INNER); gate 0 is the diagonal gate adding the small operand over
-  // (new leg, batch leg).  Slowest keeps the register legs of the chains that
-  // follow out of the low memory positions, where the warp tiles' copies would
-  // have to fall back to 4-byte accesses.
+  // (new leg, batch leg).  With the new leg slowest the chain, which doubles
+  // its tensor, reads and writes each half of the output as one contiguous
+  // stream (measured faster than innermost on the square-lattice orders).
   bool try_grow(const PStep &st, int big, int small, CGate *g, std::vector<int> *ord) {
     if (!rank_fusion()) return false;
     const std::vector<int> &ob = order[big], &os = order[small];

@@ -164,20 +164,34 @@ bool tile_map(const ChainParams &p, const int64_t *hi, TileMap *tm) {
       if (regpos[k] == pos) return k;
     return -1;
   };
+  // one low leg by default: two (16-byte owner accesses) measured the same
+  // and spill a few registers in some chains
+  static const int low_max = std::getenv("TN_JIT_NO_LOW_LEGS") ? 0
+                             : std::getenv("TN_JIT_LOW_MAX")   ? std::atoi(std::getenv("TN_JIT_LOW_MAX"))
+                                                               : 1;
+  int a = 0;
+  while (a < low_max && a < 2 && reg_of(a) >= 0) ++a;
+  tm->a = a;
   int m = 0;
   for (int q = 0; q < 5; ++q) m += reg_of(q) < 0;
   int k = 0;
-  for (int q = 0; q < 5; ++q)
+  for (int q = a; q < 5; ++q)
     if (reg_of(q) >= 0) tm->gbit[reg_of(q)] = 1 << (m + k++);
+  int nh = 0;
+  for (int c = 0; c < tm->nreg; ++c) {
+    tm->lowbit[c] = regpos[c] < a ? regpos[c] : -1;
+    tm->hibit[c] = regpos[c] < a ? -1 : nh++;
+  }
   int rank = 0;
   for (int q = 0; (int)tm->tpos.size() < 5 + tm->nreg && q < 62; ++q) {
     const int c = reg_of(q);
     if (c >= 0) {
       tm->tpos.push_back(q);
-      tm->cbit.push_back((1 << (5 + c)) ^ tm->gbit[c]);
+      tm->cbit.push_back(tm->lowbit[c] >= 0 ? 1 << tm->lowbit[c]
+                                            : (1 << (5 + a + tm->hibit[c])) ^ (tm->gbit[c] << a));
     } else if (rank++ < 5) {
       tm->tpos.push_back(q);
-      tm->cbit.push_back(1 << (rank - 1));
+      tm->cbit.push_back(1 << (a + rank - 1));
     }
   }
   if ((int)tm->tpos.size() != 5 + tm->nreg) return false;
@@ -187,13 +201,17 @@ bool tile_map(const ChainParams &p, const int64_t *hi, TileMap *tm) {
 }
 
 int tile_slot(const TileMap &tm, int lane, int e) {
-  int c = 0, g = 0;
+  int c = 0, g = 0, low = 0;
   for (int k = 0; k < tm.nreg; ++k)
     if ((e >> tm.rbit[k]) & 1) {
-      c |= 1 << k;
-      g ^= tm.gbit[k];
+      if (tm.lowbit[k] >= 0) {
+        low |= 1 << tm.lowbit[k];
+      } else {
+        c |= 1 << tm.hibit[k];
+        g ^= tm.gbit[k];
+      }
     }
-  return (c << 5) | (lane ^ g);
+  return (c << (5 + tm.a)) | ((lane ^ g) << tm.a) | low;
 }
 
 void tile_word(const TileMap &tm, int i, int *D, int64_t *off) {
@@ -224,6 +242,11 @@ void tile_vec_lane(const TileMap &tm, int w, int lane, int *D, int64_t *off) {
       *D ^= tm.cbit[5 + k];
       *off += int64_t(1) << tm.tpos[5 + k];
     }
+}
+
+bool jit_compile_source(const std::string &src, const std::string &name, std::string *cubin,
+                        std::string *err) {
+  return compile(src, name, cubin, err);
 }
 
 std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &name) {
@@ -282,6 +305,11 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
   // first word a lane moves, as in tile_vec_lane.
   const bool vec = std::getenv("TN_JIT_NO_VEC") == nullptr;
   const int win = vec ? tile_vec(tin) : 1, wout = vec ? tile_vec(tout) : 1;
+  // 16-byte copies bypass L1 (.cg) unless the layout has low register legs:
+  // there the two lanes that share a 32-byte sector write shared-memory slots
+  // that are apart, and a bypassing copy reads the sector once per lane
+  static const char *ca_env = std::getenv("TN_JIT_CA16");   // "0": never, "1": always
+  const bool ca16 = ca_env ? *ca_env == '1' : tin.a > 0;
   auto lane_vec = [&](const TileMap &tm, int w, const char *Dn, const char *On) {
     std::ostringstream d;
     const int per = 32 / w;
@@ -306,7 +334,8 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     int D;
     int64_t off;
     tile_word(tin, i, &D, &off);
-    o << "      cp_async" << 4 * win << "(dst + (Din ^ " << D << "), src + " << off << ");\n";
+    o << "      cp_async" << 4 * win << (win == 4 && ca16 ? "ca" : "") << "(dst + (Din ^ " << D
+      << "), src + " << off << ");\n";
   }
   o << "    }\n    cp_async_commit();\n  };\n"
     << "  issue(tau, 0);\n"
@@ -340,15 +369,52 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     int cnt[6] = {0, 0, 0, 0, 0, 0};
     for (int k = 0; k < p.ntg; ++k)
       if (p.tg[k].kind != 1) cnt[p.tg[k].J]++;
+    // cost of a packing leg: a replace gate on it runs on the halves (about
+    // 64 more instructions than on a packed pair), and a layout whose first
+    // low leg is another leg needs register moves to pair the states of its
+    // vector accesses (about 64 per side)
+    auto low0 = [](const TileMap &tm) {
+      for (int k = 0; k < tm.nreg; ++k)
+        if (tm.lowbit[k] == 0) return tm.rbit[k];
+      return -1;
+    };
+    static const bool by_gates = std::getenv("TN_JIT_P_BY_GATES") != nullptr;
+    const int l_in = by_gates ? -1 : low0(tin), l_out = by_gates ? -1 : low0(tout);
+    auto cost = [&](int b) {
+      return 64 * cnt[b] + (l_in >= 0 && l_in != b ? 64 : 0) + (l_out >= 0 && l_out != b ? 64 : 0);
+    };
     P = 0;
     for (int b = 1; b < RB; ++b)
-      if (cnt[b] <= cnt[P]) P = b;
+      if (cost(b) <= cost(P)) P = b;
+  }
+  // Register states from the input tile: one access per group of the 2^a
+  // states that differ in the low legs (a vector of 2^a words); a state of a
+  // leg the input layout lacks (a rank-raising chain) reads its source state.
+  auto vec_type = [](int a) {
+    return a == 2 ? std::string("V") : a == 1 ? std::string("typename Vec2<T>::t") : std::string("T");
+  };
+  auto slot_expr = [](const TileMap &tm, int sl) {
+    // tile_slot(tm, lane, e) with sl = tile_slot(tm, 0, e) and its low bits cleared
+    std::ostringstream x;
+    x << "sw + " << (sl & ~((32 << tm.a) - 1)) << " + ((lane ^ " << ((sl >> tm.a) & 31) << ") << "
+      << tm.a << ")";
+    return x.str();
+  };
+  static const char *kComp[4] = {".x", ".y", ".z", ".w"};
+  std::map<int, int> in_group;   // slot of low bits 0 -> load index
+  std::vector<std::string> in_val(E);
+  for (int e = 0; e < E; ++e) {
+    const int sl = tile_slot(tin, 0, e), key = sl & ~((1 << tin.a) - 1);
+    auto it = in_group.find(key);
+    if (it == in_group.end()) {
+      it = in_group.emplace(key, (int)in_group.size()).first;
+      o << "    const " << vec_type(tin.a) << " r" << it->second << " = *reinterpret_cast<const "
+        << vec_type(tin.a) << " *>(" << slot_expr(tin, key) << ");\n";
+    }
+    in_val[e] = "r" + std::to_string(it->second) + (tin.a ? kComp[sl & ((1 << tin.a) - 1)] : "");
   }
   if (P < 0) {
-    for (int e = 0; e < E; ++e) {
-      const int sl = tile_slot(tin, 0, e);   // (c << 5) | g(c): the lane XORs in below
-      o << "    T v" << e << " = sw[" << (sl & ~31) << " + (lane ^ " << (sl & 31) << ")];\n";
-    }
+    for (int e = 0; e < E; ++e) o << "    T v" << e << " = " << in_val[e] << ";\n";
     o << "    __syncwarp();\n";   // the slot is reused for the outputs below
     for (int k = 0; k < p.ntg; ++k) {
       const TGate &t = p.tg[k];
@@ -381,12 +447,8 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
     }
   } else {
     const int PM = 1 << P;
-    for (int e = 0; e < E; ++e) {
-      if (e & PM) continue;
-      const int s0 = tile_slot(tin, 0, e), s1 = tile_slot(tin, 0, e | PM);
-      o << "    U u" << e << " = pk2(sw[" << (s0 & ~31) << " + (lane ^ " << (s0 & 31) << ")], sw["
-        << (s1 & ~31) << " + (lane ^ " << (s1 & 31) << ")]);\n";
-    }
+    for (int e = 0; e < E; ++e)
+      if (!(e & PM)) o << "    U u" << e << " = pk2(" << in_val[e] << ", " << in_val[e | PM] << ");\n";
     o << "    __syncwarp();\n";   // the slot is reused for the outputs below
     auto tabsel = [](int k, int kdig) { return kdig ? "hi" : "lo"; };
     for (int k = 0; k < p.ntg; ++k) {
@@ -453,10 +515,25 @@ std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &
   }
   (void)nmain;
   // outputs through the warp's tile, then whole 128-byte lines
+  // every group of 2^a output states fills one vector (the output layout has
+  // every leg but a contracted one)
+  std::map<int, std::vector<int>> out_group;
   for (int e = 0; e < E; ++e) {
     if (e & cmask) continue;
-    const int sl = tile_slot(tout, 0, e);
-    o << "    sw[" << (sl & ~31) << " + (lane ^ " << (sl & 31) << ")] = v" << e << ";\n";
+    const int sl = tile_slot(tout, 0, e), key = sl & ~((1 << tout.a) - 1);
+    auto &gv = out_group[key];
+    gv.resize(1 << tout.a, -1);
+    if (gv[sl & ((1 << tout.a) - 1)] != -1) return "";
+    gv[sl & ((1 << tout.a) - 1)] = e;
+  }
+  for (auto &kv : out_group) {
+    o << "    *reinterpret_cast<" << vec_type(tout.a) << " *>(" << slot_expr(tout, kv.first) << ") = ";
+    if (tout.a) o << vec_type(tout.a) << "{";
+    for (size_t j = 0; j < kv.second.size(); ++j) {
+      if (kv.second[j] < 0) return "";
+      o << (j ? ", " : "") << "v" << kv.second[j];
+    }
+    o << (tout.a ? "};\n" : ";\n");
   }
   o << "    __syncwarp();\n"
     << "    T *dst = C + base_out(tau - lane) + Oout;\n";

@@ -31,10 +31,18 @@ bool jit_chains(const std::vector<ChainParams> &chains, Dtype dt, std::vector<co
 // base + lane + off_i and in shared-memory slot D_lane ^ D_i (tile_word:
 // D_i, off_i; D_lane = XOR_j<5 {cbit[j] : bit j of lane}); the thread of lane
 // finds register state e at slot tile_slot(lane, e).
+// Slots: the a (<= 2) register legs at memory positions 0..a-1 ("low" legs)
+// are slot bits 0..a-1, the lane (XOR a swizzle of the other register bits)
+// slot bits a..a+4 and the other register bits the bits above, so that a
+// thread moves the 2^a states that differ in its low legs with one vector
+// access and the tile copies stay vector copies too.
 struct TileMap {
   int nreg = 0;                       // register legs of this layout
+  int a = 0;                          // low register legs
   int rbit[6] = {0, 0, 0, 0, 0, 0};   // their bits in the register state index
-  int gbit[6] = {0, 0, 0, 0, 0, 0};   // slot swizzle of each of them
+  int gbit[6] = {0, 0, 0, 0, 0, 0};   // lane swizzle of each of them
+  int lowbit[6] = {-1, -1, -1, -1, -1, -1};   // slot bit of a low leg
+  int hibit[6] = {-1, -1, -1, -1, -1, -1};    // bit above the lane of another leg
   std::vector<int> cbit;
   std::vector<int> tpos;
 };
@@ -52,6 +60,11 @@ void tile_vec_lane(const TileMap &tm, int w, int lane, int *D, int64_t *off);
 
 // Source of the specialised kernel `name` for one chain (exposed for tests).
 std::string jit_chain_source(const ChainParams &p, Dtype dt, const std::string &name);
+
+// NVRTC compilation of a generated source to an sm_103a cubin (no device
+// needed; exposed for host checks of generated kernels).
+bool jit_compile_source(const std::string &src, const std::string &name, std::string *cubin,
+                        std::string *err);
 
 // Launch a compiled chain kernel with the interpreting kernel's grid.
 cudaError_t launch_jit_chain(const void *kernel, const ChainParams &p, const char *arena,

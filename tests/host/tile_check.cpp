@@ -7,12 +7,16 @@
 // state e (tile_slot) holds the element at base(tau) + hi[e] of that layout,
 // and that no warp instruction (copy, or the owners' accesses for one e) has
 // two lanes on one bank.  The vector copies (tile_vec: w words per lane when
-// memory positions below log2 w are not register legs) must move the same
-// words to the same slots, w-aligned in memory and in shared memory.  Programs include chains that start from a
+// memory positions below log2 w map to slot bits below log2 w) must move the
+// same words to the same slots, w-aligned in memory and in shared memory, with
+// the lanes of each wavefront (32 / w of them) on distinct bank groups; the
+// owners move the 2^a states that differ in the low register legs (memory
+// positions 0..a-1) as one vector, conflict-free in the same sense.  Programs include chains that start from a
 // rank-raising step (the new leg is not a leg of the input) and chains that
 // end with a contraction (the contracted leg is not a leg of the output).
 // Exit status 0 when all hold.
 #include <cstdio>
+#include <algorithm>
 #include <map>
 #include <random>
 #include "jit.h"
@@ -38,7 +42,7 @@ static Net square(int L) {
 }
 int main() {
   std::mt19937_64 rng(9);
-  int chains = 0, sides = 0, partial = 0, bad = 0, conflicts = 0, vbad = 0, vsides = 0;
+  int chains = 0, sides = 0, partial = 0, bad = 0, conflicts = 0, vbad = 0, vsides = 0, lowsides = 0;
   for (int L : {16, 20, 24}) for (int ord : {0, 1, 2, 3}) for (int mode : {0, 1}) {
     Net net = square(L);
     Tree t; std::string err;
@@ -78,6 +82,7 @@ int main() {
           // vector copies (tile_vec): the same words and slots, w at a time
           const int w = tile_vec(tm);
           std::vector<int> vseen(32 * N, 0);
+          bool vused[32] = {false};
           for (int i = 0; i < N; i += w) {
             int Di; int64_t offi;
             tile_word(tm, i, &Di, &offi);
@@ -86,6 +91,10 @@ int main() {
               tile_vec_lane(tm, w, lane, &Dv, &ov);
               const int s0 = Dv ^ Di;
               if (s0 % w || (ov + offi) % w) vbad++;
+              // one wavefront per group of 32 / w lanes: distinct bank groups
+              if (lane % (32 / w) == 0) std::fill(vused, vused + 32, false);
+              if (vused[(s0 / w) % (32 / w)]) conflicts++;
+              vused[(s0 / w) % (32 / w)] = true;
               for (int j = 0; j < w; ++j) {
                 const int line = i + lane / (32 / w), word = (lane % (32 / w)) * w + j;
                 int Dl = 0;
@@ -99,21 +108,56 @@ int main() {
           }
           for (int v : vseen) if (v != 1) vbad++;
           if (trial == 0) vsides += w > 1;
+          // owners' accesses: the 2^a states that differ in the low legs form
+          // one aligned vector of the thread; the lanes of each group of
+          // 32 / 2^a (one wavefront) hit distinct bank groups
+          const int A = 1 << tm.a;
           for (int e = 0; e < E; ++e) {
             bool used[32] = {false};
             for (int lane = 0; lane < 32; ++lane) {
               const int d = tile_slot(tm, lane, e);
               if (d < 0 || d >= 32 * N || slot[d] != base_of(p, t0 + lane, ssh) + hi[e]) bad++;
-              if (used[d & 31]) conflicts++;
-              used[d & 31] = true;
+              if ((d & (A - 1)) != (tile_slot(tm, 0, e) & (A - 1))) bad++;
+              if (lane % (32 / A) == 0) std::fill(used, used + 32, false);
+              const int bg = (d / A) % (32 / A);
+              if (used[bg]) conflicts++;
+              used[bg] = true;
             }
           }
+          lowsides += trial == 0 && tm.a > 0;
         }
       }
     }
   }
-  printf("vector copies: layouts %d wrong %d\n", vsides, vbad);
+  // the generated kernels of chains with low register legs compile (NVRTC,
+  // FP32 and INT32 forms; no device needed)
+  int compiled = 0, compile_fail = 0;
+  {
+    Net net = square(24);
+    Tree t; std::string err; CostModel cm;
+    tree_greedy(net, 7, 4, cm, &t, &err);
+    Plan pl; if (!classify(net, t, &pl, &err)) return 2;
+    for (Dtype dt : {DT_F32, DT_I32}) {
+      Program pg; if (!build_program(net, pl, PM_ENERGY, dt, 0, 0, &pg, &err)) return 2;
+      int n = 0;
+      for (const ChainParams &p : pg.chains) {
+        TileMap a, b;
+        if (p.mode != 1 || p.P != 0 || !tile_map(p, p.hi_in, &a) || !tile_map(p, p.hi_out, &b)) continue;
+        if (a.a == 0 && b.a == 0) continue;
+        if (n++ >= 3) break;
+        const std::string name = "tn_chain_check" + std::to_string(compiled + compile_fail);
+        const std::string src = jit_chain_source(p, dt, name);
+        std::string cubin, cerr;
+        if (!src.empty() && jit_compile_source(src, name, &cubin, &cerr)) compiled++;
+        else { compile_fail++; fprintf(stderr, "%s\n", cerr.c_str()); }
+      }
+    }
+  }
+  printf("generated kernels with low register legs: compiled %d failed %d\n", compiled, compile_fail);
+  if (compiled == 0 || compile_fail) return 1;
+  printf("vector copies: layouts %d wrong %d; layouts with low register legs %d\n", vsides, vbad,
+         lowsides);
   printf("chains %d layouts %d (without a register leg: %d) wrong %d bank_conflicts %d\n", chains,
          sides, partial, bad, conflicts);
-  return (bad || conflicts || vbad || chains == 0 || vsides == 0) ? 1 : 0;
+  return (bad || conflicts || vbad || chains == 0 || vsides == 0 || lowsides == 0) ? 1 : 0;
 }

@@ -56,9 +56,12 @@ def test_tile_copies_of_compiled_chains(tmp_path):
     exe = _build_check(tmp_path, "tile_check", extra_src=("jit.cpp",),
                        libs=("-I" + build.OUT_DIR, "-L" + cuda_lib, "-lnvrtc", "-lcudart", "-ldl"))
     env = dict(os.environ, LD_LIBRARY_PATH=cuda_lib + ":" + os.environ.get("LD_LIBRARY_PATH", ""))
-    r = subprocess.run([exe], capture_output=True, text=True, timeout=240, env=env)
-    assert r.returncode == 0, r.stdout + r.stderr
-    assert r.stdout.split()[-3:] == ["0", "bank_conflicts", "0"] or "wrong 0 bank_conflicts 0" in r.stdout
+    # default slot layout (at most one low register leg) and the two-leg form
+    for low_max in ("1", "2"):
+        env["TN_JIT_LOW_MAX"] = low_max
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=240, env=env)
+        assert r.returncode == 0, r.stdout + r.stderr
+        assert "wrong 0 bank_conflicts 0" in r.stdout and "compiled 6 failed 0" in r.stdout
 
 
 @pytest.mark.timeout(300)

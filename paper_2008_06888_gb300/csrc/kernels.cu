@@ -2374,6 +2374,35 @@ __global__ void __launch_bounds__(NT, MINB) k_tchain(const ChainParams p,
 // counts of the tied states; the gate's own counts multiply in unless it is a
 // leaf (all counts 1).
 
+// 2^LW consecutive 4-byte words (8- or 16-byte aligned) to and from registers
+template <int LW, typename W>
+__device__ __forceinline__ void rcc_vload(const W *src, W *dst) {
+  static_assert(sizeof(W) == 4, "vector accesses of 4-byte words");
+  if constexpr (LW == 1) {
+    const uint2 x = *reinterpret_cast<const uint2 *>(src);
+    dst[0] = __builtin_bit_cast(W, x.x);
+    dst[1] = __builtin_bit_cast(W, x.y);
+  } else {
+    const uint4 x = *reinterpret_cast<const uint4 *>(src);
+    dst[0] = __builtin_bit_cast(W, x.x);
+    dst[1] = __builtin_bit_cast(W, x.y);
+    dst[2] = __builtin_bit_cast(W, x.z);
+    dst[3] = __builtin_bit_cast(W, x.w);
+  }
+}
+template <int LW, typename W>
+__device__ __forceinline__ void rcc_vstore(W *dst, const W *src) {
+  static_assert(sizeof(W) == 4, "vector accesses of 4-byte words");
+  if constexpr (LW == 1) {
+    *reinterpret_cast<uint2 *>(dst) =
+        make_uint2(__builtin_bit_cast(uint32_t, src[0]), __builtin_bit_cast(uint32_t, src[1]));
+  } else {
+    *reinterpret_cast<uint4 *>(dst) =
+        make_uint4(__builtin_bit_cast(uint32_t, src[0]), __builtin_bit_cast(uint32_t, src[1]),
+                   __builtin_bit_cast(uint32_t, src[2]), __builtin_bit_cast(uint32_t, src[3]));
+  }
+}
+
 template <int RB, int NP, bool UNIT, typename T, typename R>
 __device__ __forceinline__ void rcc_replace(int J, T (&v)[1 << RB], R (&n)[NP][1 << RB],
                                             const ChainGate &g, const T *sB, const R *sBn,
@@ -2438,7 +2467,10 @@ __device__ __forceinline__ void rcc_diag(T (&v)[1 << RB], R (&n)[NP][1 << RB],
   }
 }
 
-template <typename T, int RB, int NP, typename R = uint64_t>
+// LW > 0 (4-byte residues only): register legs 0..LW-1 sit at memory positions
+// 0..LW-1 (low_legs_first), so the 2^LW states that differ in them are
+// consecutive words and each array moves with one 8- or 16-byte access.
+template <typename T, int RB, int NP, typename R = uint64_t, int LW = 0>
 __global__ void __launch_bounds__(256, 2) k_rchain_count(const ChainParams p,
                                                          const T *__restrict__ X,
                                                          const R *__restrict__ Xn,
@@ -2468,12 +2500,22 @@ __global__ void __launch_bounds__(256, 2) k_rchain_count(const ChainParams p,
     }
     T v[1 << RB];
     R n[NP][1 << RB];
+    if constexpr (LW == 0) {
 #pragma unroll
-    for (int e = 0; e < (1 << RB); ++e) {
-      const int64_t off = base + soff[e];
-      v[e] = A[off];
+      for (int e = 0; e < (1 << RB); ++e) {
+        const int64_t off = base + soff[e];
+        v[e] = A[off];
 #pragma unroll
-      for (int pl = 0; pl < NP; ++pl) n[pl][e] = An[pl * p.planeA + off];
+        for (int pl = 0; pl < NP; ++pl) n[pl][e] = An[pl * p.planeA + off];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < (1 << RB); e += 1 << LW) {
+        const int64_t off = base + soff[e];
+        rcc_vload<LW>(A + off, &v[e]);
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl) rcc_vload<LW>(An + pl * p.planeA + off, &n[pl][e]);
+      }
     }
     for (int gi = 0; gi < p.ngates; ++gi) {
       const ChainGate &g = p.g[gi];
@@ -2497,14 +2539,58 @@ __global__ void __launch_bounds__(256, 2) k_rchain_count(const ChainParams p,
         }
       }
     }
+    if constexpr (LW == 0) {
 #pragma unroll
-    for (int e = 0; e < (1 << RB); ++e) {
-      const int64_t off = base + soff[e];
-      C[off] = v[e];
+      for (int e = 0; e < (1 << RB); ++e) {
+        const int64_t off = base + soff[e];
+        C[off] = v[e];
 #pragma unroll
-      for (int pl = 0; pl < NP; ++pl) Cn[pl * p.planeC + off] = n[pl][e];
+        for (int pl = 0; pl < NP; ++pl) Cn[pl * p.planeC + off] = n[pl][e];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < (1 << RB); e += 1 << LW) {
+        const int64_t off = base + soff[e];
+        rcc_vstore<LW>(C + off, &v[e]);
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl) rcc_vstore<LW>(Cn + pl * p.planeC + off, &n[pl][e]);
+      }
     }
   }
+}
+
+// Register legs of a counting chain renumbered so that the legs at memory
+// positions 0 and 1 (element strides 1 and 2), where there are such, become
+// legs 0 and 1 (state bits 0 and 1); returns how many lead (0..2).  The chain
+// computes the same values: every gate names its legs through the new numbers.
+static int low_legs_first(const ChainParams &p, ChainParams *q) {
+  const int RB = p.t;
+  int l0 = -1, l1 = -1;
+  for (int b = 0; b < RB; ++b) {
+    if (p.hi_off[1 << b] == 1) l0 = b;
+    if (p.hi_off[1 << b] == 2) l1 = b;
+  }
+  const int lw = l0 < 0 ? 0 : l1 < 0 ? 1 : 2;
+  *q = p;
+  if (lw == 0) return 0;
+  int perm[TN_CHAIN_MAX_T];   // old leg -> new leg
+  int next = lw;
+  for (int b = 0; b < RB; ++b) perm[b] = b == l0 ? 0 : (lw == 2 && b == l1) ? 1 : next++;
+  for (int e = 0; e < (1 << RB); ++e) {
+    int f = 0;
+    for (int b = 0; b < RB; ++b)
+      if ((e >> b) & 1) f |= 1 << perm[b];
+    q->hi_off[f] = p.hi_off[e];
+    q->hi_in[f] = p.hi_in[e];
+    q->hi_out[f] = p.hi_out[e];
+  }
+  for (int i = 0; i < p.ngates; ++i) {
+    ChainGate &g = q->g[i];
+    if (g.kind == 0 || g.kind == 2) g.ls = perm[p.g[i].ls];
+    for (int k = 0; k < 2 && k < g.nb; ++k)
+      if (p.g[i].lsb[k] >= 0) g.lsb[k] = perm[p.g[i].lsb[k]];
+  }
+  return lw;
 }
 
 cudaError_t launch_rchain_count(Dtype dt, const ChainParams &p, const char *arena,
@@ -2512,19 +2598,39 @@ cudaError_t launch_rchain_count(Dtype dt, const ChainParams &p, const char *aren
                                 const PrimeSet &ps, const Batch &bt, cudaStream_t st) {
   if (p.t != 3 || !((p.P == 4 && !ps.r32) || (p.P == 7 && ps.r32))) return cudaErrorInvalidValue;
   const int64_t need = (p.outer + 255) / 256;
-#define TN_RCC(T_, NP_, R_)                                                                      \
+  // vector accesses (4-byte residues): the low legs lead, and every array
+  // start, plane distance and instance stride is a multiple of the vector
+  ChainParams q;
+  int lw = ps.r32 && !std::getenv("TN_RCC_NO_VEC") ? low_legs_first(p, &q) : 0;
+  if (lw > 0) {
+    const uint64_t vb = 4u << lw;
+    const bool aligned = (reinterpret_cast<uintptr_t>(Ax) | reinterpret_cast<uintptr_t>(Cx) |
+                          reinterpret_cast<uintptr_t>(An) | reinterpret_cast<uintptr_t>(Cn)) %
+                                 vb == 0 &&
+                         (uint64_t)bt.ib % vb == 0 && p.planeA % (1 << lw) == 0 &&
+                         p.planeC % (1 << lw) == 0;
+    if (!aligned) lw = 0;
+  }
+  const ChainParams &pp = lw > 0 ? q : p;
+#define TN_RCC(T_, NP_, R_, LW_)                                                                 \
   do {                                                                                           \
     const int64_t blocks =                                                                       \
-        wave_blocks(need, bt.B, resident_slots(k_rchain_count<T_, 3, NP_, R_>, 256, 0));         \
-    k_rchain_count<T_, 3, NP_, R_><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(                \
-        p, reinterpret_cast<const T_ *>(arena), reinterpret_cast<const R_ *>(arena),             \
+        wave_blocks(need, bt.B, resident_slots(k_rchain_count<T_, 3, NP_, R_, LW_>, 256, 0));    \
+    k_rchain_count<T_, 3, NP_, R_, LW_><<<dim3((unsigned)blocks, bt.B), 256, 0, st>>>(           \
+        pp, reinterpret_cast<const T_ *>(arena), reinterpret_cast<const R_ *>(arena),            \
         static_cast<const T_ *>(Ax), reinterpret_cast<const R_ *>(An), static_cast<T_ *>(Cx),    \
         reinterpret_cast<R_ *>(Cn), ps, bt.ib);                                                  \
   } while (0)
   if (dt == DT_F32) {
-    if (ps.r32) TN_RCC(float, 7, uint32_t); else TN_RCC(float, 4, uint64_t);
+    if (!ps.r32) TN_RCC(float, 4, uint64_t, 0);
+    else if (lw == 2) TN_RCC(float, 7, uint32_t, 2);
+    else if (lw == 1) TN_RCC(float, 7, uint32_t, 1);
+    else TN_RCC(float, 7, uint32_t, 0);
   } else {
-    if (ps.r32) TN_RCC(int32_t, 7, uint32_t); else TN_RCC(int32_t, 4, uint64_t);
+    if (!ps.r32) TN_RCC(int32_t, 4, uint64_t, 0);
+    else if (lw == 2) TN_RCC(int32_t, 7, uint32_t, 2);
+    else if (lw == 1) TN_RCC(int32_t, 7, uint32_t, 1);
+    else TN_RCC(int32_t, 7, uint32_t, 0);
   }
 #undef TN_RCC
   return cudaGetLastError();

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
+
 #include "kernels.h"
 #include "chain_dev.cuh"
 #include "modarith.cuh"
@@ -17,7 +19,18 @@ namespace tn {
 // indices per thread; every value and residue of A (and of B, unless its counts
 // are all 1) is loaded before any is compared, then the counts of the maximal
 // k add up (ties) with predicated modular products.
-template <typename T, int KS, int NS, int P, typename R>
+// Four consecutive 4-byte words (16-byte aligned) stored with one access.
+template <typename W>
+__device__ __forceinline__ void gtc_store4(W *dst, const W *src) {
+  static_assert(sizeof(W) == 4, "4-byte words");
+  *reinterpret_cast<uint4 *>(dst) =
+      make_uint4(__builtin_bit_cast(uint32_t, src[0]), __builtin_bit_cast(uint32_t, src[1]),
+                 __builtin_bit_cast(uint32_t, src[2]), __builtin_bit_cast(uint32_t, src[3]));
+}
+
+// VC: the NS outputs of an outer index are NS consecutive words of C (and of
+// each plane), so every four of them are stored with one 16-byte access.
+template <typename T, int KS, int NS, int P, typename R, bool VC = false>
 __global__ void __launch_bounds__(256) k_gate_tc(const GateParams p, const T *__restrict__ A,
                                                  const T *__restrict__ B, T *__restrict__ C,
                                                  const R *__restrict__ nA,
@@ -70,37 +83,64 @@ __global__ void __launch_bounds__(256) k_gate_tc(const GateParams p, const T *__
 #pragma unroll
         for (int i = 0; i < P; ++i) na[u][i][k] = nA[i * p.planeA + e];
       }
+    // output n of outer index u: the max over k and the counts of the tied k
+    auto out_one = [&](int u, int n, T &best, R (&cnt)[P]) {
+      const int64_t nb = p.nB[n];
+      T v[KS];
+      R bn[P][KS];
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const int64_t e = ob[u] + kB[k] + nb;
+        v[k] = a[u][k] + (p.hasB ? B[e] : T(0));
+#pragma unroll
+        for (int i = 0; i < P; ++i) bn[i][k] = mulB ? nB[i * p.planeB + e] : R(1);
+      }
+      best = v[0];
+#pragma unroll
+      for (int k = 1; k < KS; ++k) best = max(best, v[k]);
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        R c = 0;
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          if (v[k] == best) {
+            const R t = mulB ? mulmodR(na[u][i][k], bn[i][k], ps.c[i]) : na[u][i][k];
+            c = addmodR(c, t, ps.c[i]);
+          }
+        }
+        cnt[i] = c;
+      }
+    };
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (!live[u]) continue;
+      if constexpr (VC) {
 #pragma unroll
-      for (int n = 0; n < NS; ++n) {
-        const int64_t nb = p.nB[n];
-        T v[KS];
-        R bn[P][KS];
+        for (int n0 = 0; n0 < NS; n0 += 4) {
+          T best4[4];
+          R cnt4[P][4];
 #pragma unroll
-        for (int k = 0; k < KS; ++k) {
-          const int64_t e = ob[u] + kB[k] + nb;
-          v[k] = a[u][k] + (p.hasB ? B[e] : T(0));
+          for (int j = 0; j < 4; ++j) {
+            R cnt[P];
+            out_one(u, n0 + j, best4[j], cnt);
 #pragma unroll
-          for (int i = 0; i < P; ++i) bn[i][k] = mulB ? nB[i * p.planeB + e] : R(1);
-        }
-        T best = v[0];
-#pragma unroll
-        for (int k = 1; k < KS; ++k) best = max(best, v[k]);
-        const int64_t c = oc[u] + p.nC[n];
-        C[c] = best;
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          R cnt = 0;
-#pragma unroll
-          for (int k = 0; k < KS; ++k) {
-            if (v[k] == best) {
-              const R t = mulB ? mulmodR(na[u][i][k], bn[i][k], ps.c[i]) : na[u][i][k];
-              cnt = addmodR(cnt, t, ps.c[i]);
-            }
+            for (int i = 0; i < P; ++i) cnt4[i][j] = cnt[i];
           }
-          nC[i * p.planeC + c] = cnt;
+          const int64_t c = oc[u] + n0;
+          gtc_store4(C + c, best4);
+#pragma unroll
+          for (int i = 0; i < P; ++i) gtc_store4(nC + i * p.planeC + c, cnt4[i]);
+        }
+      } else {
+#pragma unroll
+        for (int n = 0; n < NS; ++n) {
+          T best;
+          R cnt[P];
+          out_one(u, n, best, cnt);
+          const int64_t c = oc[u] + p.nC[n];
+          C[c] = best;
+#pragma unroll
+          for (int i = 0; i < P; ++i) nC[i * p.planeC + c] = cnt[i];
         }
       }
     }
@@ -110,7 +150,7 @@ __global__ void __launch_bounds__(256) k_gate_tc(const GateParams p, const T *__
 template <typename T, typename R>
 bool launch_gate_tc_r(const GateParams &p, const T *A, const T *B, T *C, const R *nA,
                              const R *nB, R *nC, const PrimeSet &ps, dim3 blocks, int64_t ib,
-                             cudaStream_t st) {
+                             bool vc, cudaStream_t st) {
 #define TN_GTC(KS_, NS_, P_)                                                                  \
   if (p.Ks == KS_ && p.Ns == NS_ && p.P == P_) {                                              \
     k_gate_tc<T, KS_, NS_, P_, R><<<blocks, 256, 0, st>>>(p, A, B, C, nA, nB, nC, ps, ib);   \
@@ -119,6 +159,13 @@ bool launch_gate_tc_r(const GateParams &p, const T *A, const T *B, T *C, const R
 #define TN_GTC_P(P_)                                                                          \
   TN_GTC(1, 1, P_) TN_GTC(1, 2, P_) TN_GTC(2, 1, P_) TN_GTC(1, 4, P_) TN_GTC(2, 4, P_)        \
   TN_GTC(2, 16, P_)
+  if (vc && p.Ks == 2 && p.Ns == 16 && (p.P == 7 || p.P == 1)) {
+    if (p.P == 7)
+      k_gate_tc<T, 2, 16, 7, R, true><<<blocks, 256, 0, st>>>(p, A, B, C, nA, nB, nC, ps, ib);
+    else
+      k_gate_tc<T, 2, 16, 1, R, true><<<blocks, 256, 0, st>>>(p, A, B, C, nA, nB, nC, ps, ib);
+    return true;
+  }
   TN_GTC_P(1)
   TN_GTC_P(7)
 #undef TN_GTC_P
@@ -135,8 +182,16 @@ bool launch_gate_tc_typed(const GateParams &p, const T *A, const T *B, T *C, con
   const int64_t cap = (int64_t)num_sms() * 32;
   if (nb > cap) nb = cap;
   if (nb < 1) nb = 1;
+  // 16-byte output stores: the outputs of an outer index are consecutive words,
+  // and every output start, plane distance and instance stride is a multiple
+  // of four words
+  bool vc = p.Ns % 4 == 0 && !std::getenv("TN_GATE_TC_NO_VEC") &&
+            (reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(nC)) % 16 == 0 &&
+            (uint64_t)bt.ib % 16 == 0 && p.planeC % 4 == 0;
+  for (int n = 0; vc && n < p.Ns; ++n) vc = p.nC[n] == n;
+  for (int s = 0; vc && s < p.nseg; ++s) vc = p.seg_sC[s] % 4 == 0;
   return launch_gate_tc_r<T, uint32_t>(p, A, B, C, nA, nB, nC, ps, dim3((unsigned)nb, bt.B), bt.ib,
-                                       st);
+                                       vc, st);
 }
 
 }  // namespace tn

@@ -1270,6 +1270,8 @@ bool build_program(const Net &net, const Plan &plan, ProgMode mode, Dtype dt, in
                          (long long)g.seg_sA[s2], (long long)g.seg_sB[s2], (long long)g.seg_sC[s2]);
           std::fprintf(stderr, " kA");
           for (int k = 0; k < g.Ks; ++k) std::fprintf(stderr, " %lld", (long long)g.kA[k]);
+          std::fprintf(stderr, " nC");
+          for (int k = 0; k < g.Ns; ++k) std::fprintf(stderr, " %lld", (long long)g.nC[k]);
         }
         if (o.kind == OP_CHAIN) {
           const ChainParams &c = pr->chains[o.idx];

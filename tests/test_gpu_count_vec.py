@@ -97,3 +97,50 @@ def test_vector_counting_chains_in_a_mixed_batch(monkeypatch):
     st2, E2, c2, s2 = run()
     assert st1 == st2 == 0 and (s1 == 0).all() and (s2 == 0).all()
     assert np.array_equal(E1, E2) and c1 == c2
+
+
+_DUMP_CHIMERA = r"""
+import sys
+sys.path.insert(0, {root!r})
+import instances as I
+import paper_2008_06888_gb300 as P
+from paper_2008_06888_gb300 import binding as B
+inst = I.chimera({L}, coupling="pm1", seed={seed})
+sg = P.SpinGlass(inst, order="sweep", seq=I.chimera_sweep_order({L}))
+B.tn_plan_launches(sg.ctx, "count")
+"""
+
+
+def _contiguous_16_state_gates(L, seed):
+    """Gate steps of the count program with 16 new states stored as 16
+    consecutive words per outer index (host only, from the program dump)."""
+    env = dict(os.environ, TN_DUMP_PROGRAM="c")
+    r = subprocess.run([sys.executable, "-c", _DUMP_CHIMERA.format(root=ROOT, L=L, seed=seed)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    want = " nC " + " ".join(str(n) for n in range(16))
+    return sum(1 for line in r.stderr.splitlines()
+               if " Ks 2 Ns 16 " in line and line.rstrip().endswith(want))
+
+
+@pytest.mark.parametrize("L,seed", [(4, 2), (5, 7)])
+def test_vector_stores_of_16_state_counting_gates(L, seed, monkeypatch):
+    """Counting gates with two contraction states and 16 new states (the
+    chimera cell gates, Sec. IV) store four outputs per 16-byte access where
+    the 16 outputs of an outer index are consecutive; TN_GATE_TC_NO_VEC=1
+    stores them one by one.  Both equal the oracle."""
+    assert _contiguous_16_state_gates(L, seed) > 0
+    inst = I.chimera(L, coupling="pm1", seed=seed)
+    seq = I.chimera_sweep_order(L)
+    o = O.solve(inst, order=seq, config=False)
+    res = []
+    for novec in (False, True):
+        if novec:
+            monkeypatch.setenv("TN_GATE_TC_NO_VEC", "1")
+        sg = P.SpinGlass(inst, order="sweep", seq=seq)
+        try:
+            c, _, E = sg.count(3)
+        finally:
+            sg.close()
+        res.append((c, E))
+    assert res[0] == res[1] == (o["count"], o["E"]), (res, o["count"], o["E"])

@@ -371,8 +371,8 @@ def measure_gemm(shapes, reps=5):
             macs = bt * M * N * K
             ops = 2 * macs / (ms * 1e-3)
             # ALU instructions one multiply-add needs: an add and half a three-input
-            # max (FP32) or an add and a two-input max (INT32)
-            ipm = 1.5 if dt == torch.float32 else 2.0
+            # max (FP32), or one fused add-max (INT32)
+            ipm = 1.5 if dt == torch.float32 else 1.0
             out[f"{str(dt).split('.')[-1]}_{bt}x{M}x{N}x{K}"] = {
                 "ms": ms, "tropical_Top_s": ops / 1e12, "T_MAC_s": macs / (ms * 1e-3) / 1e12,
                 "frac_of_fp32_nontensor_peak": ops / peak_ops,
